@@ -1,0 +1,246 @@
+"""Python access to the FP64 CPU oracle (``pdhg_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The CUDA solver never imports this
+package, and this package imports nothing from the solver.
+
+``build()`` compiles ``pdhg_oracle.c`` with gcc into ``liboracle.so`` next to
+it (plain C, -O2, no architecture flags, so it builds the same on x86-64 and
+aarch64).  Every wrapper below converts numpy arrays and calls the C function
+of the same role; see the C file for the paper passages each follows.
+
+Parity status: every function is pinned by the not-gpu tests except the
+restart / primal-weight / adaptive-step decision logic of ``solve``, which the
+paper pins only through its own rules ("parity unpinned" beyond the invariant
+that every accepted step size satisfies eta <= eta_bar).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pdhg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc) if it is missing or stale."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Lp(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("vals", C.c_void_p),
+                ("sense", C.c_void_p), ("c", C.c_void_p), ("q", C.c_void_p),
+                ("l", C.c_void_p), ("u", C.c_void_p)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iters", C.c_int64), ("check_every", C.c_int32),
+                ("ruiz_iters", C.c_int32), ("ruiz_tol", C.c_double),
+                ("pock_chambolle", C.c_int32), ("power_iters", C.c_int32),
+                ("adaptive_step", C.c_int32), ("primal_weight_update", C.c_int32),
+                ("restarts", C.c_int32), ("eta_scale", C.c_double),
+                ("beta_sufficient", C.c_double), ("beta_necessary", C.c_double),
+                ("beta_artificial", C.c_double), ("eps_zero", C.c_double),
+                ("x0", C.c_void_p), ("y0", C.c_void_p),
+                ("omega0", C.c_double), ("eta0", C.c_double)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pad", C.c_int32), ("iters", C.c_int64),
+                ("attempts", C.c_int64), ("restarts", C.c_int64),
+                ("pobj", C.c_double), ("dobj", C.c_double), ("rel_gap", C.c_double),
+                ("rel_pres", C.c_double), ("rel_dres", C.c_double),
+                ("omega", C.c_double), ("eta", C.c_double), ("norm_K", C.c_double)]
+
+
+TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",
+                "kkt_cur", "kkt_avg", "rel_gap", "rel_pres", "rel_dres", "kkt_cand")
+
+DEFAULTS = dict(tol=1e-4, max_iters=100000, check_every=64, ruiz_iters=10, ruiz_tol=1e-4,
+                pock_chambolle=0, power_iters=100, adaptive_step=1, primal_weight_update=1,
+                restarts=1, eta_scale=0.9, beta_sufficient=0.2, beta_necessary=0.8,
+                beta_artificial=0.36, eps_zero=1e-6, omega0=0.0, eta0=0.0)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.POINTER
+        _lib.orc_spmv.argtypes = [P(_Lp), C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_spmv_t.argtypes = [P(_Lp), C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_ruiz.argtypes = [P(_Lp), C.c_int32, C.c_double, C.c_int32,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_ruiz.restype = C.c_int
+        _lib.orc_power_norm.argtypes = [P(_Lp), C.c_void_p, C.c_int32]
+        _lib.orc_power_norm.restype = C.c_double
+        _lib.orc_proj_lambda.argtypes = [C.c_int64] + [C.c_void_p] * 4
+        _lib.orc_kkt.argtypes = [P(_Lp)] + [C.c_void_p] * 7 + [C.c_double, C.c_void_p]
+        _lib.orc_pdhg_step.argtypes = [P(_Lp)] + [C.c_void_p] * 7 + [C.c_double, C.c_double,
+                                                                     C.c_void_p, C.c_void_p]
+        _lib.orc_solve.argtypes = [P(_Lp), P(_Opts), C.c_void_p, C.c_void_p, P(_Info),
+                                   C.c_void_p, C.c_int64, P(C.c_int64)]
+        _lib.orc_solve.restype = C.c_int
+        _lib.orc_unrolled_forward.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
+                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_unrolled_adjoint.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
+                                              C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p]
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class _Bound:
+    """Holds contiguous copies of an LP's arrays and the C struct over them."""
+
+    def __init__(self, lp, vals=None, c=None, q=None, l=None, u=None):
+        self.rp = np.ascontiguousarray(lp.row_ptr, dtype=np.int64)
+        self.ci = np.ascontiguousarray(lp.col_idx, dtype=np.int32)
+        self.v = _f64(lp.vals if vals is None else vals)
+        self.s = np.ascontiguousarray(lp.sense, dtype=np.uint8)
+        self.c = _f64(lp.c if c is None else c)
+        self.q = _f64(lp.q if q is None else q)
+        self.l = _f64(lp.l if l is None else l)
+        self.u = _f64(lp.u if u is None else u)
+        self.st = _Lp(lp.m, lp.n, _ptr(self.rp), _ptr(self.ci), _ptr(self.v), _ptr(self.s),
+                      _ptr(self.c), _ptr(self.q), _ptr(self.l), _ptr(self.u))
+        self.m, self.n = lp.m, lp.n
+
+
+def spmv(lp, x, vals=None):
+    b = _Bound(lp, vals)
+    x = _f64(x)
+    out = np.empty(lp.m)
+    _load().orc_spmv(C.byref(b.st), _ptr(b.v), _ptr(x), _ptr(out))
+    return out
+
+
+def spmv_t(lp, y, vals=None):
+    b = _Bound(lp, vals)
+    y = _f64(y)
+    out = np.empty(lp.n)
+    _load().orc_spmv_t(C.byref(b.st), _ptr(b.v), _ptr(y), _ptr(out))
+    return out
+
+
+def ruiz(lp, iters=10, tol=1e-4, pock_chambolle=False):
+    """Algorithm 3.  Returns (scaled values, R, C, passes) with K~ = diag(R) K diag(C)."""
+    b = _Bound(lp)
+    vs = np.empty(lp.nnz)
+    R = np.empty(lp.m)
+    Cc = np.empty(lp.n)
+    passes = _load().orc_ruiz(C.byref(b.st), iters, tol, int(pock_chambolle),
+                              _ptr(vs), _ptr(R), _ptr(Cc))
+    return vs, R, Cc, passes
+
+
+def power_norm(lp, iters=100, vals=None):
+    """Algorithm 2."""
+    b = _Bound(lp, vals)
+    return float(_load().orc_power_norm(C.byref(b.st), _ptr(b.v), iters))
+
+
+def proj_lambda(l, u, v):
+    l, u, v = _f64(l), _f64(u), _f64(v)
+    out = np.empty_like(v)
+    _load().orc_proj_lambda(v.shape[0], _ptr(l), _ptr(u), _ptr(v), _ptr(out))
+    return out
+
+
+KKT_FIELDS = ("pobj", "dobj", "pres", "dres", "rel_gap", "rel_pres", "rel_dres", "kkt_omega")
+
+
+def kkt(lp, x, y, omega=1.0, vals=None, c=None, q=None, l=None, u=None):
+    """Termination quantities (Section 2.3.2) and KKT_omega (Section 2.4.2)."""
+    b = _Bound(lp, vals, c, q, l, u)
+    x, y = _f64(x), _f64(y)
+    out = np.empty(8)
+    _load().orc_kkt(C.byref(b.st), _ptr(b.v), _ptr(b.c), _ptr(b.q), _ptr(b.l), _ptr(b.u),
+                    _ptr(x), _ptr(y), omega, _ptr(out))
+    return dict(zip(KKT_FIELDS, out.tolist()))
+
+
+def pdhg_step(lp, x, y, tau, sigma, vals=None, c=None, q=None, l=None, u=None):
+    """One step of Algorithm 1 (theta = 1)."""
+    b = _Bound(lp, vals, c, q, l, u)
+    x, y = _f64(x), _f64(y)
+    xn = np.empty(lp.n)
+    yn = np.empty(lp.m)
+    _load().orc_pdhg_step(C.byref(b.st), _ptr(b.v), _ptr(b.c), _ptr(b.q), _ptr(b.l),
+                          _ptr(b.u), _ptr(x), _ptr(y), tau, sigma, _ptr(xn), _ptr(yn))
+    return xn, yn
+
+
+def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
+    """Restarted PDHG.  Returns (x, y, info dict, trace list of dicts)."""
+    o = dict(DEFAULTS)
+    o.update(kw)
+    b = _Bound(lp)
+    x0a = None if x0 is None else _f64(x0)
+    y0a = None if y0 is None else _f64(y0)
+    opts = _Opts(o["tol"], int(o["max_iters"]), int(o["check_every"]), int(o["ruiz_iters"]),
+                 o["ruiz_tol"], int(o["pock_chambolle"]), int(o["power_iters"]),
+                 int(o["adaptive_step"]), int(o["primal_weight_update"]), int(o["restarts"]),
+                 o["eta_scale"], o["beta_sufficient"], o["beta_necessary"],
+                 o["beta_artificial"], o["eps_zero"],
+                 None if x0a is None else _ptr(x0a), None if y0a is None else _ptr(y0a),
+                 o["omega0"], o["eta0"])
+    x = np.empty(lp.n)
+    y = np.empty(lp.m)
+    info = _Info()
+    tr = np.zeros((trace_cap, len(TRACE_FIELDS)))
+    tl = C.c_int64(0)
+    _load().orc_solve(C.byref(b.st), C.byref(opts), _ptr(x), _ptr(y), C.byref(info),
+                      _ptr(tr), trace_cap, C.byref(tl))
+    d = {f: getattr(info, f) for f, _ in _Info._fields_ if f != "pad"}
+    trace = [dict(zip(TRACE_FIELDS, r.tolist())) for r in tr[: min(tl.value, trace_cap)]]
+    return x, y, d, trace
+
+
+def start_point(lp):
+    """Unscaled default start: x = proj_X(0), y = 0."""
+    return np.clip(np.zeros(lp.n), lp.l, lp.u), np.zeros(lp.m)
+
+
+def unrolled_forward(lp, tau, sigma, K_iters, x0=None, y0=None):
+    """Iterates 0..K_iters of fixed-step PDHG on the unscaled problem."""
+    b = _Bound(lp)
+    if x0 is None:
+        x0, y0 = start_point(lp)
+    x0, y0 = _f64(x0), _f64(y0)
+    xs = np.empty((K_iters + 1, lp.n))
+    ys = np.empty((K_iters + 1, lp.m))
+    _load().orc_unrolled_forward(C.byref(b.st), tau, sigma, K_iters, _ptr(x0), _ptr(y0),
+                                 _ptr(xs), _ptr(ys))
+    return xs, ys
+
+
+def unrolled_adjoint(lp, tau, sigma, K_iters, gxK, x0=None, y0=None):
+    """Gradient of L(x_K) w.r.t. (c, q, nonzeros of K) given dL/dx_K."""
+    b = _Bound(lp)
+    if x0 is None:
+        x0, y0 = start_point(lp)
+    x0, y0, g = _f64(x0), _f64(y0), _f64(gxK)
+    dc = np.empty(lp.n)
+    dq = np.empty(lp.m)
+    dv = np.empty(lp.nnz)
+    _load().orc_unrolled_adjoint(C.byref(b.st), tau, sigma, K_iters, _ptr(x0), _ptr(y0),
+                                 _ptr(g), _ptr(dc), _ptr(dq), _ptr(dv))
+    return dc, dq, dv

@@ -1,0 +1,634 @@
+/*
+ * FP64 single-threaded CPU oracle of restarted PDHG for linear programming.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark call this code.  It shares nothing with the CUDA
+ * solver: no headers, helpers, tables or kernels.  It is deliberately plain and
+ * slow: explicit loops over the CSR matrix, no blocking, no fusion, no
+ * reordering beyond what the paper's formulas state.
+ *
+ * Problem (Section 2.2):  min c^T x  s.t.  G x >= h,  A x = b,  l <= x <= u.
+ * K = (G; A) is given row-wise in CSR with a per-row sense flag
+ * (sense[i] = 1: row of G, K_i x >= q_i;  sense[i] = 0: row of A, K_i x = q_i),
+ * q = (h; b).  Bounds may be +-INFINITY.
+ *
+ * Function map (paper sections, algorithms, equations):
+ *   orc_spmv / orc_spmv_t     products K x and K^T y
+ *   orc_ruiz                  Algorithm 3 (Ruiz), Section 2.4.1 change of variables,
+ *                             optional Pock-Chambolle pass (alpha = 1)
+ *   orc_power_norm            Algorithm 2 (spectral norm estimate)
+ *   orc_proj_lambda           projection onto Lambda (Section 2.2 dual)
+ *   orc_kkt                   termination quantities, Eqs. (term1)-(term3) of
+ *                             Section 2.3.2, and the KKT_omega error of Section 2.4.2
+ *   orc_pdhg_step             one PDHG step, Algorithm 1 with theta = 1 in the sign
+ *                             form of Appendix D (c - K^T y, q - K xbar)
+ *   orc_solve                 Algorithm 1 + restarts (Section 2.4.2), primal weight
+ *                             (Section 2.4.3, Algorithm 4), adaptive step
+ *                             (Algorithm 5), termination (Section 2.3.2)
+ *   orc_unrolled_forward /
+ *   orc_unrolled_adjoint      K fixed-step iterations and their exact reverse-mode
+ *                             derivative (the paper names autodiff only; the reverse
+ *                             equations follow from Appendix D's step by the chain rule)
+ *
+ * Readings where the paper is silent or garbled are marked "reading:".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int64_t m, n;
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    const double* vals;
+    const uint8_t* sense;
+    const double* c;
+    const double* q;
+    const double* l;
+    const double* u;
+} orc_lp;
+
+typedef struct {
+    double tol;               /* epsilon of Section 2.3.2 */
+    int64_t max_iters;        /* accepted PDHG iterations */
+    int32_t check_every;      /* reading: the paper's "a set number" of iterations */
+    int32_t ruiz_iters;       /* N_iter of Algorithm 3 (0 = no scaling) */
+    double ruiz_tol;          /* "converged to 1 within tolerance" */
+    int32_t pock_chambolle;   /* reading: one alpha = 1 pass after Ruiz */
+    int32_t power_iters;      /* N_iter of Algorithm 2 */
+    int32_t adaptive_step;    /* Algorithm 5 on/off */
+    int32_t primal_weight_update; /* Algorithm 4 on/off */
+    int32_t restarts;         /* Section 2.4.2 on/off */
+    double eta_scale;         /* eta = eta_scale / ||K||_2 (0.9, Section 3.2) */
+    double beta_sufficient, beta_necessary, beta_artificial;
+    double eps_zero;          /* 1e-6 */
+    const double* x0;         /* optional warm start, unscaled (NULL: x = proj_X(0)) */
+    const double* y0;         /* optional warm start, unscaled (NULL: y = 0) */
+    double omega0;            /* > 0: use instead of InitializePrimalWeight */
+    double eta0;              /* > 0: use instead of eta_scale / ||K||_2 */
+} orc_opts;
+
+typedef struct {
+    int32_t status;           /* 1 optimal, 4 iteration limit */
+    int32_t pad;
+    int64_t iters;            /* accepted iterations */
+    int64_t attempts;         /* step attempts (accepted + rejected) */
+    int64_t restarts;
+    double pobj, dobj, rel_gap, rel_pres, rel_dres;
+    double omega, eta, norm_K;
+} orc_info;
+
+/* One record per termination / restart check. */
+typedef struct {
+    double k, attempts, restart, cand_is_avg, omega, eta;
+    double kkt_cur, kkt_avg, rel_gap, rel_pres, rel_dres, kkt_cand;
+} orc_trace;
+
+/* ------------------------------------------------------------------ */
+/* basic linear algebra                                                */
+/* ------------------------------------------------------------------ */
+
+/* out = K x  (row-wise CSR product) */
+void orc_spmv(const orc_lp* lp, const double* vals, const double* x, double* out)
+{
+    for (int64_t i = 0; i < lp->m; ++i) {
+        double s = 0.0;
+        for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p)
+            s += vals[p] * x[lp->col_idx[p]];
+        out[i] = s;
+    }
+}
+
+/* out = K^T y  (scatter over the rows of K; no transposed copy) */
+void orc_spmv_t(const orc_lp* lp, const double* vals, const double* y, double* out)
+{
+    for (int64_t j = 0; j < lp->n; ++j) out[j] = 0.0;
+    for (int64_t i = 0; i < lp->m; ++i)
+        for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p)
+            out[lp->col_idx[p]] += vals[p] * y[i];
+}
+
+static double dot(int64_t n, const double* a, const double* b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+static double nrm2(int64_t n, const double* a) { return sqrt(dot(n, a, a)); }
+
+static double clamp(double v, double lo, double hi)
+{
+    if (v < lo) return lo;
+    if (v > hi) return hi;
+    return v;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 3: Ruiz scaling (+ optional Pock-Chambolle pass)          */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Produces the scaled matrix vals_s and the accumulated diagonal factors
+ * R (length m) and C (length n) with  K~ = diag(R) K diag(C).
+ * In the paper's notation D_r = diag(R)^-1 and D_c = diag(C)^-1, so that
+ * K~ = D_r^-1 K D_c^-1, x~ = D_c x = x / C, c~ = D_c^-1 c = C c, q~ = R q
+ * (Section 2.4.1); bounds follow x: l~ = l / C, u~ = u / C.
+ *
+ * Each pass takes both factor sets from the current K~ (row and column
+ * infinity norms), then rescales.  reading: the loop stops before a pass when
+ * every non-empty row's and column's infinity norm is within ruiz_tol of 1
+ * (the same set of passes as testing after each update); an empty row or
+ * column keeps factor 1.  Returns the number of passes applied.
+ */
+int orc_ruiz(const orc_lp* lp, int32_t iters, double tol, int32_t pock_chambolle,
+             double* vals_s, double* R, double* C)
+{
+    const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
+    double* rn = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double* cn = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    memcpy(vals_s, lp->vals, sizeof(double) * (size_t)nnz);
+    for (int64_t i = 0; i < m; ++i) R[i] = 1.0;
+    for (int64_t j = 0; j < n; ++j) C[j] = 1.0;
+    int passes = 0;
+    for (int32_t it = 0; it < iters; ++it) {
+        for (int64_t i = 0; i < m; ++i) rn[i] = 0.0;
+        for (int64_t j = 0; j < n; ++j) cn[j] = 0.0;
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p) {
+                double a = fabs(vals_s[p]);
+                if (a > rn[i]) rn[i] = a;
+                if (a > cn[lp->col_idx[p]]) cn[lp->col_idx[p]] = a;
+            }
+        double dev = 0.0;
+        for (int64_t i = 0; i < m; ++i)
+            if (rn[i] > 0.0 && fabs(1.0 - rn[i]) > dev) dev = fabs(1.0 - rn[i]);
+        for (int64_t j = 0; j < n; ++j)
+            if (cn[j] > 0.0 && fabs(1.0 - cn[j]) > dev) dev = fabs(1.0 - cn[j]);
+        if (dev <= tol) break;
+        for (int64_t i = 0; i < m; ++i) rn[i] = rn[i] > 0.0 ? 1.0 / sqrt(rn[i]) : 1.0;
+        for (int64_t j = 0; j < n; ++j) cn[j] = cn[j] > 0.0 ? 1.0 / sqrt(cn[j]) : 1.0;
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p)
+                vals_s[p] = vals_s[p] * rn[i] * cn[lp->col_idx[p]];
+        for (int64_t i = 0; i < m; ++i) R[i] *= rn[i];
+        for (int64_t j = 0; j < n; ++j) C[j] *= cn[j];
+        ++passes;
+    }
+    if (pock_chambolle) {
+        /* reading: alpha = 1, rows by 1/sqrt(sum_j |K~_ij|), columns by 1/sqrt(sum_i |K~_ij|) */
+        for (int64_t i = 0; i < m; ++i) rn[i] = 0.0;
+        for (int64_t j = 0; j < n; ++j) cn[j] = 0.0;
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p) {
+                rn[i] += fabs(vals_s[p]);
+                cn[lp->col_idx[p]] += fabs(vals_s[p]);
+            }
+        for (int64_t i = 0; i < m; ++i) rn[i] = rn[i] > 0.0 ? 1.0 / sqrt(rn[i]) : 1.0;
+        for (int64_t j = 0; j < n; ++j) cn[j] = cn[j] > 0.0 ? 1.0 / sqrt(cn[j]) : 1.0;
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p)
+                vals_s[p] = vals_s[p] * rn[i] * cn[lp->col_idx[p]];
+        for (int64_t i = 0; i < m; ++i) R[i] *= rn[i];
+        for (int64_t j = 0; j < n; ++j) C[j] *= cn[j];
+    }
+    free(rn);
+    free(cn);
+    return passes;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2: spectral norm by power iteration                       */
+/* ------------------------------------------------------------------ */
+
+double orc_power_norm(const orc_lp* lp, const double* vals, int32_t iters)
+{
+    const int64_t m = lp->m, n = lp->n;
+    double* b = (double*)malloc(sizeof(double) * (size_t)n);
+    double* t = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < n; ++j) b[j] = 1.0;
+    for (int32_t it = 0; it < iters; ++it) {
+        orc_spmv(lp, vals, b, t);
+        orc_spmv_t(lp, vals, t, b);
+        double nb = nrm2(n, b);
+        if (nb == 0.0) break;
+        for (int64_t j = 0; j < n; ++j) b[j] /= nb;
+    }
+    orc_spmv(lp, vals, b, t);
+    double r = nrm2(m, t);
+    free(b);
+    free(t);
+    return r;
+}
+
+/* ------------------------------------------------------------------ */
+/* dual multipliers and the KKT quantities (Sections 2.2, 2.3.2, 2.4.2) */
+/* ------------------------------------------------------------------ */
+
+/* lambda = proj_Lambda(v): Lambda_i = {0} (free), R^- (only u finite),
+ * R^+ (only l finite), R (both finite). */
+void orc_proj_lambda(int64_t n, const double* l, const double* u, const double* v,
+                     double* lam)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        int lf = isfinite(l[j]), uf = isfinite(u[j]);
+        if (!lf && !uf) lam[j] = 0.0;
+        else if (!lf) lam[j] = v[j] < 0.0 ? v[j] : 0.0;
+        else if (!uf) lam[j] = v[j] > 0.0 ? v[j] : 0.0;
+        else lam[j] = v[j];
+    }
+}
+
+/*
+ * KKT quantities of (x, y) for the LP with matrix values ``vals`` and vectors
+ * c, q, l, u (scaled or not, whichever the caller passes).
+ * out[0] pobj = c^T x
+ * out[1] dobj = q^T y + l^T lambda^+ + u^T lambda^-   (a term is 0 when its
+ *        lambda part is 0: reading of 0 * inf for infinite bounds)
+ * out[2] ||(Ax - b, [h - Gx]^+)||_2   primal residual norm
+ * out[3] ||c - K^T y - lambda||_2     dual residual norm
+ * out[4] rel_gap   (term1)  |dobj - pobj| / (1 + |dobj| + |pobj|)
+ * out[5] rel_pres  (term2)  out[2] / (1 + ||q||_2)
+ * out[6] rel_dres  (term3)  out[3] / (1 + ||c||_2)
+ * out[7] KKT_omega (Section 2.4.2) = sqrt(w^2 out[2]^2 + out[3]^2 / w^2 + (dobj - pobj)^2)
+ */
+void orc_kkt(const orc_lp* lp, const double* vals, const double* c, const double* q,
+             const double* l, const double* u, const double* x, const double* y,
+             double omega, double* out)
+{
+    const int64_t m = lp->m, n = lp->n;
+    double* Kx = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double* v = (double*)malloc(sizeof(double) * (size_t)n);
+    double* lam = (double*)malloc(sizeof(double) * (size_t)n);
+    orc_spmv(lp, vals, x, Kx);
+    double pres2 = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double r = q[i] - Kx[i];             /* h - Gx or b - Ax */
+        if (lp->sense[i]) r = r > 0.0 ? r : 0.0;  /* [h - Gx]^+ */
+        pres2 += r * r;
+    }
+    orc_spmv_t(lp, vals, y, v);
+    for (int64_t j = 0; j < n; ++j) v[j] = c[j] - v[j];   /* c - K^T y */
+    orc_proj_lambda(n, l, u, v, lam);
+    double dres2 = 0.0, lterm = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double r = v[j] - lam[j];
+        dres2 += r * r;
+        if (lam[j] > 0.0) lterm += l[j] * lam[j];
+        if (lam[j] < 0.0) lterm += u[j] * lam[j];
+    }
+    double pobj = dot(n, c, x);
+    double dobj = dot(m, q, y) + lterm;
+    double gap = dobj - pobj;
+    out[0] = pobj;
+    out[1] = dobj;
+    out[2] = sqrt(pres2);
+    out[3] = sqrt(dres2);
+    out[4] = fabs(gap) / (1.0 + fabs(dobj) + fabs(pobj));
+    out[5] = out[2] / (1.0 + nrm2(m, q));
+    out[6] = out[3] / (1.0 + nrm2(n, c));
+    out[7] = sqrt(omega * omega * pres2 + dres2 / (omega * omega) + gap * gap);
+    free(Kx);
+    free(v);
+    free(lam);
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1 (theta = 1), sign form of Appendix D                    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * x' = proj_X(x - tau (c - K^T y))
+ * y' = proj_Y(y + sigma (q - K (2 x' - x)))
+ * proj_X clamps to [l, u]; proj_Y clamps inequality rows at 0 (Appendix C).
+ */
+void orc_pdhg_step(const orc_lp* lp, const double* vals, const double* c, const double* q,
+                   const double* l, const double* u, const double* x, const double* y,
+                   double tau, double sigma, double* xn, double* yn)
+{
+    const int64_t m = lp->m, n = lp->n;
+    double* KTy = (double*)malloc(sizeof(double) * (size_t)n);
+    double* xbar = (double*)malloc(sizeof(double) * (size_t)n);
+    double* Kxb = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    orc_spmv_t(lp, vals, y, KTy);
+    for (int64_t j = 0; j < n; ++j) {
+        xn[j] = clamp(x[j] - tau * (c[j] - KTy[j]), l[j], u[j]);
+        xbar[j] = 2.0 * xn[j] - x[j];
+    }
+    orc_spmv(lp, vals, xbar, Kxb);
+    for (int64_t i = 0; i < m; ++i) {
+        double v = y[i] + sigma * (q[i] - Kxb[i]);
+        if (lp->sense[i] && v < 0.0) v = 0.0;
+        yn[i] = v;
+    }
+    free(KTy);
+    free(xbar);
+    free(Kxb);
+}
+
+/* ------------------------------------------------------------------ */
+/* the restarted, adaptive solver                                      */
+/* ------------------------------------------------------------------ */
+
+static void* xalloc(int64_t count) { return calloc((size_t)(count > 0 ? count : 1), sizeof(double)); }
+
+/*
+ * Restarted PDHG.  Returns the status (1 optimal, 4 iteration limit) and
+ * writes the unscaled candidate solution to x_out, y_out.
+ *
+ * Steps, in the paper's order:
+ *  1. Ruiz (Algorithm 3) -> K~, c~, q~, l~, u~.
+ *  2. ||K~||_2 by Algorithm 2; eta = 0.9 / ||K~||_2 (Section 3.2);
+ *     reading: eta = 1 when K~ = 0.
+ *  3. omega = ||c~|| / ||q~|| if both exceed eps_zero, else 1 (Section 2.4.3).
+ *  4. Start (reading): x = proj_X(0), y = 0; the restart anchor is the start.
+ *  5. Each iteration takes a step of Algorithm 1 (fixed eta), or of Algorithm 5
+ *     (adaptive eta; reading: its k is the 1-based index of the iteration being
+ *     taken, i.e. accepted iterations so far + 1).  Accepted iterates enter the
+ *     eta-weighted averages (Section 2.4.2).
+ *  6. At the start and every check_every accepted iterations (and at max_iters):
+ *     KKT_omega of the current point and of the average on the scaled problem
+ *     (reading); candidate = current if strictly better, else average;
+ *     termination (Section 2.3.2) on the unscaled candidate: all three
+ *     relative errors <= tol; then the three restart criteria; at a restart the
+ *     iterate becomes the candidate, omega is updated by Algorithm 4 (reading:
+ *     ratio Delta_y / Delta_x, smoothing 1/2) and the averages are reset.
+ */
+int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
+              orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len)
+{
+    const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
+    double* vs = (double*)xalloc(nnz);
+    double* R = (double*)xalloc(m);
+    double* C = (double*)xalloc(n);
+    double *cs = (double*)xalloc(n), *qs = (double*)xalloc(m);
+    double *ls = (double*)xalloc(n), *us = (double*)xalloc(n);
+    double *x = (double*)xalloc(n), *y = (double*)xalloc(m);
+    double *xn = (double*)xalloc(n), *yn = (double*)xalloc(m);
+    double *xsum = (double*)xalloc(n), *ysum = (double*)xalloc(m);
+    double *xa = (double*)xalloc(n), *ya = (double*)xalloc(m);
+    double *xanc = (double*)xalloc(n), *yanc = (double*)xalloc(m);
+    double *dx = (double*)xalloc(n), *Kdx = (double*)xalloc(m);
+    double *xu = (double*)xalloc(n), *yu = (double*)xalloc(m);
+    double kc[8], ka[8], kk[8];
+    int64_t tl = 0;
+
+    /* 1. preconditioning */
+    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, vs, R, C);
+    for (int64_t j = 0; j < n; ++j) {
+        cs[j] = C[j] * lp->c[j];
+        ls[j] = lp->l[j] / C[j];
+        us[j] = lp->u[j] / C[j];
+    }
+    for (int64_t i = 0; i < m; ++i) qs[i] = R[i] * lp->q[i];
+
+    /* 2. step size */
+    double normK = orc_power_norm(lp, vs, o->power_iters);
+    double eta = normK > 0.0 ? o->eta_scale / normK : 1.0;
+    if (o->eta0 > 0.0) eta = o->eta0;
+
+    /* 3. primal weight */
+    double nc = nrm2(n, cs), nq = nrm2(m, qs);
+    double omega = (nc > o->eps_zero && nq > o->eps_zero) ? nc / nq : 1.0;
+    if (o->omega0 > 0.0) omega = o->omega0;
+
+    /* 4. start */
+    for (int64_t j = 0; j < n; ++j) {
+        double x0 = o->x0 ? o->x0[j] / C[j] : 0.0;
+        x[j] = clamp(x0, ls[j], us[j]);
+    }
+    for (int64_t i = 0; i < m; ++i) {
+        double y0 = o->y0 ? o->y0[i] / R[i] : 0.0;
+        if (lp->sense[i] && y0 < 0.0) y0 = 0.0;
+        y[i] = y0;
+    }
+    memcpy(xanc, x, sizeof(double) * (size_t)n);
+    memcpy(yanc, y, sizeof(double) * (size_t)m);
+    double wsum = 0.0;
+    double kkt_anchor = 0.0, kkt_prev = INFINITY;
+    int64_t k = 0, attempts = 0, epoch_k = 0, nrestarts = 0;
+    int status = 0;
+    int first = 1;
+    double rel[3] = {0, 0, 0}, pobj = 0, dobj = 0;
+
+    for (;;) {
+        int do_check = first || (k % o->check_every == 0) || (k >= o->max_iters);
+        if (do_check) {
+            /* 6. KKT of current and average on the scaled problem */
+            orc_kkt(lp, vs, cs, qs, ls, us, x, y, omega, kc);
+            double kkt_avg = INFINITY;
+            if (wsum > 0.0) {
+                for (int64_t j = 0; j < n; ++j) xa[j] = xsum[j] / wsum;
+                for (int64_t i = 0; i < m; ++i) ya[i] = ysum[i] / wsum;
+                orc_kkt(lp, vs, cs, qs, ls, us, xa, ya, omega, ka);
+                kkt_avg = ka[7];
+            }
+            int cand_avg = !(kc[7] < kkt_avg);
+            const double* xc = cand_avg ? xa : x;
+            const double* yc = cand_avg ? ya : y;
+            double kkt_c = cand_avg ? kkt_avg : kc[7];
+            /* termination on the unscaled candidate (Section 2.3.2) */
+            for (int64_t j = 0; j < n; ++j) xu[j] = C[j] * xc[j];
+            for (int64_t i = 0; i < m; ++i) yu[i] = R[i] * yc[i];
+            orc_kkt(lp, lp->vals, lp->c, lp->q, lp->l, lp->u, xu, yu, omega, kk);
+            rel[0] = kk[4]; rel[1] = kk[5]; rel[2] = kk[6];
+            pobj = kk[0]; dobj = kk[1];
+            int converged = rel[0] <= o->tol && rel[1] <= o->tol && rel[2] <= o->tol;
+            int restart = 0;
+            if (first) {
+                kkt_anchor = kkt_c;
+            } else if (!converged && o->restarts) {
+                int crit1 = kkt_c <= o->beta_sufficient * kkt_anchor;
+                int crit2 = kkt_c <= o->beta_necessary * kkt_anchor && kkt_c > kkt_prev;
+                int crit3 = (double)epoch_k > o->beta_artificial * (double)k;
+                restart = crit1 || crit2 || crit3;
+            }
+            if (restart) {
+                if (cand_avg) {
+                    memcpy(x, xa, sizeof(double) * (size_t)n);
+                    memcpy(y, ya, sizeof(double) * (size_t)m);
+                }
+                if (o->primal_weight_update) {
+                    /* Algorithm 4 */
+                    double ddx = 0.0, ddy = 0.0;
+                    for (int64_t j = 0; j < n; ++j) ddx += (x[j] - xanc[j]) * (x[j] - xanc[j]);
+                    for (int64_t i = 0; i < m; ++i) ddy += (y[i] - yanc[i]) * (y[i] - yanc[i]);
+                    ddx = sqrt(ddx);
+                    ddy = sqrt(ddy);
+                    if (ddx > o->eps_zero && ddy > o->eps_zero)
+                        omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(omega));
+                }
+                memcpy(xanc, x, sizeof(double) * (size_t)n);
+                memcpy(yanc, y, sizeof(double) * (size_t)m);
+                kkt_anchor = kkt_c;
+                kkt_prev = INFINITY;
+                epoch_k = 0;
+                wsum = 0.0;
+                memset(xsum, 0, sizeof(double) * (size_t)n);
+                memset(ysum, 0, sizeof(double) * (size_t)m);
+                ++nrestarts;
+            } else if (!first) {
+                kkt_prev = kkt_c;
+            }
+            if (trace && tl < trace_cap) {
+                orc_trace* t = &trace[tl];
+                t->k = (double)k; t->attempts = (double)attempts; t->restart = restart;
+                t->cand_is_avg = cand_avg; t->omega = omega; t->eta = eta;
+                t->kkt_cur = kc[7]; t->kkt_avg = kkt_avg;
+                t->rel_gap = rel[0]; t->rel_pres = rel[1]; t->rel_dres = rel[2];
+                t->kkt_cand = kkt_c;
+            }
+            ++tl;
+            if (converged || k >= o->max_iters) {
+                memcpy(x_out, xu, sizeof(double) * (size_t)n);
+                memcpy(y_out, yu, sizeof(double) * (size_t)m);
+                status = converged ? 1 : 4;
+                break;
+            }
+            first = 0;
+        }
+
+        /* 5. one accepted iteration */
+        double used = eta;   /* the eta the accepted step was taken with */
+        for (;;) {
+            double tau = eta / omega, sigma = eta * omega;
+            orc_pdhg_step(lp, vs, cs, qs, ls, us, x, y, tau, sigma, xn, yn);
+            ++attempts;
+            used = eta;
+            if (!o->adaptive_step) break;
+            /* Algorithm 5 */
+            double dx2 = 0.0, dy2 = 0.0;
+            for (int64_t j = 0; j < n; ++j) { dx[j] = xn[j] - x[j]; dx2 += dx[j] * dx[j]; }
+            orc_spmv(lp, vs, dx, Kdx);
+            double inter = 0.0;
+            for (int64_t i = 0; i < m; ++i) {
+                double d = yn[i] - y[i];
+                dy2 += d * d;
+                inter += d * Kdx[i];
+            }
+            double movement = omega * dx2 + dy2 / omega;   /* ||(dx, dy)||_omega^2 */
+            double eta_bar = inter != 0.0 ? movement / (2.0 * fabs(inter)) : INFINITY;
+            double kp1 = (double)(k + 1) + 1.0;            /* the paper's (k + 1), k 1-based */
+            double e1 = (1.0 - pow(kp1, -0.3)) * eta_bar;
+            double e2 = (1.0 + pow(kp1, -0.6)) * eta;
+            double eta_next = e1 < e2 ? e1 : e2;
+            int accept = eta <= eta_bar;
+            eta = eta_next;            /* eta' is used by the next attempt either way */
+            if (accept) break;
+        }
+        /* eta-weighted averages of the accepted iterates (Section 2.4.2) */
+        for (int64_t j = 0; j < n; ++j) xsum[j] += used * xn[j];
+        for (int64_t i = 0; i < m; ++i) ysum[i] += used * yn[i];
+        wsum += used;
+        memcpy(x, xn, sizeof(double) * (size_t)n);
+        memcpy(y, yn, sizeof(double) * (size_t)m);
+        ++k;
+        ++epoch_k;
+    }
+
+    if (info) {
+        info->status = status;
+        info->iters = k;
+        info->attempts = attempts;
+        info->restarts = nrestarts;
+        info->pobj = pobj; info->dobj = dobj;
+        info->rel_gap = rel[0]; info->rel_pres = rel[1]; info->rel_dres = rel[2];
+        info->omega = omega; info->eta = eta; info->norm_K = normK;
+    }
+    if (trace_len) *trace_len = tl;
+    free(vs); free(R); free(C); free(cs); free(qs); free(ls); free(us);
+    free(x); free(y); free(xn); free(yn); free(xsum); free(ysum); free(xa); free(ya);
+    free(xanc); free(yanc); free(dx); free(Kdx); free(xu); free(yu);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* unrolled fixed-step PDHG and its reverse-mode derivative            */
+/* ------------------------------------------------------------------ */
+
+/*
+ * K_iters fixed-step iterations on the unscaled problem from (x0, y0):
+ * xs[t*n ..], ys[t*m ..] hold iterate t = 0..K_iters (caller sizes them).
+ */
+void orc_unrolled_forward(const orc_lp* lp, double tau, double sigma, int32_t K_iters,
+                          const double* x0, const double* y0, double* xs, double* ys)
+{
+    const int64_t m = lp->m, n = lp->n;
+    memcpy(xs, x0, sizeof(double) * (size_t)n);
+    memcpy(ys, y0, sizeof(double) * (size_t)m);
+    for (int32_t t = 0; t < K_iters; ++t)
+        orc_pdhg_step(lp, lp->vals, lp->c, lp->q, lp->l, lp->u,
+                      xs + (int64_t)t * n, ys + (int64_t)t * m, tau, sigma,
+                      xs + (int64_t)(t + 1) * n, ys + (int64_t)(t + 1) * m);
+}
+
+/*
+ * Gradient of L(x_K) with respect to c, q and the nonzeros of K, given
+ * gxK = dL/dx_K, with tau and sigma held constant.  For one step
+ *   v_x = x - tau (c - K^T y),  x' = clamp(v_x, l, u),  xbar = 2 x' - x,
+ *   v_y = y + sigma (q - K xbar), y' = proj_Y(v_y),
+ * the chain rule gives, for incoming adjoints (gx', gy'):
+ *   gv_y = M_y * gy'      M_y = 1 on equality rows or where v_y > 0
+ *   gq  += sigma gv_y;    gxbar = -sigma K^T gv_y;   gK_ij += -sigma gv_y_i xbar_j
+ *   gv_x = M_x * (gx' + 2 gxbar)   M_x = 1 where l < v_x < u (strict interior)
+ *   gc  += -tau gv_x;     gK_ij += tau y_i gv_x_j
+ *   gx   = gv_x - gxbar;  gy = gv_y + tau K gv_x
+ * dc, dq, dvals are overwritten.
+ */
+void orc_unrolled_adjoint(const orc_lp* lp, double tau, double sigma, int32_t K_iters,
+                          const double* x0, const double* y0, const double* gxK,
+                          double* dc, double* dq, double* dvals)
+{
+    const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
+    double* xs = (double*)xalloc((int64_t)(K_iters + 1) * n);
+    double* ys = (double*)xalloc((int64_t)(K_iters + 1) * m);
+    orc_unrolled_forward(lp, tau, sigma, K_iters, x0, y0, xs, ys);
+    double *gx = (double*)xalloc(n), *gy = (double*)xalloc(m);
+    double *KTy = (double*)xalloc(n), *vx = (double*)xalloc(n), *xbar = (double*)xalloc(n);
+    double *Kxb = (double*)xalloc(m), *gvy = (double*)xalloc(m), *gxbar = (double*)xalloc(n);
+    double *gvx = (double*)xalloc(n), *Kgvx = (double*)xalloc(m);
+    memcpy(gx, gxK, sizeof(double) * (size_t)n);
+    for (int64_t i = 0; i < m; ++i) gy[i] = 0.0;
+    for (int64_t j = 0; j < n; ++j) dc[j] = 0.0;
+    for (int64_t i = 0; i < m; ++i) dq[i] = 0.0;
+    for (int64_t p = 0; p < nnz; ++p) dvals[p] = 0.0;
+    for (int32_t t = K_iters - 1; t >= 0; --t) {
+        const double* x = xs + (int64_t)t * n;
+        const double* y = ys + (int64_t)t * m;
+        const double* xn = xs + (int64_t)(t + 1) * n;
+        /* recompute the step's intermediates */
+        orc_spmv_t(lp, lp->vals, y, KTy);
+        for (int64_t j = 0; j < n; ++j) {
+            vx[j] = x[j] - tau * (lp->c[j] - KTy[j]);
+            xbar[j] = 2.0 * xn[j] - x[j];
+        }
+        orc_spmv(lp, lp->vals, xbar, Kxb);
+        /* dual half */
+        for (int64_t i = 0; i < m; ++i) {
+            double vy = y[i] + sigma * (lp->q[i] - Kxb[i]);
+            int my = !lp->sense[i] || vy > 0.0;
+            gvy[i] = my ? gy[i] : 0.0;
+            dq[i] += sigma * gvy[i];
+        }
+        orc_spmv_t(lp, lp->vals, gvy, gxbar);
+        for (int64_t j = 0; j < n; ++j) gxbar[j] *= -sigma;
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p)
+                dvals[p] += -sigma * gvy[i] * xbar[lp->col_idx[p]];
+        /* primal half */
+        for (int64_t j = 0; j < n; ++j) {
+            int mx = lp->l[j] < vx[j] && vx[j] < lp->u[j];
+            gvx[j] = mx ? gx[j] + 2.0 * gxbar[j] : 0.0;
+            dc[j] += -tau * gvx[j];
+        }
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p)
+                dvals[p] += tau * y[i] * gvx[lp->col_idx[p]];
+        orc_spmv(lp, lp->vals, gvx, Kgvx);
+        for (int64_t j = 0; j < n; ++j) gx[j] = gvx[j] - gxbar[j];
+        for (int64_t i = 0; i < m; ++i) gy[i] = gvy[i] + tau * Kgvx[i];
+    }
+    free(xs); free(ys); free(gx); free(gy); free(KTy); free(vx); free(xbar);
+    free(Kxb); free(gvy); free(gxbar); free(gvx); free(Kgvx);
+}
