@@ -1,0 +1,219 @@
+/*
+ * lp.h -- C ABI of the GB300 restarted-PDHG linear-programming solver.
+ *
+ * Problem (the paper's Section 2.2 primal form):
+ *
+ *     min  c^T x   s.t.  G x >= h,  A x = b,  l <= x <= u,
+ *
+ * given as one CSR matrix K = (G; A) whose rows may come in any order, with a
+ * per-row sense flag: sense[i] = 1 marks a row of G (K_i x >= q_i), sense[i] = 0
+ * a row of A (K_i x == q_i); q stacks h and b the same way.  A <= row is passed
+ * negated.  Bounds may be -INFINITY / +INFINITY (IEEE).  The dual (Section 2.2)
+ * is  max q^T y + l^T lambda^+ + u^T lambda^-  with lambda = c - K^T y in Lambda
+ * and y >= 0 on the rows of G.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns lp_status.  Negative values are API or device failures;
+ *     non-negative values are solver outcomes.  Nothing aborts, prints or traps.
+ *   - Pointers are host or device memory as the accompanying memory_space field
+ *     says (LP_MEM_HOST / LP_MEM_DEVICE).  Device pointers must belong to the
+ *     current CUDA device.
+ *   - lp_create deep-copies its inputs; the handle owns all device memory it
+ *     allocates and releases it in lp_destroy.  The caller owns every input and
+ *     every result buffer.
+ *   - All work of a handle runs on the CUDA stream given to lp_create (or a
+ *     private stream if that is NULL).  lp_solve / lp_solve_batch / lp_grad
+ *     return after that stream has finished the call's work.
+ *   - A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef GB300_PDHG_LP_H
+#define GB300_PDHG_LP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LP_ABI_VERSION 1
+
+typedef struct lp_problem_s* lp_handle;
+
+typedef enum {
+    LP_OK = 0,
+    LP_OPTIMAL = 1,              /* all three relative errors of Section 2.3.2 <= tol */
+    LP_PRIMAL_INFEASIBLE = 2,    /* reserved: certificate of Section 2.4.5 */
+    LP_DUAL_INFEASIBLE = 3,      /* reserved: certificate of Section 2.4.5 */
+    LP_ITERATION_LIMIT = 4,
+    LP_TIME_LIMIT = 5,
+    LP_NUMERICAL_ERROR = 6,      /* NaN / Inf met in an iterate or a reduction */
+    LP_INVALID_ARGUMENT = -1,
+    LP_CUDA_ERROR = -2,
+    LP_OUT_OF_MEMORY = -3,
+    LP_DEVICE_TIMEOUT = -4,
+    LP_NOT_SUPPORTED = -5
+} lp_status;
+
+enum { LP_MEM_HOST = 0, LP_MEM_DEVICE = 1 };
+
+/* Arithmetic of the PDHG iterations.
+ * LP_PREC_FP64: matrix, iterates and reductions in FP64.
+ * LP_PREC_MIXED: matrix, iterates and SpMV accumulation in FP32, every
+ *   reduction (KKT terms, step-size terms) in FP64; once the FP32 phase reaches
+ *   max(tol, polish_switch_tol) the state moves to FP64 and FP64 iterations
+ *   continue to tol (FP64 polish). */
+enum { LP_PREC_FP64 = 0, LP_PREC_MIXED = 1 };
+
+/* The LP.  Arrays: row_ptr[m+1] (row_ptr[0] = 0, non-decreasing,
+ * row_ptr[m] = nnz), col_idx[nnz] in [0, n) (any order inside a row; duplicates
+ * are summed), vals[nnz], sense[m], c[n], q[m], l[n], u[n] with l <= u and no
+ * NaN anywhere.  Requirements: m >= 1, n >= 1, nnz < 2^31. */
+typedef struct {
+    int64_t m, n, nnz;
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    const double* vals;
+    const uint8_t* sense;
+    const double* c;
+    const double* q;
+    const double* l;
+    const double* u;
+    int32_t memory_space;     /* LP_MEM_HOST or LP_MEM_DEVICE, for all arrays above */
+    int32_t reserved;
+} lp_desc;
+
+/* Solver options.  Fill with lp_opts_default, then change fields. */
+typedef struct {
+    double tol;                  /* epsilon of Section 2.3.2 (default 1e-4) */
+    int64_t max_iters;           /* accepted PDHG iterations (default 1e6) */
+    double time_limit_s;         /* wall-clock limit checked on the device (default 3600) */
+    int32_t precision;           /* LP_PREC_FP64 (default) or LP_PREC_MIXED */
+    int32_t check_every;         /* accepted iterations between KKT checks (default 64) */
+    int32_t ruiz_iters;          /* passes of Algorithm 3 (default 10; 0 disables) */
+    int32_t pock_chambolle;      /* 1: one alpha = 1 Pock-Chambolle pass after Ruiz (default 0) */
+    int32_t adaptive_step;       /* 1: Algorithm 5 (default 1); 0: fixed eta */
+    int32_t primal_weight_update;/* 1: Algorithm 4 at restarts (default 1) */
+    int32_t restarts;            /* 1: adaptive restarts of Section 2.4.2 (default 1) */
+    int32_t power_iters;         /* iterations of Algorithm 2 (default 100) */
+    double ruiz_tol;             /* Algorithm 3 stops when all norms are within this of 1 (1e-4) */
+    double eta_scale;            /* initial eta = eta_scale / ||K~||_2 (default 0.9) */
+    double beta_sufficient;      /* 0.2 */
+    double beta_necessary;       /* 0.8 */
+    double beta_artificial;      /* 0.36 */
+    double eps_zero;             /* 1e-6 */
+    double polish_switch_tol;    /* LP_PREC_MIXED: FP32 phase target (default 1e-5) */
+    const double* x0;            /* optional warm start (unscaled primal, length n) or NULL */
+    const double* y0;            /* optional warm start (unscaled dual, length m) or NULL */
+    double omega0;               /* > 0: initial primal weight instead of ||c~||/||q~|| */
+    double eta0;                 /* > 0: initial step size instead of eta_scale/||K~|| */
+    int32_t warm_memory_space;   /* memory space of x0 / y0 */
+    int32_t reserved;
+} lp_opts;
+
+/* One record per KKT check (the start, every check_every accepted
+ * iterations, and the last iteration). */
+typedef struct {
+    double k;            /* accepted iterations so far */
+    double attempts;     /* step attempts (accepted + rejected by Algorithm 5) */
+    double restart;      /* 1 if this check restarted */
+    double cand_is_avg;  /* 1 if the restart candidate was the average */
+    double omega;        /* primal weight after this check */
+    double eta;          /* step size at this check */
+    double kkt_cur;      /* KKT_omega of the current iterate (scaled problem) */
+    double kkt_avg;      /* KKT_omega of the average (+inf when empty) */
+    double rel_gap;      /* Section 2.3.2 relative errors of the candidate, unscaled */
+    double rel_pres;
+    double rel_dres;
+    double kkt_cand;     /* KKT_omega of the candidate */
+} lp_trace_rec;
+
+/* Results.  x (length n) and y (length m) are caller-owned buffers in
+ * memory_space; either may be NULL.  They receive the unscaled candidate of the
+ * last check.  trace (host, trace_cap records) is optional. */
+typedef struct {
+    lp_status status;
+    int32_t precision_used;      /* precision of the last phase */
+    int64_t iters;               /* accepted iterations (all phases) */
+    int64_t attempts;            /* step attempts (all phases) */
+    int64_t restarts;
+    int64_t fp64_iters;          /* accepted iterations of the FP64 phase */
+    double pobj, dobj;           /* c^T x and q^T y + l^T lambda^+ + u^T lambda^- (unscaled) */
+    double rel_gap, rel_pres, rel_dres;
+    double omega, eta;           /* final primal weight and step size */
+    double norm_K;               /* Algorithm 2 estimate of ||K~||_2 */
+    double setup_s;              /* scaling + power iteration + casts (host wall clock) */
+    double solve_s;              /* iterations (host wall clock) */
+    double* x;
+    double* y;
+    int32_t memory_space;        /* of x and y */
+    int32_t reserved;
+    lp_trace_rec* trace;
+    int64_t trace_cap;
+    int64_t trace_len;           /* records produced (may exceed trace_cap) */
+} lp_result;
+
+/* Fills *opts with the defaults listed above.  No CUDA call. */
+void lp_opts_default(lp_opts* opts);
+
+/* Copies the LP (Section 2.2) to the current device, validates it on the
+ * device (row_ptr monotone and in range, col_idx in [0, n), no NaN, l <= u) and
+ * builds the transposed CSR K^T (Section 2.3, products K^T y) and the row-block
+ * schedules of both matrices.  cuda_stream: a cudaStream_t or NULL.
+ * Errors: LP_INVALID_ARGUMENT (NULL pointers, bad sizes, failed validation),
+ * LP_OUT_OF_MEMORY, LP_CUDA_ERROR.  On error *out is NULL. */
+lp_status lp_create(const lp_desc* desc, void* cuda_stream, lp_handle* out);
+
+/* Restarted PDHG (Algorithm 1 with theta = 1; Ruiz scaling, Algorithm 3;
+ * step size from Algorithm 2; adaptive restarts, Section 2.4.2; primal weight,
+ * Algorithm 4; adaptive steps, Algorithm 5; termination, Section 2.3.2, on the
+ * unscaled problem).  The iteration loop runs on the device inside a CUDA graph
+ * with a device-side while condition; the host waits once at the end.
+ * Returns the solver outcome (LP_OPTIMAL, LP_ITERATION_LIMIT, LP_TIME_LIMIT,
+ * LP_NUMERICAL_ERROR), also stored in res->status, or a negative error. */
+lp_status lp_solve(lp_handle h, const lp_opts* opts, lp_result* res);
+
+/* Solves count independent LPs with the same options; results[i] belongs to
+ * hs[i].  Returns LP_OK when every solve returned a non-negative status (the
+ * per-LP outcomes are in results[i].status), else the first negative error. */
+lp_status lp_solve_batch(const lp_handle* hs, int32_t count, const lp_opts* opts,
+                         lp_result* results);
+
+/* Gradient of a loss L(x_K) through K_iters unrolled fixed-step PDHG
+ * iterations (Algorithm 1, theta = 1, unscaled problem, start x = proj_X(0),
+ * y = 0) with tau = eta / omega, sigma = eta * omega held constant; eta and
+ * omega come from opts->eta0 / opts->omega0 when positive, else
+ * eta_scale / ||K||_2 (Algorithm 2 on the unscaled K) and ||c|| / ||q||.
+ * opts->precision selects FP64 or FP32 arithmetic.  Iterates are checkpointed
+ * every ckpt_every iterations and recomputed segment by segment.
+ * dL_dxK[n]: input adjoint.  Outputs (caller-owned, overwritten): dc[n],
+ * dq[m], dvals[nnz] in the nonzero order of lp_desc, and x_K[n] if not NULL.
+ * All of them live in memory_space.  tau_sigma_out (host, 2 doubles, or NULL)
+ * receives the tau and sigma used. */
+lp_status lp_grad(lp_handle h, const lp_opts* opts, int32_t K_iters, int32_t ckpt_every,
+                  const double* dL_dxK, double* dc, double* dq, double* dvals,
+                  double* x_K, int32_t memory_space, double* tau_sigma_out);
+
+/* Measurement hook: runs `reps` PDHG step attempts of the given precision on
+ * the state left by the last lp_solve of that precision, timing each kernel
+ * class with CUDA events on the handle's stream.  ms_out (host, 4 doubles)
+ * receives the mean milliseconds per launch of: [0] primal update,
+ * [1] K x' SpMV + dual update, [2] K^T y' SpMV + step terms, [3] step control.
+ * bytes_out (host, 4 doubles, or NULL) receives the algorithmic bytes per launch
+ * of the same kernels.  The solver state afterwards is unspecified. */
+lp_status lp_profile_step(lp_handle h, int32_t precision, int32_t reps, double* ms_out,
+                          double* bytes_out);
+
+/* Releases the handle and all its device memory.  NULL is ignored. */
+void lp_destroy(lp_handle h);
+
+/* Static, NUL-terminated name of a status. */
+const char* lp_status_string(lp_status s);
+
+/* LP_ABI_VERSION of the library. */
+int32_t lp_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_PDHG_LP_H */

@@ -1,0 +1,291 @@
+// C ABI (include/lp.h): handle lifetime, solve orchestration (FP64 or FP32 +
+// FP64 polish), batch, gradient and measurement entry points.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+using namespace pdhg;
+
+struct lp_problem_s {
+    Handle h;
+};
+
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+void free_all(Handle* h)
+{
+    for (auto* E : {&h->e64.exec, &h->e64.body_exec, &h->e32.exec, &h->e32.body_exec})
+        if (*E) {
+            cudaGraphExecDestroy(*E);
+            *E = nullptr;
+        }
+    for (auto& b : h->allocs) cudaFree(b.p);
+    h->allocs.clear();
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    h->stream = nullptr;
+}
+
+lp_status check_opts(const lp_opts* o)
+{
+    if (!o) return LP_INVALID_ARGUMENT;
+    if (!(o->tol >= 0.0) || o->max_iters < 0 || o->check_every < 1 || o->ruiz_iters < 0 ||
+        o->power_iters < 0 || !(o->eta_scale > 0.0) || !(o->time_limit_s > 0.0))
+        return LP_INVALID_ARGUMENT;
+    if (o->precision != LP_PREC_FP64 && o->precision != LP_PREC_MIXED) return LP_INVALID_ARGUMENT;
+    return LP_OK;
+}
+
+void fill_result(lp_result* r, const Ctrl& c)
+{
+    r->status = (lp_status)c.status;
+    r->iters = c.k;
+    r->attempts = c.attempts;
+    r->restarts = c.restarts;
+    r->pobj = c.pobj;
+    r->dobj = c.dobj;
+    r->rel_gap = c.rel_gap;
+    r->rel_pres = c.rel_pres;
+    r->rel_dres = c.rel_dres;
+    r->omega = c.omega;
+    r->eta = c.eta;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lp_opts_default(lp_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-4;
+    o->max_iters = 1000000;
+    o->time_limit_s = 3600.0;
+    o->precision = LP_PREC_FP64;
+    o->check_every = 64;
+    o->ruiz_iters = 10;
+    o->pock_chambolle = 0;
+    o->adaptive_step = 1;
+    o->primal_weight_update = 1;
+    o->restarts = 1;
+    o->power_iters = 100;
+    o->ruiz_tol = 1e-4;
+    o->eta_scale = 0.9;
+    o->beta_sufficient = 0.2;
+    o->beta_necessary = 0.8;
+    o->beta_artificial = 0.36;
+    o->eps_zero = 1e-6;
+    o->polish_switch_tol = 1e-5;
+    o->x0 = nullptr;
+    o->y0 = nullptr;
+    o->omega0 = 0.0;
+    o->eta0 = 0.0;
+    o->warm_memory_space = LP_MEM_HOST;
+}
+
+const char* lp_status_string(lp_status s)
+{
+    switch (s) {
+    case LP_OK: return "LP_OK";
+    case LP_OPTIMAL: return "LP_OPTIMAL";
+    case LP_PRIMAL_INFEASIBLE: return "LP_PRIMAL_INFEASIBLE";
+    case LP_DUAL_INFEASIBLE: return "LP_DUAL_INFEASIBLE";
+    case LP_ITERATION_LIMIT: return "LP_ITERATION_LIMIT";
+    case LP_TIME_LIMIT: return "LP_TIME_LIMIT";
+    case LP_NUMERICAL_ERROR: return "LP_NUMERICAL_ERROR";
+    case LP_INVALID_ARGUMENT: return "LP_INVALID_ARGUMENT";
+    case LP_CUDA_ERROR: return "LP_CUDA_ERROR";
+    case LP_OUT_OF_MEMORY: return "LP_OUT_OF_MEMORY";
+    case LP_DEVICE_TIMEOUT: return "LP_DEVICE_TIMEOUT";
+    case LP_NOT_SUPPORTED: return "LP_NOT_SUPPORTED";
+    }
+    return "LP_UNKNOWN_STATUS";
+}
+
+int32_t lp_abi_version(void) { return LP_ABI_VERSION; }
+
+lp_status lp_create(const lp_desc* d, void* cuda_stream, lp_handle* out)
+{
+    if (!out) return LP_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (!d || d->m < 1 || d->n < 1 || d->nnz < 0 || d->nnz >= ((int64_t)1 << 31) ||
+        d->n >= ((int64_t)1 << 31) || d->m >= ((int64_t)1 << 31))
+        return LP_INVALID_ARGUMENT;
+    if (!d->row_ptr || (d->nnz > 0 && (!d->col_idx || !d->vals)) || !d->sense || !d->c || !d->q ||
+        !d->l || !d->u)
+        return LP_INVALID_ARGUMENT;
+    if (d->memory_space != LP_MEM_HOST && d->memory_space != LP_MEM_DEVICE)
+        return LP_INVALID_ARGUMENT;
+    if (d->memory_space == LP_MEM_HOST) {
+        // cheap host-side checks of the structure before any device work
+        if (d->row_ptr[0] != 0 || d->row_ptr[d->m] != d->nnz) return LP_INVALID_ARGUMENT;
+    }
+    lp_problem_s* p = new (std::nothrow) lp_problem_s();
+    if (!p) return LP_OUT_OF_MEMORY;
+    Handle* h = &p->h;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete p;
+        return LP_CUDA_ERROR;
+    }
+    if (cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            delete p;
+            return LP_CUDA_ERROR;
+        }
+        h->own_stream = true;
+    }
+    lp_status s = setup_create(h, d);
+    if (s != LP_OK) {
+        cudaStreamSynchronize(h->stream);
+        (void)cudaGetLastError();
+        free_all(h);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return LP_OK;
+}
+
+void lp_destroy(lp_handle p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(p->h.stream);
+    free_all(&p->h);
+    delete p;
+}
+
+static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
+{
+    LP_TRY(check_opts(o));
+    if (!r) return LP_INVALID_ARGUMENT;
+    if (r->memory_space != LP_MEM_HOST && r->memory_space != LP_MEM_DEVICE)
+        return LP_INVALID_ARGUMENT;
+    if ((o->x0 || o->y0) && o->warm_memory_space != LP_MEM_HOST &&
+        o->warm_memory_space != LP_MEM_DEVICE)
+        return LP_INVALID_ARGUMENT;
+    const double t0 = now_s();
+    // setup: scaling (Algorithm 3), norm (Algorithm 2), step size and weight
+    LP_TRY(setup_engine<double>(h, o));
+    double normK = 0.0;
+    LP_TRY(setup_scale(h, o, &normK));
+    double cs2 = 0.0, qs2 = 0.0;
+    LP_TRY(sum_of_squares(h, h->e64.c, h->n, &cs2));
+    LP_TRY(sum_of_squares(h, h->e64.q, h->m, &qs2));
+    const double cn = std::sqrt(cs2), qn = std::sqrt(qs2);
+    double omega0 = (cn > o->eps_zero && qn > o->eps_zero) ? cn / qn : 1.0;
+    if (o->omega0 > 0.0) omega0 = o->omega0;
+    double eta0 = normK > 0.0 ? o->eta_scale / normK : 1.0;
+    if (o->eta0 > 0.0) eta0 = o->eta0;
+    if (o->precision == LP_PREC_MIXED) LP_TRY(setup_engine<float>(h, o));
+    LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const double t1 = now_s();
+    r->setup_s = t1 - t0;
+    r->norm_K = normK;
+
+    Ctrl c;
+    std::memset(&c, 0, sizeof(c));
+    r->trace_len = 0;
+    if (o->precision == LP_PREC_MIXED) {
+        lp_opts o32 = *o;
+        o32.tol = std::max(o->tol, o->polish_switch_tol);
+        LP_TRY(run_solve<float>(h, &o32, eta0, omega0, nullptr, nullptr, o->x0, o->y0,
+                                o->warm_memory_space, 0, 0, 0, r->trace, r->trace_cap, 0, &c));
+        r->trace_len = c.trace_len;
+        r->precision_used = LP_PREC_MIXED;
+        r->fp64_iters = 0;
+        const bool polish = c.status == LP_OPTIMAL && o->tol < o32.tol;
+        if (!polish) {
+            fill_result(r, c);
+            LP_TRY(extract_solution<float>(h, r->x, r->y, r->memory_space));
+        } else {
+            if (!h->wbuf) LP_TRY(dev_alloc_n(h, &h->wbuf, (size_t)(h->n + h->m)));
+            LP_TRY(extract_solution_ex<float>(h, nullptr, nullptr, LP_MEM_DEVICE, h->wbuf,
+                                              h->wbuf + h->n));
+            lp_opts o64 = *o;
+            o64.time_limit_s = std::max(1e-3, o->time_limit_s - (now_s() - t1));
+            const long long k32 = c.k;
+            Ctrl c2;
+            LP_TRY(run_solve<double>(h, &o64, c.eta, c.omega, h->wbuf, h->wbuf + h->n, nullptr,
+                                     nullptr, LP_MEM_HOST, c.k, c.attempts, c.restarts, r->trace,
+                                     r->trace_cap, std::min<long long>(c.trace_len, r->trace_cap),
+                                     &c2));
+            r->trace_len = c.trace_len + c2.trace_len;
+            fill_result(r, c2);
+            r->fp64_iters = c2.k - k32;
+            r->precision_used = LP_PREC_FP64;
+            LP_TRY(extract_solution<double>(h, r->x, r->y, r->memory_space));
+        }
+    } else {
+        LP_TRY(run_solve<double>(h, o, eta0, omega0, nullptr, nullptr, o->x0, o->y0,
+                                 o->warm_memory_space, 0, 0, 0, r->trace, r->trace_cap, 0, &c));
+        r->trace_len = c.trace_len;
+        fill_result(r, c);
+        r->fp64_iters = c.k;
+        r->precision_used = LP_PREC_FP64;
+        LP_TRY(extract_solution<double>(h, r->x, r->y, r->memory_space));
+    }
+    r->solve_s = now_s() - t1;
+    return r->status;
+}
+
+lp_status lp_solve(lp_handle p, const lp_opts* o, lp_result* r)
+{
+    if (!p) return LP_INVALID_ARGUMENT;
+    lp_status s = solve_impl(&p->h, o, r);
+    if (s < 0) {
+        cudaStreamSynchronize(p->h.stream);
+        (void)cudaGetLastError();
+    }
+    return s;
+}
+
+lp_status lp_solve_batch(const lp_handle* hs, int32_t count, const lp_opts* o, lp_result* rs)
+{
+    if (!hs || !rs || count < 0) return LP_INVALID_ARGUMENT;
+    for (int32_t i = 0; i < count; ++i) {
+        lp_status s = lp_solve(hs[i], o, &rs[i]);
+        if (s < 0) return s;
+    }
+    return LP_OK;
+}
+
+lp_status lp_grad(lp_handle p, const lp_opts* o, int32_t K_iters, int32_t ckpt_every,
+                  const double* dL_dxK, double* dc, double* dq, double* dvals, double* x_K,
+                  int32_t memory_space, double* tau_sigma_out)
+{
+    if (!p || !o || K_iters < 0 || ckpt_every < 1 || !dL_dxK || !dc || !dq || !dvals)
+        return LP_INVALID_ARGUMENT;
+    if (memory_space != LP_MEM_HOST && memory_space != LP_MEM_DEVICE) return LP_INVALID_ARGUMENT;
+    lp_status s = run_grad(&p->h, o, K_iters, ckpt_every, dL_dxK, dc, dq, dvals, x_K,
+                           memory_space, tau_sigma_out);
+    if (s < 0) {
+        cudaStreamSynchronize(p->h.stream);
+        (void)cudaGetLastError();
+    }
+    return s;
+}
+
+lp_status lp_profile_step(lp_handle p, int32_t precision, int32_t reps, double* ms_out,
+                          double* bytes_out)
+{
+    if (!p || !ms_out || reps < 1) return LP_INVALID_ARGUMENT;
+    if (precision == LP_PREC_FP64) return profile_step<double>(&p->h, reps, ms_out, bytes_out);
+    if (precision == LP_PREC_MIXED) return profile_step<float>(&p->h, reps, ms_out, bytes_out);
+    return LP_INVALID_ARGUMENT;
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+// Shared declarations of the CUDA solver: device control block, handle layout,
+// error plumbing and small device reductions.  Everything here is the solver's
+// own; nothing is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+
+#include "../../include/lp.h"
+
+namespace pdhg {
+
+// ----------------------------------------------------------------- constants
+
+constexpr int kNT = 256;          // threads of an SpMV row-block
+constexpr int kEW = 256;          // threads of an elementwise block
+constexpr int kEWGrid = 1216;     // elementwise grid cap: 152 SMs x 8 resident blocks
+constexpr int kCtlNT = 512;       // threads of a control (single-block) kernel
+
+// nnz staged in shared memory per row-block (CSR-stream); rows longer than
+// this form a block of their own that loops over the row.
+template <typename T> struct Cap;
+template <> struct Cap<double> { static constexpr int value = 2048; };
+template <> struct Cap<float>  { static constexpr int value = 4096; };
+
+// status codes shared with the ABI
+constexpr int kRunning = -100;
+
+// --------------------------------------------------------------- control block
+// One per handle and precision, in device memory.  Written only by
+// single-thread sections of control kernels, read by all kernels of a step.
+struct Ctrl {
+    // step state
+    double eta, omega;
+    double pend_w;       // eta of the last accepted iterate not yet added to the averages
+    double W;            // sum of eta over the iterates in the averages
+    // restart state (Section 2.4.2)
+    double kkt_anchor, kkt_prev;
+    // last check
+    double kkt_cur, kkt_avg, kkt_cand, rel_gap, rel_pres, rel_dres, pobj, dobj;
+    // options
+    double tol, beta_s, beta_n, beta_a, eps_zero;
+    double qnorm, cnorm;         // ||q||_2, ||c||_2 of the unscaled problem
+    double time_limit_ns;
+    // counters
+    long long k, attempts, epoch_k, restarts, max_iters, t0_ns, trace_len, trace_cap;
+    int cur;             // which half of each double buffer holds the current iterate
+    int skip;            // step kernels return at once (check pending or done)
+    int want_check;      // the check kernels run
+    int done;            // loop finished; status holds the outcome
+    int status;
+    int first;           // the next check is the start-point check
+    int cand_avg;        // candidate of the last check is the average
+    int restart;         // the last check restarted
+    int adaptive, pwu, restarts_on, check_every;
+    int rejects;         // consecutive rejected attempts (a guard against a stuck loop)
+    int pad0;
+};
+
+// ------------------------------------------------------------- device buffers
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// State and scaled data of one precision T (double or float).
+template <typename T>
+struct Engine {
+    bool ready = false;
+    // scaled matrix in both orientations (values only; structure is shared)
+    T* val = nullptr;      // K~, CSR order of K   (padded to a multiple of 8)
+    T* tval = nullptr;     // K~^T, CSR order of K^T
+    T *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr;   // scaled vectors
+    // iterate double buffers
+    T* X[2] = {nullptr, nullptr};
+    T* Y[2] = {nullptr, nullptr};
+    T* KX[2] = {nullptr, nullptr};
+    T* KTY[2] = {nullptr, nullptr};
+    T *XS = nullptr, *YS = nullptr;      // eta-weighted sums
+    T *XA = nullptr, *YA = nullptr;      // averages
+    T *KXA = nullptr, *KTYA = nullptr;   // their products
+    T *XANC = nullptr, *YANC = nullptr;  // restart anchor
+    // row-block schedules for this precision's staging capacity
+    int32_t* brow = nullptr;   int nblk = 0;    // K rows
+    int32_t* bcol = nullptr;   int ntblk = 0;   // K^T rows
+    // reduction partials
+    double* partD = nullptr;   // [nblk]
+    double* partT = nullptr;   // [2][ntblk]
+    double* partR = nullptr;   // [8][kEWGrid]
+    double* partC = nullptr;   // [10][kEWGrid]
+    Ctrl* ctrl = nullptr;
+    lp_trace_rec* trace = nullptr;  // device trace ring
+    long long trace_cap = 0;
+    // loop graph
+    cudaGraphExec_t exec = nullptr;
+    int graph_check_every = -1;
+    int graph_slots = -1;
+    bool graph_conditional = false;
+    cudaGraphExec_t body_exec = nullptr;   // host-loop fallback
+};
+
+struct Handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t m = 0, n = 0, nnz = 0;
+    // original (unscaled) problem, FP64
+    int64_t* rp = nullptr;       // [m+1]
+    int32_t* ci = nullptr;       // [nnz] padded
+    double* val0 = nullptr;      // [nnz] padded
+    uint8_t* sense = nullptr;    // [m]
+    double *c0 = nullptr, *q0 = nullptr, *l0 = nullptr, *u0 = nullptr;
+    int32_t* krow = nullptr;     // row of each nonzero of K
+    // transpose
+    int64_t* trp = nullptr;      // [n+1]
+    int32_t* tci = nullptr;      // [nnz] padded: row index i of each K^T entry
+    int32_t* tperm = nullptr;    // [nnz]: K^T entry -> nonzero index of K
+    // scaling
+    double *R = nullptr, *C = nullptr;
+    double qnorm = 0, cnorm = 0;
+    // host copies of the structure (for the schedulers)
+    std::vector<int64_t> h_rp, h_trp;
+    // scratch
+    double* scratch = nullptr;   size_t scratch_bytes = 0;
+    double* wbuf = nullptr;      // [n + m] scaled FP64 hand-off state (mixed precision polish)
+    std::vector<DevBuf> allocs;
+    Engine<double> e64;
+    Engine<float> e32;
+    int built_precision_mask = 0;
+};
+
+template <typename T> Engine<T>& engine_of(Handle* h);
+template <> inline Engine<double>& engine_of<double>(Handle* h) { return h->e64; }
+template <> inline Engine<float>& engine_of<float>(Handle* h) { return h->e32; }
+
+// ------------------------------------------------------------ error plumbing
+
+#define LP_CUDA_TRY(expr)                                                        \
+    do {                                                                         \
+        cudaError_t _e = (expr);                                                 \
+        if (_e != cudaSuccess) {                                                 \
+            (void)cudaGetLastError();                                            \
+            return _e == cudaErrorMemoryAllocation ? LP_OUT_OF_MEMORY : LP_CUDA_ERROR; \
+        }                                                                        \
+    } while (0)
+
+#define LP_TRY(expr)                                                             \
+    do {                                                                         \
+        lp_status _s = (expr);                                                   \
+        if (_s != LP_OK) return _s;                                              \
+    } while (0)
+
+lp_status dev_alloc(Handle* h, void** p, size_t bytes);
+template <typename T>
+inline lp_status dev_alloc_n(Handle* h, T** p, size_t count)
+{
+    void* q = nullptr;
+    lp_status s = dev_alloc(h, &q, count * sizeof(T) + 64);
+    *p = static_cast<T*>(q);
+    return s;
+}
+inline size_t pad8(int64_t n) { return (size_t)((n + 7) & ~(int64_t)7); }
+
+// ------------------------------------------------------- device reductions
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums NQ per-thread values over the block (fixed order) and stores the block
+// totals at part[q * stride + blockIdx.x].
+template <int NQ, int NT>
+__device__ __forceinline__ void block_partials(const double (&v)[NQ], double* part, int stride)
+{
+    __shared__ double sh[NQ][NT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double t = warp_sum(v[q]);
+        if (lane == 0) sh[q][warp] = t;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = lane < NT / 32 ? sh[q][lane] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) part[(size_t)q * stride + blockIdx.x] = t;
+        }
+    }
+}
+
+// Fixed-order sum of part[0..count) by a whole block of NT threads; the
+// result is valid in every thread.
+template <int NT>
+__device__ double block_sum_array(const double* part, int count)
+{
+    __shared__ double sh[NT / 32];
+    __shared__ double total;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += NT) s += part[i];
+    s = warp_sum(s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        double t = lane < NT / 32 ? sh[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) total = t;
+    }
+    __syncthreads();
+    double r = total;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------ entry points
+// setup.cu
+lp_status setup_create(Handle* h, const lp_desc* d);
+lp_status setup_scale(Handle* h, const lp_opts* o, double* normK);
+template <typename T> lp_status setup_engine(Handle* h, const lp_opts* o);
+// solver.cu
+template <typename T>
+lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
+                    const double* warm_x_scaled_dev, const double* warm_y_scaled_dev,
+                    const double* warm_x_user, const double* warm_y_user, int warm_space,
+                    long long k0, long long attempts0, long long restarts0,
+                    lp_trace_rec* trace_host, long long trace_cap_host, long long trace_off,
+                    Ctrl* out_ctrl);
+template <typename T>
+lp_status extract_solution(Handle* h, double* x, double* y, int space);
+template <typename T>
+lp_status extract_solution_ex(Handle* h, double* x, double* y, int space, double* xs_dev,
+                              double* ys_dev);
+lp_status sum_of_squares(Handle* h, const double* v, int64_t count, double* out_host);
+template <typename T>
+lp_status profile_step(Handle* h, int reps, double* ms, double* bytes);
+// grad.cu
+lp_status run_grad(Handle* h, const lp_opts* o, int K_iters, int ckpt, const double* gxK,
+                   double* dc, double* dq, double* dvals, double* xK, int space,
+                   double* tau_sigma);
+
+}  // namespace pdhg

@@ -1,0 +1,590 @@
+// Problem setup on the device: copy + validation, the transposed CSR K^T,
+// Ruiz / Pock-Chambolle scaling (Algorithm 3, Section 2.4.1), the spectral
+// norm estimate (Algorithm 2) and the per-precision scaled copies.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "common.cuh"
+#include "spmv.cuh"
+
+namespace pdhg {
+
+lp_status dev_alloc(Handle* h, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 64;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? LP_OUT_OF_MEMORY : LP_CUDA_ERROR;
+    }
+    h->allocs.push_back(DevBuf{*p, bytes});
+    return LP_OK;
+}
+
+std::vector<int32_t> make_row_blocks(const int64_t* rp, int64_t rows, int cap, int max_rows)
+{
+    std::vector<int32_t> b;
+    b.reserve((size_t)(rows / 16 + 2));
+    b.push_back(0);
+    int64_t nnz_acc = 0, rows_acc = 0;
+    for (int64_t r = 0; r < rows; ++r) {
+        const int64_t len = rp[r + 1] - rp[r];
+        if (len > cap) {
+            if (rows_acc > 0) b.push_back((int32_t)r);
+            b.push_back((int32_t)(r + 1));
+            nnz_acc = rows_acc = 0;
+            continue;
+        }
+        if (rows_acc > 0 && (nnz_acc + len > cap || rows_acc == max_rows)) {
+            b.push_back((int32_t)r);
+            nnz_acc = rows_acc = 0;
+        }
+        nnz_acc += len;
+        ++rows_acc;
+    }
+    if (rows_acc > 0) b.push_back((int32_t)rows);
+    return b;
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_validate(int64_t m, int64_t n, int64_t nnz, const int64_t* rp,
+                           const int32_t* ci, const double* val, const uint8_t* sense,
+                           const double* c, const double* q, const double* l,
+                           const double* u, int* flags)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int f = 0;
+    if (t0 == 0 && (rp[0] != 0 || rp[m] != nnz)) f |= 1;
+    for (int64_t i = t0; i < m; i += stride) {
+        if (rp[i + 1] < rp[i]) f |= 1;
+        if (sense[i] > 1) f |= 16;
+        if (isnan(q[i]) || isinf(q[i])) f |= 4;
+    }
+    for (int64_t p = t0; p < nnz; p += stride) {
+        if (ci[p] < 0 || ci[p] >= n) f |= 2;
+        if (!isfinite(val[p])) f |= 4;
+    }
+    for (int64_t j = t0; j < n; j += stride) {
+        if (isnan(c[j]) || isinf(c[j])) f |= 4;
+        if (isnan(l[j]) || isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY || u[j] == -INFINITY)
+            f |= 8;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+// one warp per row: krow[p] = i for every nonzero of row i
+__global__ void k_row_of_nnz(int64_t m, const int64_t* rp, int32_t* krow)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < m; w += nw)
+        for (int64_t p = rp[w] + lane; p < rp[w + 1]; p += 32) krow[p] = (int32_t)w;
+}
+
+__global__ void k_col_count(int64_t nnz, const int32_t* ci, int64_t* cnt)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(reinterpret_cast<unsigned long long*>(cnt + ci[p]), 1ull);
+}
+
+__global__ void k_scatter_t(int64_t nnz, const int32_t* ci, unsigned long long* cursor,
+                            int32_t* tperm)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long pos = atomicAdd(cursor + ci[p], 1ull);
+        tperm[pos] = (int32_t)p;
+    }
+}
+
+// Segments of <= 32 entries: one thread, insertion sort (ascending nonzero index).
+__global__ void k_sort_short(int64_t n, const int64_t* trp, int32_t* tperm)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = trp[j], e = trp[j + 1];
+        if (e - s > 32) continue;
+        for (int64_t a = s + 1; a < e; ++a) {
+            const int32_t key = tperm[a];
+            int64_t b = a - 1;
+            while (b >= s && tperm[b] > key) {
+                tperm[b + 1] = tperm[b];
+                --b;
+            }
+            tperm[b + 1] = key;
+        }
+    }
+}
+
+// Longer segments: one block per listed segment, bitonic sort over a
+// power-of-two buffer padded with INT32_MAX; the buffer is shared memory when
+// it fits (len2 <= smem_cap) and global scratch otherwise.
+__global__ void k_sort_long(const int32_t* segs, const int64_t* trp, int32_t* tperm,
+                            int32_t* gscratch, int smem_cap)
+{
+    extern __shared__ int32_t sbuf[];
+    const int64_t j = segs[blockIdx.x];
+    const int64_t s = trp[j], e = trp[j + 1];
+    const int64_t len = e - s;
+    int64_t len2 = 1;
+    while (len2 < len) len2 <<= 1;
+    int32_t* buf = len2 <= smem_cap ? sbuf : gscratch + 2 * s;
+    for (int64_t i = threadIdx.x; i < len2; i += blockDim.x)
+        buf[i] = i < len ? tperm[s + i] : INT32_MAX;
+    __syncthreads();
+    for (int64_t k = 2; k <= len2; k <<= 1) {
+        for (int64_t jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int64_t i = threadIdx.x; i < len2; i += blockDim.x) {
+                const int64_t ixj = i ^ jj;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const int32_t a = buf[i], b = buf[ixj];
+                    if ((a > b) == up) {
+                        buf[i] = b;
+                        buf[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) tperm[s + i] = buf[i];
+}
+
+__global__ void k_fill_tci(int64_t nnz, const int32_t* tperm, const int32_t* krow, int32_t* tci)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz;
+         t += (int64_t)gridDim.x * blockDim.x)
+        tci[t] = krow[tperm[t]];
+}
+
+template <typename T>
+__global__ void k_fill(T* p, int64_t count, T v)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x)
+        p[t] = v;
+}
+
+// Ruiz: row infinity norms (one warp per row, exact max)
+__global__ void k_row_inf(int64_t m, const int64_t* rp, const double* v, double* rn)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the trip count is uniform per warp (w steps by whole warps)
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < m; w += nw) {
+        double a = 0.0;
+        for (int64_t p = rp[w] + lane; p < rp[w + 1]; p += 32) a = fmax(a, fabs(v[p]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+        if (lane == 0) rn[w] = a;
+    }
+}
+
+// Ruiz: column infinity norms by an integer max on the bit pattern
+// (non-negative IEEE doubles order like their bits).
+__global__ void k_col_inf(int64_t nnz, const int32_t* ci, const double* v, unsigned long long* cn)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double a = fabs(v[p]);
+        atomicMax(cn + ci[p], (unsigned long long)__double_as_longlong(a));
+    }
+}
+
+// deviation max |1 - norm| over non-empty rows and columns -> dev (bit pattern max)
+__global__ void k_ruiz_dev(int64_t m, int64_t n, const double* rn, const double* cn,
+                           unsigned long long* dev)
+{
+    double d = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m + n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double v = t < m ? rn[t] : cn[t - m];
+        if (v > 0.0) d = fmax(d, fabs(1.0 - v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dev, (unsigned long long)__double_as_longlong(d));
+}
+
+// norm -> factor 1/sqrt(norm) (1 for an empty row/column); accumulate
+__global__ void k_ruiz_factors(int64_t count, double* nrm, double* acc)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double f = nrm[t] > 0.0 ? 1.0 / sqrt(nrm[t]) : 1.0;
+        nrm[t] = f;
+        acc[t] *= f;
+    }
+}
+
+__global__ void k_scale_vals(int64_t nnz, const int32_t* krow, const int32_t* ci,
+                             const double* r, const double* s, double* v)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x)
+        v[p] = v[p] * r[krow[p]] * s[ci[p]];
+}
+
+// Pock-Chambolle (alpha = 1): sequential per-row and per-column |.| sums in
+// row order (rows: CSR order; columns: K^T order, ascending rows).
+__global__ void k_pc_sums(int64_t m, int64_t n, const int64_t* rp, const int64_t* trp,
+                          const int32_t* tperm, const double* v, double* rs, double* cs)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m + n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        if (t < m) {
+            for (int64_t p = rp[t]; p < rp[t + 1]; ++p) a += fabs(v[p]);
+            rs[t] = a;
+        } else {
+            const int64_t j = t - m;
+            for (int64_t p = trp[j]; p < trp[j + 1]; ++p) a += fabs(v[tperm[p]]);
+            cs[j] = a;
+        }
+    }
+}
+
+__global__ void k_scale_vectors(int64_t m, int64_t n, const double* R, const double* C,
+                                const double* c0, const double* q0, const double* l0,
+                                const double* u0, double* c, double* q, double* l, double* u)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m + n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n) {
+            c[t] = C[t] * c0[t];
+            l[t] = l0[t] / C[t];
+            u[t] = u0[t] / C[t];
+        } else {
+            const int64_t i = t - n;
+            q[i] = R[i] * q0[i];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_gather_cast(int64_t count, const int32_t* perm, const double* src, T* dst)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = (T)src[perm ? perm[t] : t];
+}
+
+// FP64 sum of squares: fixed grid, partials then one block
+__global__ void k_sumsq_part(int64_t count, const double* v, double* part)
+{
+    double s = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * kEW)
+        s += v[t] * v[t];
+    const double a[1] = {s};
+    block_partials<1, kEW>(a, part, gridDim.x);
+}
+
+__global__ void k_sum_final(const double* part, int count, double* out)
+{
+    const double s = block_sum_array<kCtlNT>(part, count);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// power iteration step: b /= ||b||, or stop when ||b|| = 0
+__global__ void k_pow_normalize(int64_t n, double* b, const double* part, int nparts, int* go)
+{
+    __shared__ double nb;
+    if (*go == 0) return;
+    const double s = block_sum_array<kCtlNT>(part, nparts);
+    if (threadIdx.x == 0) nb = sqrt(s);
+    __syncthreads();
+    if (nb == 0.0) {
+        if (threadIdx.x == 0) *go = 0;
+        return;
+    }
+    for (int64_t j = threadIdx.x; j < n; j += kCtlNT) b[j] = b[j] / nb;
+}
+
+// ------------------------------------------------------------------ host
+
+static inline int grid_for(int64_t count, int nt = 256, int cap = 65535 * 8)
+{
+    int64_t g = (count + nt - 1) / nt;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+static lp_status copy_in(Handle* h, void* dst, const void* src, size_t bytes, int space)
+{
+    if (bytes == 0) return LP_OK;
+    LP_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes,
+                                space == LP_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice,
+                                h->stream));
+    return LP_OK;
+}
+
+lp_status sum_of_squares(Handle* h, const double* v, int64_t count, double* out_host)
+{
+    double* part = h->scratch;   // [kEWGrid] partials, then the total
+    const int g = grid_for(count, kEW, kEWGrid);
+    k_sumsq_part<<<g, kEW, 0, h->stream>>>(count, v, part);
+    k_sum_final<<<1, kCtlNT, 0, h->stream>>>(part, g, part + kEWGrid);
+    LP_CUDA_TRY(cudaGetLastError());
+    LP_CUDA_TRY(cudaMemcpyAsync(out_host, part + kEWGrid, sizeof(double),
+                                cudaMemcpyDeviceToHost, h->stream));
+    LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+lp_status setup_create(Handle* h, const lp_desc* d)
+{
+    const int64_t m = d->m, n = d->n, nnz = d->nnz;
+    h->m = m;
+    h->n = n;
+    h->nnz = nnz;
+    LP_TRY(dev_alloc_n(h, &h->rp, (size_t)m + 1));
+    LP_TRY(dev_alloc_n(h, &h->ci, pad8(nnz)));
+    LP_TRY(dev_alloc_n(h, &h->val0, pad8(nnz)));
+    LP_TRY(dev_alloc_n(h, &h->sense, (size_t)m));
+    LP_TRY(dev_alloc_n(h, &h->c0, (size_t)n));
+    LP_TRY(dev_alloc_n(h, &h->q0, (size_t)m));
+    LP_TRY(dev_alloc_n(h, &h->l0, (size_t)n));
+    LP_TRY(dev_alloc_n(h, &h->u0, (size_t)n));
+    LP_TRY(dev_alloc_n(h, &h->krow, pad8(nnz)));
+    LP_TRY(dev_alloc_n(h, &h->trp, (size_t)n + 1));
+    LP_TRY(dev_alloc_n(h, &h->tci, pad8(nnz)));
+    LP_TRY(dev_alloc_n(h, &h->tperm, pad8(nnz)));
+    LP_TRY(dev_alloc_n(h, &h->R, (size_t)m));
+    LP_TRY(dev_alloc_n(h, &h->C, (size_t)n));
+    h->scratch_bytes = std::max<size_t>((size_t)(2 * pad8(nnz) + 64) * sizeof(int32_t),
+                                        (size_t)(std::max(m, n) + 2 * kEWGrid + 64) * sizeof(double));
+    h->scratch_bytes = std::max<size_t>(h->scratch_bytes, (size_t)(m + n + 64) * 8 * 2);
+    LP_TRY(dev_alloc(h, (void**)&h->scratch, h->scratch_bytes));
+
+    LP_CUDA_TRY(cudaMemsetAsync(h->ci, 0, pad8(nnz) * sizeof(int32_t), h->stream));
+    LP_CUDA_TRY(cudaMemsetAsync(h->val0, 0, pad8(nnz) * sizeof(double), h->stream));
+    const int sp = d->memory_space;
+    LP_TRY(copy_in(h, h->rp, d->row_ptr, sizeof(int64_t) * (size_t)(m + 1), sp));
+    LP_TRY(copy_in(h, h->ci, d->col_idx, sizeof(int32_t) * (size_t)nnz, sp));
+    LP_TRY(copy_in(h, h->val0, d->vals, sizeof(double) * (size_t)nnz, sp));
+    LP_TRY(copy_in(h, h->sense, d->sense, (size_t)m, sp));
+    LP_TRY(copy_in(h, h->c0, d->c, sizeof(double) * (size_t)n, sp));
+    LP_TRY(copy_in(h, h->q0, d->q, sizeof(double) * (size_t)m, sp));
+    LP_TRY(copy_in(h, h->l0, d->l, sizeof(double) * (size_t)n, sp));
+    LP_TRY(copy_in(h, h->u0, d->u, sizeof(double) * (size_t)n, sp));
+
+    // validation on the device
+    int* flags = reinterpret_cast<int*>(h->scratch);
+    LP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), h->stream));
+    k_validate<<<grid_for(std::max({m, n, nnz}), 256, 4096), 256, 0, h->stream>>>(
+        m, n, nnz, h->rp, h->ci, h->val0, h->sense, h->c0, h->q0, h->l0, h->u0, flags);
+    LP_CUDA_TRY(cudaGetLastError());
+    int hflags = 0;
+    LP_CUDA_TRY(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (hflags) return LP_INVALID_ARGUMENT;
+
+    // host copy of row_ptr for the row-block scheduler
+    h->h_rp.resize((size_t)m + 1);
+    LP_CUDA_TRY(cudaMemcpyAsync(h->h_rp.data(), h->rp, sizeof(int64_t) * (size_t)(m + 1),
+                                cudaMemcpyDeviceToHost, h->stream));
+
+    // transpose: histogram, host scan, atomic scatter, per-segment sort
+    const int gm = grid_for(m * 32, 256);
+    k_row_of_nnz<<<gm, 256, 0, h->stream>>>(m, h->rp, h->krow);
+    int64_t* cnt = reinterpret_cast<int64_t*>(h->scratch);
+    LP_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (size_t)n, h->stream));
+    k_col_count<<<grid_for(nnz, 256, 8192), 256, 0, h->stream>>>(nnz, h->ci, cnt);
+    LP_CUDA_TRY(cudaGetLastError());
+    std::vector<int64_t> hc((size_t)n);
+    LP_CUDA_TRY(cudaMemcpyAsync(hc.data(), cnt, sizeof(int64_t) * (size_t)n,
+                                cudaMemcpyDeviceToHost, h->stream));
+    LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->h_trp.assign((size_t)n + 1, 0);
+    std::vector<int32_t> long_segs;
+    int64_t max_long = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        h->h_trp[(size_t)j + 1] = h->h_trp[(size_t)j] + hc[(size_t)j];
+        if (hc[(size_t)j] > 32) {
+            long_segs.push_back((int32_t)j);
+            max_long = std::max(max_long, hc[(size_t)j]);
+        }
+    }
+    LP_CUDA_TRY(cudaMemcpyAsync(h->trp, h->h_trp.data(), sizeof(int64_t) * (size_t)(n + 1),
+                                cudaMemcpyHostToDevice, h->stream));
+    unsigned long long* cursor = reinterpret_cast<unsigned long long*>(h->scratch);
+    LP_CUDA_TRY(cudaMemcpyAsync(cursor, h->trp, sizeof(int64_t) * (size_t)n,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    k_scatter_t<<<grid_for(nnz, 256, 8192), 256, 0, h->stream>>>(nnz, h->ci, cursor, h->tperm);
+    k_sort_short<<<grid_for(n, 256), 256, 0, h->stream>>>(n, h->trp, h->tperm);
+    LP_CUDA_TRY(cudaGetLastError());
+    if (!long_segs.empty()) {
+        int32_t* segs = nullptr;
+        int32_t* gscr = nullptr;
+        // segment list after the global scratch area (2 * nnz ints)
+        LP_TRY(dev_alloc_n(h, &segs, long_segs.size()));
+        LP_TRY(dev_alloc_n(h, &gscr, 2 * pad8(nnz)));
+        LP_CUDA_TRY(cudaMemcpyAsync(segs, long_segs.data(), sizeof(int32_t) * long_segs.size(),
+                                    cudaMemcpyHostToDevice, h->stream));
+        const int smem_cap = 8192;
+        LP_CUDA_TRY(cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_cap * (int)sizeof(int32_t)));
+        k_sort_long<<<(int)long_segs.size(), 512, smem_cap * sizeof(int32_t), h->stream>>>(
+            segs, h->trp, h->tperm, gscr, smem_cap);
+        LP_CUDA_TRY(cudaGetLastError());
+        LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        // the scratch lists are not needed after the sort
+        for (auto it = h->allocs.begin(); it != h->allocs.end();) {
+            if (it->p == segs || it->p == gscr) {
+                cudaFree(it->p);
+                it = h->allocs.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+    LP_CUDA_TRY(cudaMemsetAsync(h->tci, 0, pad8(nnz) * sizeof(int32_t), h->stream));
+    k_fill_tci<<<grid_for(nnz, 256, 8192), 256, 0, h->stream>>>(nnz, h->tperm, h->krow, h->tci);
+    LP_CUDA_TRY(cudaGetLastError());
+
+    // unscaled norms for the relative termination criteria (Section 2.3.2)
+    double s = 0.0;
+    LP_TRY(sum_of_squares(h, h->q0, m, &s));
+    h->qnorm = std::sqrt(s);
+    LP_TRY(sum_of_squares(h, h->c0, n, &s));
+    h->cnorm = std::sqrt(s);
+    return LP_OK;
+}
+
+// Algorithm 3 (+ optional Pock-Chambolle) into e64.val and R, C, the scaled
+// vectors e64.c/q/l/u and the scaled transpose e64.tval; then Algorithm 2.
+lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
+{
+    const int64_t m = h->m, n = h->n, nnz = h->nnz;
+    Engine<double>& E = h->e64;
+    cudaStream_t st = h->stream;
+    LP_CUDA_TRY(cudaMemcpyAsync(E.val, h->val0, pad8(nnz) * sizeof(double),
+                                cudaMemcpyDeviceToDevice, st));
+    k_fill<double><<<grid_for(m), 256, 0, st>>>(h->R, m, 1.0);
+    k_fill<double><<<grid_for(n), 256, 0, st>>>(h->C, n, 1.0);
+    double* rn = h->scratch;
+    double* cn = h->scratch + m;
+    unsigned long long* dev = reinterpret_cast<unsigned long long*>(h->scratch + m + n);
+    for (int it = 0; it < o->ruiz_iters; ++it) {
+        k_row_inf<<<grid_for(m * 32), 256, 0, st>>>(m, h->rp, E.val, rn);
+        LP_CUDA_TRY(cudaMemsetAsync(cn, 0, sizeof(double) * (size_t)n, st));
+        k_col_inf<<<grid_for(nnz, 256, 8192), 256, 0, st>>>(
+            nnz, h->ci, E.val, reinterpret_cast<unsigned long long*>(cn));
+        LP_CUDA_TRY(cudaMemsetAsync(dev, 0, sizeof(unsigned long long), st));
+        k_ruiz_dev<<<grid_for(m + n, 256, 4096), 256, 0, st>>>(m, n, rn, cn, dev);
+        LP_CUDA_TRY(cudaGetLastError());
+        unsigned long long hdev = 0;
+        LP_CUDA_TRY(cudaMemcpyAsync(&hdev, dev, sizeof(hdev), cudaMemcpyDeviceToHost, st));
+        LP_CUDA_TRY(cudaStreamSynchronize(st));
+        double dv;
+        std::memcpy(&dv, &hdev, sizeof(dv));
+        if (dv <= o->ruiz_tol) break;
+        k_ruiz_factors<<<grid_for(m), 256, 0, st>>>(m, rn, h->R);
+        k_ruiz_factors<<<grid_for(n), 256, 0, st>>>(n, cn, h->C);
+        k_scale_vals<<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, h->krow, h->ci, rn, cn, E.val);
+        LP_CUDA_TRY(cudaGetLastError());
+    }
+    if (o->pock_chambolle) {
+        k_pc_sums<<<grid_for(m + n), 256, 0, st>>>(m, n, h->rp, h->trp, h->tperm, E.val, rn, cn);
+        k_ruiz_factors<<<grid_for(m), 256, 0, st>>>(m, rn, h->R);
+        k_ruiz_factors<<<grid_for(n), 256, 0, st>>>(n, cn, h->C);
+        k_scale_vals<<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, h->krow, h->ci, rn, cn, E.val);
+        LP_CUDA_TRY(cudaGetLastError());
+    }
+    k_scale_vectors<<<grid_for(m + n), 256, 0, st>>>(m, n, h->R, h->C, h->c0, h->q0, h->l0, h->u0,
+                                                     E.c, E.q, E.l, E.u);
+    LP_CUDA_TRY(cudaMemsetAsync(E.tval, 0, pad8(nnz) * sizeof(double), st));
+    k_gather_cast<double><<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, h->tperm, E.val, E.tval);
+    LP_CUDA_TRY(cudaGetLastError());
+
+    // Algorithm 2 on K~: b = 1; repeat b <- K~^T (K~ b), b <- b / ||b||; ||K~ b||
+    double* b = E.XA;          // n
+    double* t = E.KXA;         // m
+    double* part = h->scratch;  // partials of ||b||^2 (ntblk) / ||t||^2 (nblk)
+    int* go = reinterpret_cast<int*>(h->scratch + std::max(E.nblk, E.ntblk) + 8);
+    k_fill<double><<<grid_for(n), 256, 0, st>>>(b, n, 1.0);
+    LP_CUDA_TRY(cudaMemsetAsync(go, 0, sizeof(int), st));
+    k_fill<int><<<1, 32, 0, st>>>(go, 1, 1);
+    for (int it = 0; it < o->power_iters; ++it) {
+        EpiStore<double> e1{b, t, nullptr, nullptr, go};
+        k_spmv<double, EpiStore<double>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e1);
+        EpiStore<double> e2{t, b, nullptr, part, go};
+        k_spmv<double, EpiStore<double>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, e2);
+        k_pow_normalize<<<1, kCtlNT, 0, st>>>(n, b, part, E.ntblk, go);
+        LP_CUDA_TRY(cudaGetLastError());
+    }
+    EpiStore<double> e3{b, t, nullptr, part, nullptr};
+    k_spmv<double, EpiStore<double>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e3);
+    k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.nblk, part + E.nblk + 4);
+    LP_CUDA_TRY(cudaGetLastError());
+    double s2 = 0.0;
+    LP_CUDA_TRY(cudaMemcpyAsync(&s2, part + E.nblk + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LP_CUDA_TRY(cudaStreamSynchronize(st));
+    *normK = std::sqrt(s2);
+    return LP_OK;
+}
+
+// Allocation, schedules and (for T = float) the FP32 casts of the scaled data.
+template <typename T>
+lp_status setup_engine(Handle* h, const lp_opts* o)
+{
+    (void)o;
+    const int64_t m = h->m, n = h->n, nnz = h->nnz;
+    Engine<T>& E = engine_of<T>(h);
+    if (!E.ready) {
+        const int cap = Cap<T>::value;
+        std::vector<int32_t> bk = make_row_blocks(h->h_rp.data(), m, cap, kNT);
+        std::vector<int32_t> bt = make_row_blocks(h->h_trp.data(), n, cap, kNT);
+        E.nblk = (int)bk.size() - 1;
+        E.ntblk = (int)bt.size() - 1;
+        LP_TRY(dev_alloc_n(h, &E.brow, bk.size()));
+        LP_TRY(dev_alloc_n(h, &E.bcol, bt.size()));
+        LP_CUDA_TRY(cudaMemcpyAsync(E.brow, bk.data(), bk.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, h->stream));
+        LP_CUDA_TRY(cudaMemcpyAsync(E.bcol, bt.data(), bt.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, h->stream));
+        LP_TRY(dev_alloc_n(h, &E.val, pad8(nnz)));
+        LP_TRY(dev_alloc_n(h, &E.tval, pad8(nnz)));
+        LP_CUDA_TRY(cudaMemsetAsync(E.val, 0, pad8(nnz) * sizeof(T), h->stream));
+        LP_CUDA_TRY(cudaMemsetAsync(E.tval, 0, pad8(nnz) * sizeof(T), h->stream));
+        T** vn[] = {&E.c, &E.l, &E.u, &E.X[0], &E.X[1], &E.KTY[0], &E.KTY[1],
+                    &E.XS, &E.XA, &E.KTYA, &E.XANC};
+        for (T** p : vn) LP_TRY(dev_alloc_n(h, p, (size_t)n));
+        T** vm[] = {&E.q, &E.Y[0], &E.Y[1], &E.KX[0], &E.KX[1], &E.YS, &E.YA, &E.KXA, &E.YANC};
+        for (T** p : vm) LP_TRY(dev_alloc_n(h, p, (size_t)m));
+        LP_TRY(dev_alloc_n(h, &E.partD, (size_t)E.nblk + 8));
+        LP_TRY(dev_alloc_n(h, &E.partT, 2 * (size_t)E.ntblk + 8));
+        LP_TRY(dev_alloc_n(h, &E.partR, 8 * (size_t)kEWGrid));
+        LP_TRY(dev_alloc_n(h, &E.partC, 10 * (size_t)kEWGrid));
+        LP_TRY(dev_alloc_n(h, &E.ctrl, 1));
+        E.ready = true;
+    }
+    if (std::is_same<T, float>::value) {
+        const Engine<double>& D = h->e64;
+        cudaStream_t st = h->stream;
+        k_gather_cast<T><<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, nullptr, D.val, E.val);
+        k_gather_cast<T><<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, h->tperm, D.val, E.tval);
+        k_gather_cast<T><<<grid_for(n), 256, 0, st>>>(n, nullptr, D.c, E.c);
+        k_gather_cast<T><<<grid_for(n), 256, 0, st>>>(n, nullptr, D.l, E.l);
+        k_gather_cast<T><<<grid_for(n), 256, 0, st>>>(n, nullptr, D.u, E.u);
+        k_gather_cast<T><<<grid_for(m), 256, 0, st>>>(m, nullptr, D.q, E.q);
+        LP_CUDA_TRY(cudaGetLastError());
+    }
+    return LP_OK;
+}
+
+template lp_status setup_engine<double>(Handle*, const lp_opts*);
+template lp_status setup_engine<float>(Handle*, const lp_opts*);
+
+}  // namespace pdhg

@@ -1,0 +1,839 @@
+// The restarted PDHG iteration on the device.
+//
+// One step attempt (Algorithm 1 with theta = 1, step sizes tau = eta / omega,
+// sigma = eta * omega, Section 2.3.1) is four launches:
+//   k_primal      x' = clamp(x - tau (c - K^T y), l, u)        (K^T y kept from the last step)
+//   k_spmv<Dual>  K x', then y' = proj_Y(y + sigma (q - (2 K x' - K x)))  (K x kept)
+//   k_spmv<PrT>   K^T y' and the Algorithm 5 terms ||dx||^2, dx . (K^T y' - K^T y)
+//   k_step_ctrl   accept / reject (Algorithm 5), swap the double buffers
+// Every check_every accepted iterations the check launches run: averages
+// (Section 2.4.2), their products, FP64 KKT reductions, the candidate, the
+// termination test on the unscaled problem (Section 2.3.2), the three restart
+// criteria and the primal-weight update (Algorithm 4).  The whole loop is a CUDA
+// graph whose body is (check_every + spare) attempt slots plus the check, inside
+// a conditional WHILE node; k_set_cond writes the loop condition on the device.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "spmv.cuh"
+
+namespace pdhg {
+
+// ------------------------------------------------------------------ step kernels
+
+template <typename T>
+__global__ void __launch_bounds__(kEW)
+k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0,
+         const T* __restrict__ kty1, const T* __restrict__ c, const T* __restrict__ l,
+         const T* __restrict__ u, T* xs, int64_t n)
+{
+    if (ctrl->skip) return;
+    const int cur = ctrl->cur;
+    const T tau = (T)(ctrl->eta / ctrl->omega);
+    const T pw = (T)ctrl->pend_w;
+    const T* x = cur ? x1 : x0;
+    T* xn = cur ? x0 : x1;
+    const T* kty = cur ? kty1 : kty0;
+    for (int64_t j = (int64_t)blockIdx.x * kEW + threadIdx.x; j < n; j += (int64_t)gridDim.x * kEW) {
+        const T xj = x[j];
+        if (pw != T(0)) xs[j] += pw * xj;
+        T v = xj - tau * (c[j] - kty[j]);
+        const T lo = l[j], hi = u[j];
+        if (v < lo) v = lo;
+        if (v > hi) v = hi;
+        xn[j] = v;
+    }
+}
+
+// K x' SpMV + dual step: y' = proj_Y(y + sigma (q - (2 K x' - K x)))
+template <typename T>
+struct EpiDual {
+    const Ctrl* ctrl;
+    const T* xs0; const T* xs1;     // X[0], X[1]
+    T* y0; T* y1; T* kx0; T* kx1;
+    T* ys;
+    const T* q;
+    const uint8_t* sense;
+    double* part;
+    int cur; T sigma; T pw; int adapt;
+    struct Acc { double dy2 = 0.0; };
+    __device__ bool begin() {
+        if (ctrl->skip) return false;
+        cur = ctrl->cur;
+        sigma = (T)(ctrl->eta * ctrl->omega);
+        pw = (T)ctrl->pend_w;
+        adapt = ctrl->adaptive;
+        return true;
+    }
+    __device__ const T* xin() const { return cur ? xs0 : xs1; }   // x' lives in the other half
+    __device__ void row(int i, T kxn, Acc& a) const {
+        const T* y = cur ? y1 : y0;
+        T* yn = cur ? y0 : y1;
+        const T* kx = cur ? kx1 : kx0;
+        T* kxo = cur ? kx0 : kx1;
+        const T yi = y[i];
+        if (pw != T(0)) ys[i] += pw * yi;
+        T v = yi + sigma * (q[i] - (T(2) * kxn - kx[i]));
+        if (sense[i] && v < T(0)) v = T(0);
+        yn[i] = v;
+        kxo[i] = kxn;
+        const double d = (double)v - (double)yi;
+        a.dy2 += d * d;
+    }
+    __device__ void finish(Acc& a) const {
+        if (adapt) {
+            const double t[1] = {a.dy2};
+            block_partials<1, kNT>(t, part, gridDim.x);
+        }
+    }
+};
+
+// K^T y' SpMV + Algorithm 5 terms
+template <typename T>
+struct EpiPrimalT {
+    const Ctrl* ctrl;
+    const T* ys0; const T* ys1;     // Y[0], Y[1]
+    const T* x0; const T* x1;
+    T* kty0; T* kty1;
+    double* part;
+    int cur; int adapt;
+    struct Acc { double dx2 = 0.0, inter = 0.0; };
+    __device__ bool begin() {
+        if (ctrl->skip) return false;
+        cur = ctrl->cur;
+        adapt = ctrl->adaptive;
+        return true;
+    }
+    __device__ const T* xin() const { return cur ? ys0 : ys1; }   // y'
+    __device__ void row(int j, T ktyn, Acc& a) const {
+        T* kto = cur ? kty0 : kty1;
+        kto[j] = ktyn;
+        if (adapt) {
+            const T* x = cur ? x1 : x0;
+            const T* xn = cur ? x0 : x1;
+            const T* kt = cur ? kty1 : kty0;
+            const double dx = (double)xn[j] - (double)x[j];
+            a.dx2 += dx * dx;
+            a.inter += dx * ((double)ktyn - (double)kt[j]);
+        }
+    }
+    __device__ void finish(Acc& a) const {
+        if (adapt) {
+            const double t[2] = {a.dx2, a.inter};
+            block_partials<2, kNT>(t, part, gridDim.x);
+        }
+    }
+};
+
+// Algorithm 5 decision (or the plain swap of a fixed step).  The paper's k is
+// read as the 1-based index of the iteration being taken.
+__global__ void __launch_bounds__(kCtlNT)
+k_step_ctrl(Ctrl* ctrl, const double* partD, int nD, const double* partT, int nT)
+{
+    if (ctrl->skip) return;
+    double dy2 = 0.0, dx2 = 0.0, inter = 0.0;
+    const int adapt = ctrl->adaptive;
+    if (adapt) {
+        dy2 = block_sum_array<kCtlNT>(partD, nD);
+        dx2 = block_sum_array<kCtlNT>(partT, nT);
+        inter = block_sum_array<kCtlNT>(partT + nT, nT);
+    }
+    if (threadIdx.x != 0) return;
+    const double eta = ctrl->eta, omega = ctrl->omega;
+    bool accept = true;
+    double eta_next = eta;
+    if (adapt) {
+        const double movement = omega * dx2 + dy2 / omega;
+        const double eta_bar = inter != 0.0 ? movement / (2.0 * fabs(inter)) : INFINITY;
+        const double kp1 = (double)(ctrl->k + 1) + 1.0;
+        const double e1 = (1.0 - pow(kp1, -0.3)) * eta_bar;
+        const double e2 = (1.0 + pow(kp1, -0.6)) * eta;
+        eta_next = e1 < e2 ? e1 : e2;
+        accept = eta <= eta_bar;
+        if (!isfinite(movement) || isnan(inter)) {
+            ctrl->status = LP_NUMERICAL_ERROR;
+            ctrl->done = 1;
+            ctrl->skip = 1;
+            return;
+        }
+    }
+    ctrl->attempts += 1;
+    if (accept) {
+        ctrl->cur ^= 1;
+        ctrl->k += 1;
+        ctrl->epoch_k += 1;
+        ctrl->pend_w = eta;
+        ctrl->W += eta;
+        ctrl->rejects = 0;
+    } else {
+        ctrl->pend_w = 0.0;
+        ctrl->rejects += 1;
+    }
+    ctrl->eta = eta_next;
+    if (ctrl->k % ctrl->check_every == 0 || ctrl->k >= ctrl->max_iters) {
+        ctrl->want_check = 1;
+        ctrl->skip = 1;
+    }
+    // guards that end the device loop even if no check is reached: Algorithm 5
+    // accepts once eta <= 1/||K||, so a long run of rejections means broken
+    // arithmetic; the wall-clock limit is also enforced per attempt.
+    if (ctrl->rejects > 1000 || !(eta_next > 0.0)) {
+        ctrl->status = LP_NUMERICAL_ERROR;
+        ctrl->done = 1;
+        ctrl->skip = 1;
+        ctrl->want_check = 0;
+    } else if ((double)(global_ns() - (unsigned long long)ctrl->t0_ns) > ctrl->time_limit_ns) {
+        ctrl->status = LP_TIME_LIMIT;
+        ctrl->done = 1;
+        ctrl->skip = 1;
+        ctrl->want_check = 0;
+    }
+}
+
+// ------------------------------------------------------------------ check kernels
+
+// Adds the pending iterate to the sums and materialises the averages.
+template <typename T>
+__global__ void __launch_bounds__(kEW)
+k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y0, const T* y1,
+             T* xs, T* ys, T* xa, T* ya, int64_t n, int64_t m)
+{
+    if (!ctrl->want_check) return;
+    const int cur = ctrl->cur;
+    const T pw = (T)ctrl->pend_w;
+    const double W = ctrl->W;
+    const T* x = cur ? x1 : x0;
+    const T* y = cur ? y1 : y0;
+    for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < n + m;
+         t += (int64_t)gridDim.x * kEW) {
+        if (t < n) {
+            T s = xs[t];
+            if (pw != T(0)) { s += pw * x[t]; xs[t] = s; }
+            xa[t] = W > 0.0 ? (T)((double)s / W) : T(0);
+        } else {
+            const int64_t i = t - n;
+            T s = ys[i];
+            if (pw != T(0)) { s += pw * y[i]; ys[i] = s; }
+            ya[i] = W > 0.0 ? (T)((double)s / W) : T(0);
+        }
+    }
+}
+
+// Row side of the KKT terms for the current point and the average:
+// [0] sum r_s^2  [1] sum (r_s / R)^2  [2] q~^T y  [3] ||y - y_anchor||^2   (current)
+// [4..7] the same for the average.  r = q~ - K~ x, clamped at 0 on >= rows.
+template <typename T>
+__global__ void __launch_bounds__(kEW)
+k_check_rows(const Ctrl* __restrict__ ctrl, const T* y0, const T* y1, const T* kx0,
+             const T* kx1, const T* ya, const T* kxa, const T* yanc, const T* q,
+             const uint8_t* sense, const double* R, int64_t m, double* part)
+{
+    if (!ctrl->want_check) return;
+    const int cur = ctrl->cur;
+    const T* y = cur ? y1 : y0;
+    const T* kx = cur ? kx1 : kx0;
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * kEW + threadIdx.x; i < m; i += (int64_t)gridDim.x * kEW) {
+        const double qi = (double)q[i], Ri = R[i];
+        const bool ge = sense[i] != 0;
+        const double ya_ = (double)yanc[i];
+        double r = qi - (double)kx[i];
+        if (ge && r < 0.0) r = 0.0;
+        v[0] += r * r;
+        v[1] += (r / Ri) * (r / Ri);
+        const double yc = (double)y[i];
+        v[2] += qi * yc;
+        v[3] += (yc - ya_) * (yc - ya_);
+        double ra = qi - (double)kxa[i];
+        if (ge && ra < 0.0) ra = 0.0;
+        v[4] += ra * ra;
+        v[5] += (ra / Ri) * (ra / Ri);
+        const double yv = (double)ya[i];
+        v[6] += qi * yv;
+        v[7] += (yv - ya_) * (yv - ya_);
+    }
+    block_partials<8, kEW>(v, part, gridDim.x);
+}
+
+// Column side: [0] sum d_s^2  [1] sum (d_s / C)^2  [2] c~^T x
+// [3] l~^T lambda^+ + u~^T lambda^-  [4] ||x - x_anchor||^2  (current), [5..9] average;
+// d = v - lambda, v = c~ - K~^T y, lambda = proj_Lambda(v).
+template <typename T>
+__global__ void __launch_bounds__(kEW)
+k_check_cols(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* kty0,
+             const T* kty1, const T* xa, const T* ktya, const T* xanc, const T* c,
+             const T* l, const T* u, const double* C, int64_t n, double* part)
+{
+    if (!ctrl->want_check) return;
+    const int cur = ctrl->cur;
+    const T* x = cur ? x1 : x0;
+    const T* kty = cur ? kty1 : kty0;
+    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t j = (int64_t)blockIdx.x * kEW + threadIdx.x; j < n; j += (int64_t)gridDim.x * kEW) {
+        const double cj = (double)c[j], lj = (double)l[j], uj = (double)u[j], Cj = C[j];
+        const bool lf = isfinite(lj), uf = isfinite(uj);
+        const double xan = (double)xanc[j];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const double vj = cj - (double)(side ? ktya[j] : kty[j]);
+            double lam;
+            if (!lf && !uf) lam = 0.0;
+            else if (!lf) lam = vj < 0.0 ? vj : 0.0;
+            else if (!uf) lam = vj > 0.0 ? vj : 0.0;
+            else lam = vj;
+            const double d = vj - lam;
+            const double xv = (double)(side ? xa[j] : x[j]);
+            double lt = 0.0;
+            if (lam > 0.0) lt += lj * lam;
+            if (lam < 0.0) lt += uj * lam;
+            v[5 * side + 0] += d * d;
+            v[5 * side + 1] += (d / Cj) * (d / Cj);
+            v[5 * side + 2] += cj * xv;
+            v[5 * side + 3] += lt;
+            v[5 * side + 4] += (xv - xan) * (xv - xan);
+        }
+    }
+    block_partials<10, kEW>(v, part, gridDim.x);
+}
+
+// KKT_omega (Section 2.4.2), candidate, termination (Section 2.3.2, unscaled),
+// restart criteria (Section 2.4.2) and Algorithm 4.
+__global__ void __launch_bounds__(kCtlNT)
+k_check_ctrl(Ctrl* ctrl, const double* partR, const double* partC, int nparts,
+             lp_trace_rec* trace)
+{
+    if (!ctrl->want_check) return;
+    double r[8], cc[10];
+    for (int q = 0; q < 8; ++q) r[q] = block_sum_array<kCtlNT>(partR + (size_t)q * nparts, nparts);
+    for (int q = 0; q < 10; ++q) cc[q] = block_sum_array<kCtlNT>(partC + (size_t)q * nparts, nparts);
+    if (threadIdx.x != 0) return;
+    const double w = ctrl->omega;
+    // current
+    const double pobj_c = cc[2], dobj_c = r[2] + cc[3];
+    const double gap_c = dobj_c - pobj_c;
+    const double kkt_c = sqrt(w * w * r[0] + cc[0] / (w * w) + gap_c * gap_c);
+    // average
+    const double pobj_a = cc[7], dobj_a = r[6] + cc[8];
+    const double gap_a = dobj_a - pobj_a;
+    const double kkt_a = ctrl->W > 0.0 ? sqrt(w * w * r[4] + cc[5] / (w * w) + gap_a * gap_a)
+                                       : INFINITY;
+    const int cand_avg = !(kkt_c < kkt_a);
+    const double kkt_cand = cand_avg ? kkt_a : kkt_c;
+    const double pobj = cand_avg ? pobj_a : pobj_c;
+    const double dobj = cand_avg ? dobj_a : dobj_c;
+    const double pres_u = sqrt(cand_avg ? r[5] : r[1]);
+    const double dres_u = sqrt(cand_avg ? cc[6] : cc[1]);
+    const double rel_gap = fabs(dobj - pobj) / (1.0 + fabs(dobj) + fabs(pobj));
+    const double rel_pres = pres_u / (1.0 + ctrl->qnorm);
+    const double rel_dres = dres_u / (1.0 + ctrl->cnorm);
+    const int converged = rel_gap <= ctrl->tol && rel_pres <= ctrl->tol && rel_dres <= ctrl->tol;
+    const int first = ctrl->first;
+    int restart = 0;
+    if (first) {
+        ctrl->kkt_anchor = kkt_cand;
+    } else if (!converged && ctrl->restarts_on) {
+        const int c1 = kkt_cand <= ctrl->beta_s * ctrl->kkt_anchor;
+        const int c2 = kkt_cand <= ctrl->beta_n * ctrl->kkt_anchor && kkt_cand > ctrl->kkt_prev;
+        const int c3 = (double)ctrl->epoch_k > ctrl->beta_a * (double)ctrl->k;
+        restart = c1 || c2 || c3;
+    }
+    double omega = w;
+    if (restart) {
+        if (ctrl->pwu) {
+            const double ddx = sqrt(cand_avg ? cc[9] : cc[4]);
+            const double ddy = sqrt(cand_avg ? r[7] : r[3]);
+            if (ddx > ctrl->eps_zero && ddy > ctrl->eps_zero)
+                omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(w));
+        }
+        ctrl->kkt_anchor = kkt_cand;
+        ctrl->kkt_prev = INFINITY;
+        ctrl->epoch_k = 0;
+        ctrl->W = 0.0;
+        ctrl->restarts += 1;
+    } else if (!first) {
+        ctrl->kkt_prev = kkt_cand;
+    }
+    ctrl->omega = omega;
+    ctrl->restart = restart;
+    ctrl->cand_avg = cand_avg;
+    ctrl->kkt_cur = kkt_c;
+    ctrl->kkt_avg = kkt_a;
+    ctrl->kkt_cand = kkt_cand;
+    ctrl->rel_gap = rel_gap;
+    ctrl->rel_pres = rel_pres;
+    ctrl->rel_dres = rel_dres;
+    ctrl->pobj = pobj;
+    ctrl->dobj = dobj;
+    ctrl->pend_w = 0.0;
+    ctrl->first = 0;
+    if (trace && ctrl->trace_len < ctrl->trace_cap) {
+        lp_trace_rec* t = trace + ctrl->trace_len;
+        t->k = (double)ctrl->k;
+        t->attempts = (double)ctrl->attempts;
+        t->restart = restart;
+        t->cand_is_avg = cand_avg;
+        t->omega = omega;
+        t->eta = ctrl->eta;
+        t->kkt_cur = kkt_c;
+        t->kkt_avg = kkt_a;
+        t->rel_gap = rel_gap;
+        t->rel_pres = rel_pres;
+        t->rel_dres = rel_dres;
+        t->kkt_cand = kkt_cand;
+    }
+    ctrl->trace_len += 1;
+    const bool bad = !isfinite(kkt_c) || isnan(rel_gap) || isnan(rel_pres) || isnan(rel_dres);
+    if (bad) {
+        ctrl->status = LP_NUMERICAL_ERROR;
+        ctrl->done = 1;
+    } else if (converged) {
+        ctrl->status = LP_OPTIMAL;
+        ctrl->done = 1;
+    } else if (ctrl->k >= ctrl->max_iters) {
+        ctrl->status = LP_ITERATION_LIMIT;
+        ctrl->done = 1;
+    } else if ((double)(global_ns() - (unsigned long long)ctrl->t0_ns) > ctrl->time_limit_ns) {
+        ctrl->status = LP_TIME_LIMIT;
+        ctrl->done = 1;
+    }
+}
+
+// At a restart the iterate becomes the candidate and the anchor; sums reset.
+template <typename T>
+__global__ void __launch_bounds__(kEW)
+k_restart_apply(const Ctrl* __restrict__ ctrl, T* x0, T* x1, T* y0, T* y1, T* kx0, T* kx1,
+                T* kty0, T* kty1, const T* xa, const T* ya, const T* kxa, const T* ktya,
+                T* xanc, T* yanc, T* xs, T* ys, int64_t n, int64_t m)
+{
+    if (!ctrl->want_check || !ctrl->restart) return;
+    const int cur = ctrl->cur, avg = ctrl->cand_avg;
+    T* x = cur ? x1 : x0;
+    T* y = cur ? y1 : y0;
+    T* kx = cur ? kx1 : kx0;
+    T* kty = cur ? kty1 : kty0;
+    for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < n + m;
+         t += (int64_t)gridDim.x * kEW) {
+        if (t < n) {
+            T v = x[t];
+            if (avg) {
+                v = xa[t];
+                x[t] = v;
+                kty[t] = ktya[t];
+            }
+            xanc[t] = v;
+            xs[t] = T(0);
+        } else {
+            const int64_t i = t - n;
+            T v = y[i];
+            if (avg) {
+                v = ya[i];
+                y[i] = v;
+                kx[i] = kxa[i];
+            }
+            yanc[i] = v;
+            ys[i] = T(0);
+        }
+    }
+}
+
+__global__ void k_set_cond(Ctrl* ctrl, cudaGraphConditionalHandle handle, int use_handle)
+{
+    ctrl->want_check = 0;
+    ctrl->restart = 0;
+    ctrl->skip = ctrl->done;
+    if (use_handle) cudaGraphSetConditional(handle, ctrl->done ? 0u : 1u);
+}
+
+// Start point (reading: x = proj_X(0), y = 0; or the warm start) in scaled space.
+template <typename T>
+__global__ void k_init_state(T* x, T* y, T* xanc, T* yanc, T* xs, T* ys, const T* l, const T* u,
+                             const uint8_t* sense, const double* R, const double* C,
+                             const double* wx_scaled, const double* wy_scaled,
+                             const double* wx_user, const double* wy_user, int64_t n, int64_t m)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n + m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n) {
+            double v = 0.0;
+            if (wx_scaled) v = wx_scaled[t];
+            else if (wx_user) v = wx_user[t] / C[t];
+            T xv = (T)v;
+            if (xv < l[t]) xv = l[t];
+            if (xv > u[t]) xv = u[t];
+            x[t] = xv;
+            xanc[t] = xv;
+            xs[t] = T(0);
+        } else {
+            const int64_t i = t - n;
+            double v = 0.0;
+            if (wy_scaled) v = wy_scaled[i];
+            else if (wy_user) v = wy_user[i] / R[i];
+            if (sense[i] && v < 0.0) v = 0.0;
+            y[i] = (T)v;
+            yanc[i] = (T)v;
+            ys[i] = T(0);
+        }
+    }
+}
+
+// Unscaled candidate -> caller buffers (double).
+template <typename T>
+__global__ void k_extract(const Ctrl* ctrl, const T* x0, const T* x1, const T* y0, const T* y1,
+                          const T* xa, const T* ya, const double* R, const double* C,
+                          double* xo, double* yo, double* xs_scaled, double* ys_scaled,
+                          int64_t n, int64_t m)
+{
+    const int cur = ctrl->cur, avg = ctrl->cand_avg;
+    const T* x = avg ? xa : (cur ? x1 : x0);
+    const T* y = avg ? ya : (cur ? y1 : y0);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n + m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n) {
+            const double v = (double)x[t];
+            if (xo) xo[t] = C[t] * v;
+            if (xs_scaled) xs_scaled[t] = v;
+        } else {
+            const int64_t i = t - n;
+            const double v = (double)y[i];
+            if (yo) yo[i] = R[i] * v;
+            if (ys_scaled) ys_scaled[i] = v;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static inline int ew_grid(int64_t count)
+{
+    int64_t g = (count + kEW - 1) / kEW;
+    if (g < 1) g = 1;
+    if (g > kEWGrid) g = kEWGrid;
+    return (int)g;
+}
+
+__global__ void k_read_clock(unsigned long long* t) { *t = global_ns(); }
+
+template <typename T>
+static void launch_attempt(Handle* h, Engine<T>& E, cudaStream_t st)
+{
+    const int64_t n = h->n;
+    k_primal<T><<<ew_grid(n), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c, E.l,
+                                             E.u, E.XS, n);
+    EpiDual<T> ed{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS, E.q, h->sense,
+                  E.partD};
+    k_spmv<T, EpiDual<T>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, ed);
+    EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.partT};
+    k_spmv<T, EpiPrimalT<T>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, et);
+    k_step_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partD, E.nblk, E.partT, E.ntblk);
+}
+
+template <typename T>
+static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphConditionalHandle hd,
+                         int use_handle)
+{
+    const int64_t m = h->m, n = h->n;
+    k_check_prep<T><<<ew_grid(n + m), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.XS,
+                                                     E.YS, E.XA, E.YA, n, m);
+    const int* gate = &E.ctrl->want_check;
+    EpiStore<T> e1{E.XA, E.KXA, nullptr, nullptr, gate};
+    k_spmv<T, EpiStore<T>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e1);
+    EpiStore<T> e2{E.YA, E.KTYA, nullptr, nullptr, gate};
+    k_spmv<T, EpiStore<T>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, e2);
+    k_check_rows<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YA,
+                                             E.KXA, E.YANC, E.q, h->sense, h->R, m, E.partR);
+    k_check_cols<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.XA,
+                                             E.KTYA, E.XANC, E.c, E.l, E.u, h->C, n, E.partC);
+    k_check_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partR, E.partC, kEWGrid, E.trace);
+    k_restart_apply<T><<<ew_grid(n + m), kEW, 0, st>>>(
+        E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.KTY[0], E.KTY[1], E.XA, E.YA,
+        E.KXA, E.KTYA, E.XANC, E.YANC, E.XS, E.YS, n, m);
+    k_set_cond<<<1, 1, 0, st>>>(E.ctrl, hd, use_handle);
+}
+
+template <typename T>
+static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots)
+{
+    if (E.exec && E.graph_check_every == check_every && E.graph_slots == slots) return LP_OK;
+    if (E.exec) {
+        cudaGraphExecDestroy(E.exec);
+        E.exec = nullptr;
+    }
+    if (E.body_exec) {
+        cudaGraphExecDestroy(E.body_exec);
+        E.body_exec = nullptr;
+    }
+    cudaStream_t st = h->stream;
+    cudaGraph_t graph = nullptr;
+    LP_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle hd{};
+    cudaError_t ce = cudaGraphConditionalHandleCreate(&hd, graph, 1, cudaGraphCondAssignDefault);
+    bool conditional = ce == cudaSuccess;
+    cudaGraph_t body = nullptr;
+    if (conditional) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hd;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+        if (ce == cudaSuccess) body = cp.conditional.phGraph_out[0];
+        else conditional = false;
+    }
+    (void)cudaGetLastError();
+    if (conditional) {
+        LP_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+        for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st);
+        launch_check<T>(h, E, st, hd, 1);
+        cudaGraph_t captured = nullptr;
+        LP_CUDA_TRY(cudaStreamEndCapture(st, &captured));
+        LP_CUDA_TRY(cudaGraphInstantiate(&E.exec, graph, 0));
+        cudaGraphDestroy(graph);
+    } else {
+        cudaGraphDestroy(graph);
+        LP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st);
+        launch_check<T>(h, E, st, hd, 0);
+        cudaGraph_t g2 = nullptr;
+        LP_CUDA_TRY(cudaStreamEndCapture(st, &g2));
+        LP_CUDA_TRY(cudaGraphInstantiate(&E.body_exec, g2, 0));
+        cudaGraphDestroy(g2);
+    }
+    E.graph_conditional = conditional;
+    E.graph_check_every = check_every;
+    E.graph_slots = slots;
+    return LP_OK;
+}
+
+template <typename T>
+lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
+                    const double* wxs, const double* wys, const double* wxu, const double* wyu,
+                    int warm_space, long long k0, long long attempts0, long long restarts0,
+                    lp_trace_rec* trace_host, long long trace_cap_host, long long trace_off,
+                    Ctrl* out)
+{
+    Engine<T>& E = engine_of<T>(h);
+    const int64_t m = h->m, n = h->n;
+    cudaStream_t st = h->stream;
+    // warm start from the caller (unscaled) must be on the device
+    const double* dwx = nullptr;
+    const double* dwy = nullptr;
+    double* tmp = nullptr;
+    if (wxu || wyu) {
+        if (warm_space == LP_MEM_DEVICE) {
+            dwx = wxu;
+            dwy = wyu;
+        } else {
+            LP_TRY(dev_alloc_n(h, &tmp, (size_t)(n + m)));
+            if (wxu) LP_CUDA_TRY(cudaMemcpyAsync(tmp, wxu, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+            if (wyu) LP_CUDA_TRY(cudaMemcpyAsync(tmp + n, wyu, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+            dwx = wxu ? tmp : nullptr;
+            dwy = wyu ? tmp + n : nullptr;
+        }
+    }
+    k_init_state<T><<<ew_grid(n + m), kEW, 0, st>>>(E.X[0], E.Y[0], E.XANC, E.YANC, E.XS, E.YS,
+                                                     E.l, E.u, h->sense, h->R, h->C, wxs, wys,
+                                                     dwx, dwy, n, m);
+    EpiStore<T> e1{E.X[0], E.KX[0], nullptr, nullptr, nullptr};
+    k_spmv<T, EpiStore<T>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e1);
+    EpiStore<T> e2{E.Y[0], E.KTY[0], nullptr, nullptr, nullptr};
+    k_spmv<T, EpiStore<T>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, e2);
+    LP_CUDA_TRY(cudaGetLastError());
+
+    // device trace buffer
+    long long cap = trace_host ? std::max<long long>(0, trace_cap_host - trace_off) : 0;
+    if (cap > E.trace_cap) {
+        LP_TRY(dev_alloc_n(h, &E.trace, (size_t)cap));
+        E.trace_cap = cap;
+    }
+
+    Ctrl c;
+    std::memset(&c, 0, sizeof(c));
+    c.eta = eta0;
+    c.omega = omega0;
+    c.kkt_prev = INFINITY;
+    c.tol = o->tol;
+    c.beta_s = o->beta_sufficient;
+    c.beta_n = o->beta_necessary;
+    c.beta_a = o->beta_artificial;
+    c.eps_zero = o->eps_zero;
+    c.qnorm = h->qnorm;
+    c.cnorm = h->cnorm;
+    c.time_limit_ns = o->time_limit_s * 1e9;
+    c.k = k0;
+    c.attempts = attempts0;
+    c.restarts = restarts0;
+    c.max_iters = o->max_iters;
+    c.trace_len = 0;
+    c.trace_cap = cap;
+    c.status = kRunning;
+    c.first = 1;
+    c.want_check = 1;
+    c.skip = 1;
+    c.adaptive = o->adaptive_step ? 1 : 0;
+    c.pwu = o->primal_weight_update ? 1 : 0;
+    c.restarts_on = o->restarts ? 1 : 0;
+    c.check_every = o->check_every;
+    {
+        // the time origin is the device clock read now
+        unsigned long long* tns = reinterpret_cast<unsigned long long*>(h->scratch);
+        k_read_clock<<<1, 1, 0, st>>>(tns);
+        unsigned long long t0 = 0;
+        LP_CUDA_TRY(cudaMemcpyAsync(&t0, tns, sizeof(t0), cudaMemcpyDeviceToHost, st));
+        LP_CUDA_TRY(cudaStreamSynchronize(st));
+        c.t0_ns = (long long)t0;
+    }
+    LP_CUDA_TRY(cudaMemcpyAsync(E.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+
+    // the start-point check (KKT of z^0, anchor)
+    launch_check<T>(h, E, st, cudaGraphConditionalHandle{}, 0);
+    LP_CUDA_TRY(cudaGetLastError());
+
+    const int slots = o->check_every + (o->adaptive_step ? 4 : 0);
+    LP_TRY(build_graph<T>(h, E, o->check_every, slots));
+    if (E.graph_conditional) {
+        LP_CUDA_TRY(cudaGraphLaunch(E.exec, st));
+        LP_CUDA_TRY(cudaMemcpyAsync(out, E.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        LP_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        // fallback: host loop over body launches, reading the done flag each time
+        for (;;) {
+            LP_CUDA_TRY(cudaMemcpyAsync(out, E.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+            LP_CUDA_TRY(cudaStreamSynchronize(st));
+            if (out->done) break;
+            LP_CUDA_TRY(cudaGraphLaunch(E.body_exec, st));
+        }
+    }
+    if (trace_host && cap > 0) {
+        const long long got = std::min<long long>(out->trace_len, cap);
+        if (got > 0)
+            LP_CUDA_TRY(cudaMemcpyAsync(trace_host + trace_off, E.trace, sizeof(lp_trace_rec) * got,
+                                        cudaMemcpyDeviceToHost, st));
+        LP_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (tmp) {
+        for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+            if (it->p == tmp) {
+                cudaFree(tmp);
+                h->allocs.erase(it);
+                break;
+            }
+    }
+    return LP_OK;
+}
+
+// Writes the unscaled candidate to x / y (space: host or device), or, when
+// x_scaled_dev / y_scaled_dev are given, the scaled candidate in FP64.
+template <typename T>
+lp_status extract_solution_ex(Handle* h, double* x, double* y, int space, double* xs_dev,
+                              double* ys_dev)
+{
+    Engine<T>& E = engine_of<T>(h);
+    const int64_t m = h->m, n = h->n;
+    cudaStream_t st = h->stream;
+    double* dx = x;
+    double* dy = y;
+    double* tmp = nullptr;
+    if (space == LP_MEM_HOST && (x || y)) {
+        tmp = h->scratch;   // n + m doubles fit in scratch
+        dx = x ? tmp : nullptr;
+        dy = y ? tmp + n : nullptr;
+    }
+    k_extract<T><<<ew_grid(n + m), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.XA, E.YA,
+                                                  h->R, h->C, dx, dy, xs_dev, ys_dev, n, m);
+    LP_CUDA_TRY(cudaGetLastError());
+    if (tmp) {
+        if (x) LP_CUDA_TRY(cudaMemcpyAsync(x, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        if (y) LP_CUDA_TRY(cudaMemcpyAsync(y, tmp + n, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    }
+    LP_CUDA_TRY(cudaStreamSynchronize(st));
+    return LP_OK;
+}
+
+template <typename T>
+lp_status extract_solution(Handle* h, double* x, double* y, int space)
+{
+    return extract_solution_ex<T>(h, x, y, space, nullptr, nullptr);
+}
+
+template <typename T>
+lp_status profile_step(Handle* h, int reps, double* ms, double* bytes)
+{
+    Engine<T>& E = engine_of<T>(h);
+    if (!E.ready || reps <= 0) return LP_INVALID_ARGUMENT;
+    cudaStream_t st = h->stream;
+    const int64_t m = h->m, n = h->n, nnz = h->nnz;
+    // free-running state: no check, no stop
+    Ctrl c;
+    LP_CUDA_TRY(cudaMemcpyAsync(&c, E.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    LP_CUDA_TRY(cudaStreamSynchronize(st));
+    c.skip = 0;
+    c.want_check = 0;
+    c.done = 0;
+    c.max_iters = (long long)1 << 60;
+    c.check_every = 1 << 30;
+    LP_CUDA_TRY(cudaMemcpyAsync(E.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    cudaEvent_t ev[5];
+    for (auto& e : ev) LP_CUDA_TRY(cudaEventCreate(&e));
+    double acc[4] = {0, 0, 0, 0};
+    for (int r = 0; r < reps + 2; ++r) {
+        cudaEventRecord(ev[0], st);
+        k_primal<T><<<ew_grid(n), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c,
+                                                 E.l, E.u, E.XS, n);
+        cudaEventRecord(ev[1], st);
+        EpiDual<T> ed{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS, E.q, h->sense,
+                      E.partD};
+        k_spmv<T, EpiDual<T>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, ed);
+        cudaEventRecord(ev[2], st);
+        EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.partT};
+        k_spmv<T, EpiPrimalT<T>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, et);
+        cudaEventRecord(ev[3], st);
+        k_step_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partD, E.nblk, E.partT, E.ntblk);
+        cudaEventRecord(ev[4], st);
+        LP_CUDA_TRY(cudaGetLastError());
+        LP_CUDA_TRY(cudaEventSynchronize(ev[4]));
+        if (r >= 2) {
+            for (int k = 0; k < 4; ++k) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+                acc[k] += t;
+            }
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < 4; ++k) ms[k] = acc[k] / reps;
+    if (bytes) {
+        const double s = sizeof(T);
+        // primal: read x, c, l, u, K^T y, x-sum; write x', x-sum
+        bytes[0] = (double)n * 8 * s;
+        // K x' + dual: values + indices + row_ptr + gathered x' (once) + y, q, Kx, y-sum,
+        // sense read; y', Kx', y-sum written
+        bytes[1] = (double)nnz * (s + 4) + (double)(m + 1) * 8 + (double)n * s +
+                   (double)m * (7 * s + 1);
+        // K^T y' + step terms: values + indices + row_ptr + gathered y' (once);
+        // K^T y' written; x, x', K^T y read
+        bytes[2] = (double)nnz * (s + 4) + (double)(n + 1) * 8 + (double)m * s + (double)n * 4 * s;
+        bytes[3] = (double)(E.nblk + 2 * E.ntblk) * 8;
+    }
+    return LP_OK;
+}
+
+template lp_status run_solve<double>(Handle*, const lp_opts*, double, double, const double*,
+                                     const double*, const double*, const double*, int, long long,
+                                     long long, long long, lp_trace_rec*, long long, long long,
+                                     Ctrl*);
+template lp_status run_solve<float>(Handle*, const lp_opts*, double, double, const double*,
+                                    const double*, const double*, const double*, int, long long,
+                                    long long, long long, lp_trace_rec*, long long, long long,
+                                    Ctrl*);
+template lp_status extract_solution<double>(Handle*, double*, double*, int);
+template lp_status extract_solution<float>(Handle*, double*, double*, int);
+template lp_status extract_solution_ex<double>(Handle*, double*, double*, int, double*, double*);
+template lp_status extract_solution_ex<float>(Handle*, double*, double*, int, double*, double*);
+template lp_status profile_step<double>(Handle*, int, double*, double*);
+template lp_status profile_step<float>(Handle*, int, double*, double*);
+
+}  // namespace pdhg

@@ -346,3 +346,37 @@ def from_dense(K, sense, c, q, l, u, name: str = "dense") -> LP:
 
     return LP(m, n, row_ptr, cols.astype(np.int32), K[rows, cols].copy(),
               np.asarray(sense, dtype=np.uint8), vec(c), vec(q), vec(l), vec(u), name=name)
+
+
+def ragged_lp(seed: int = 7, m: int = 10000, n: int = 6000) -> LP:
+    """Planted LP whose row lengths hit every SpMV code path: empty rows,
+    1 / 31 / 32 / 33 nonzeros, rows around the shared-memory staging sizes
+    (2047..2049, 4095..4097, 4500, 5000), three dense columns (long rows of
+    K^T, about m/2 entries each) and an empty column 0."""
+    rng = np.random.default_rng(seed)
+    special = [0, 0, 1, 31, 32, 33, 1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097,
+               4500, 5000]
+    lengths = rng.integers(1, 12, m)
+    pos = rng.choice(m, len(special), replace=False)
+    lengths[pos] = special
+    rows = np.repeat(np.arange(m, dtype=np.int64), lengths)
+    cols = rng.integers(1, n, rows.shape[0])
+    row_ptr, col_idx = _csr_from_rows_cols(m, n, rows, cols, rng)
+    # three dense columns: append (i, j) for j in {5, 6, 7} on a quarter of the rows
+    keep_r = np.repeat(np.arange(m, dtype=np.int64), np.diff(row_ptr))
+    chunks = [np.flatnonzero(rng.random(m) < 0.5) for _ in range(3)]
+    extra_r = np.concatenate(chunks)
+    extra_c = np.concatenate([np.full(len(ch), j) for ch, j in zip(chunks, (5, 6, 7))])
+    rows = np.concatenate([keep_r, extra_r])
+    cols = np.concatenate([col_idx.astype(np.int64), extra_c])
+    key = rows * n + cols
+    key = np.unique(key)
+    rows, cols = key // n, key % n
+    keep = (cols != 0) & (rows != pos[0])      # empty column 0 and an empty row
+    rows, cols = rows[keep], cols[keep]
+    counts = np.bincount(rows, minlength=m).astype(np.int64)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    vals = rng.standard_normal(int(row_ptr[-1]))
+    sense = (rng.random(m) < 0.5).astype(np.uint8)
+    return plant(m, n, row_ptr, cols.astype(np.int32), vals, sense, rng, name="ragged")

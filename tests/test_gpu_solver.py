@@ -1,0 +1,216 @@
+"""GPU parity of the CUDA solver against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: the FP64 path tracks the oracle's iterates to <= 1e-10 relative
+(2-norm) over the first 1000 iterations and reaches the same objective to
+<= 1e-6 relative at the tolerance; the trace of restart decisions is identical.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2508_16806_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_16806_gb300 import lp as L
+    L.load()
+    return L
+
+
+def rel(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _problems():
+    return {
+        "lp200x400": synth.small_dense_lp(),
+        "ragged": synth.ragged_lp(),
+        "shuffled": synth.shuffle_sense(synth.small_dense_lp(), 3),
+        "powerlaw": synth.power_law_lp(4000, 8000, 4, 600, seed=11),
+    }
+
+
+PROBS = _problems()
+
+
+# ---------------------------------------------------------------- one step
+
+@pytest.mark.parametrize("name", ["lp200x400", "ragged", "powerlaw"])
+def test_single_fixed_step_matches_oracle_step(L, oracle_mod, name):
+    """One PDHG step (no scaling) from the start point equals the oracle's
+    Algorithm 1 step: exercises both SpMVs (every row-length path) and the
+    fused projections."""
+    lp = PROBS[name]
+    prob = L.Problem(lp)
+    eta, omega = 0.37, 1.3
+    x, y, info, _ = prob.solve(tol=0.0, max_iters=1, check_every=1, ruiz_iters=0,
+                               adaptive_step=0, restarts=0, primal_weight_update=0,
+                               eta0=eta, omega0=omega)
+    assert info["status"] == L.LP_ITERATION_LIMIT and info["iters"] == 1
+    x0, y0 = oracle_mod.start_point(lp)
+    xo, yo = oracle_mod.pdhg_step(lp, x0, y0, eta / omega, eta * omega)
+    assert rel(x, xo) < 1e-13
+    assert rel(y, yo) < 1e-13
+
+
+# ---------------------------------------------------------------- iterate tracking
+
+@pytest.mark.parametrize("name", ["lp200x400", "ragged", "shuffled", "powerlaw"])
+@pytest.mark.parametrize("iters", [1, 10, 100, 1000])
+def test_fp64_iterates_track_oracle(L, oracle_mod, name, iters):
+    """Restarted, adaptive, scaled FP64 PDHG: the candidate after `iters`
+    iterations matches the oracle's to 1e-10 relative, and every check record
+    (restart flag, candidate choice, omega, eta, KKT values) agrees."""
+    lp = PROBS[name]
+    prob = L.Problem(lp)
+    x, y, info, tr = prob.solve(tol=1e-13, max_iters=iters, trace_cap=4096)
+    xo, yo, io, tro = oracle_mod.solve(lp, tol=1e-13, max_iters=iters, trace_cap=4096)
+    assert info["status"] == io["status"] == L.LP_ITERATION_LIMIT
+    assert info["iters"] == io["iters"] == iters
+    assert info["attempts"] == io["attempts"]
+    assert info["restarts"] == io["restarts"]
+    assert rel(x, xo) <= 1e-10, rel(x, xo)
+    assert rel(y, yo) <= 1e-10, rel(y, yo)
+    assert info["norm_K"] == pytest.approx(io["norm_K"], rel=1e-12)
+    assert len(tr) == len(tro)
+    for a, b in zip(tr, tro):
+        assert a["k"] == b["k"] and a["attempts"] == b["attempts"]
+        assert a["restart"] == b["restart"] and a["cand_is_avg"] == b["cand_is_avg"]
+        for f in ("omega", "eta", "kkt_cur", "kkt_cand", "rel_gap", "rel_pres", "rel_dres"):
+            assert a[f] == pytest.approx(b[f], rel=1e-8, abs=1e-13), (f, a[f], b[f])
+
+
+# ---------------------------------------------------------------- to tolerance
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-8])
+def test_fp64_solve_reaches_oracle_objective(L, oracle_mod, tol):
+    lp = PROBS["lp200x400"]
+    prob = L.Problem(lp)
+    x, y, info, tr = prob.solve(tol=tol, max_iters=200000, trace_cap=8192)
+    xo, yo, io, _ = oracle_mod.solve(lp, tol=tol, max_iters=200000)
+    assert info["status"] == L.LP_OPTIMAL == io["status"]
+    assert info["iters"] == io["iters"]
+    assert float(lp.c @ x) == pytest.approx(float(lp.c @ xo), rel=1e-6)
+    k = oracle_mod.kkt(lp, x, y)
+    assert max(k["rel_gap"], k["rel_pres"], k["rel_dres"]) <= tol * (1 + 1e-6)
+    if tol <= 1e-8:
+        assert float(lp.c @ x) == pytest.approx(lp.f_star, rel=1e-6)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-8])
+def test_mixed_precision_reaches_tolerance(L, oracle_mod, tol):
+    """FP32 iterations with FP64 reductions, then FP64 polish below 1e-5: the
+    returned point satisfies the tolerance when the oracle re-checks it in FP64."""
+    lp = PROBS["lp200x400"]
+    prob = L.Problem(lp)
+    x, y, info, tr = prob.solve(tol=tol, max_iters=400000, precision=L.LP_PREC_MIXED,
+                                trace_cap=8192)
+    assert info["status"] == L.LP_OPTIMAL
+    k = oracle_mod.kkt(lp, x, y)
+    slack = 2.0 if tol >= 1e-5 else 1.0 + 1e-6
+    assert max(k["rel_gap"], k["rel_pres"], k["rel_dres"]) <= tol * slack
+    assert info["precision_used"] == (L.LP_PREC_MIXED if tol >= 1e-5 else L.LP_PREC_FP64)
+    if tol < 1e-5:
+        assert info["fp64_iters"] > 0
+        assert float(lp.c @ x) == pytest.approx(lp.f_star, rel=1e-6)
+
+
+# ---------------------------------------------------------------- behaviour
+
+def test_repeat_solves_are_bitwise_identical(L):
+    lp = PROBS["ragged"]
+    prob = L.Problem(lp)
+    r1 = prob.solve(tol=1e-13, max_iters=300, trace_cap=64)
+    r2 = prob.solve(tol=1e-13, max_iters=300, trace_cap=64)
+    assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1])
+    assert r1[3] == r2[3]
+
+
+def test_host_and_device_inputs_agree(L):
+    lp = PROBS["powerlaw"]
+    a = L.Problem(lp, device_copy=True).solve(tol=1e-13, max_iters=200)
+    b = L.Problem(lp, device_copy=False).solve(tol=1e-13, max_iters=200)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_device_output_buffers(L):
+    lp = PROBS["lp200x400"]
+    prob = L.Problem(lp)
+    xh, yh, _, _ = prob.solve(tol=1e-6, max_iters=100000)
+    xd, yd, _, _ = prob.solve(tol=1e-6, max_iters=100000, out_device=True)
+    assert np.array_equal(xh, xd.cpu().numpy()) and np.array_equal(yh, yd.cpu().numpy())
+
+
+def test_warm_start_at_optimum_stops_at_first_check(L):
+    lp = PROBS["lp200x400"]
+    prob = L.Problem(lp)
+    x, y, info, tr = prob.solve(tol=1e-8, x0=lp.x_star, y0=lp.y_star, trace_cap=16)
+    assert info["status"] == L.LP_OPTIMAL and info["iters"] == 0
+    assert rel(x, lp.x_star) < 1e-12
+
+
+def test_iteration_and_time_limits(L):
+    lp = PROBS["ragged"]
+    prob = L.Problem(lp)
+    _, _, info, _ = prob.solve(tol=1e-14, max_iters=130)
+    assert info["status"] == L.LP_ITERATION_LIMIT and info["iters"] == 130
+    _, _, info, _ = prob.solve(tol=1e-14, max_iters=10**9, time_limit_s=1e-7)
+    assert info["status"] == L.LP_TIME_LIMIT
+
+
+def _desc_copy(lp, **changes):
+    d = {f: getattr(lp, f) for f in ("m", "n", "row_ptr", "col_idx", "vals", "sense",
+                                     "c", "q", "l", "u")}
+    d.update(changes)
+    return synth.LP(**d)
+
+
+@pytest.mark.parametrize("bad", ["col", "nan", "bounds", "rowptr", "sense"])
+def test_invalid_problems_are_rejected(L, bad):
+    lp = PROBS["lp200x400"]
+    if bad == "col":
+        ci = lp.col_idx.copy(); ci[5] = lp.n
+        b = _desc_copy(lp, col_idx=ci)
+    elif bad == "nan":
+        v = lp.vals.copy(); v[3] = np.nan
+        b = _desc_copy(lp, vals=v)
+    elif bad == "bounds":
+        l = lp.l.copy(); l[2] = lp.u[2] + 1
+        b = _desc_copy(lp, l=l)
+    elif bad == "rowptr":
+        rp = lp.row_ptr.copy(); rp[10], rp[11] = rp[11], rp[10] - 1
+        b = _desc_copy(lp, row_ptr=rp)
+    else:
+        s = lp.sense.copy(); s[0] = 7
+        b = _desc_copy(lp, sense=s)
+    with pytest.raises(L.LpError) as e:
+        L.Problem(b)
+    assert e.value.status == L.LP_INVALID_ARGUMENT
+
+
+def test_constraint_free_columns_and_free_variables(L, oracle_mod):
+    """Free variables (l = -inf, u = +inf) and one-sided bounds: lambda's
+    projection onto {0}, R^+, R^- on the device agrees with the oracle."""
+    lp = synth.small_dense_lp()
+    rng = np.random.default_rng(5)
+    l, u = lp.l.copy(), lp.u.copy()
+    interior = (lp.x_star > lp.l) & (lp.x_star < lp.u)
+    idx = np.flatnonzero(interior)
+    l[idx[: len(idx) // 3]] = -np.inf
+    u[idx[len(idx) // 3: 2 * len(idx) // 3]] = np.inf
+    both = idx[2 * len(idx) // 3:][:10]
+    l[both], u[both] = -np.inf, np.inf
+    lp2 = _desc_copy(lp, l=l, u=u)
+    prob = L.Problem(lp2)
+    x, y, info, tr = prob.solve(tol=1e-13, max_iters=500, trace_cap=64)
+    xo, yo, io, tro = oracle_mod.solve(lp2, tol=1e-13, max_iters=500)
+    assert rel(x, xo) <= 1e-10 and rel(y, yo) <= 1e-10
