@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark: time to 1e-4 relative KKT error of restarted PDHG on one GB300.
+
+Workload: the synthetic 1,000,000 x 2,000,000 LP with power-law row lengths
+(alpha = 2.1 on 4..5000 nonzeros, nnz ~ 20.07M, N(0,1) values, half >= rows,
+half = rows, planted optimum), solved to 1e-4 relative KKT error.  One step is
+one full lp_solve: Ruiz scaling, power iteration, and the restarted adaptive
+PDHG loop with its KKT checks, in the mixed path (FP32 matrix, iterates and SpMV
+accumulation; FP64 reductions).  The plain FP64 path is solved once beside it.
+
+Prints one JSON line (rank 0).  With torchrun and N GPUs each rank solves its
+own instance (seed + rank): replicas, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "time to 1e-4 rel KKT (s), PDHG iters/s, SpMV HBM GB/s vs FP64 plain"
+FALLBACK_HBM_GBS = 6800.0
+CACHE = os.environ.get("PDHG_BENCH_CACHE", "/tmp/pdhg_bench_cache")
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from one ncu capture of the current kernel source; None when
+# the kernel changed after the capture.  Summary: profiles/spmv_powerlaw_1Mx2M.md
+NCU_TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="powerlaw", choices=["powerlaw", "small"])
+    p.add_argument("--tol", type=float, default=1e-4)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(name, seed_offset=0):
+    from paper_2508_16806_gb300 import synth
+    if name == "small":
+        lp = synth.small_dense_lp(20250816 + seed_offset)
+        return lp, "lp200x400 (100 >= / 100 = rows, 2% N(0,1) sparsity, planted optimum)"
+    os.makedirs(CACHE, exist_ok=True)
+    path = os.path.join(CACHE, f"powerlaw_{20250817 + seed_offset}.npz")
+    desc = ("powerlaw LP 1,000,000 x 2,000,000 (row lengths alpha 2.1 on 4..5000, "
+            "N(0,1) values, half >= / half = rows, planted optimum)")
+    if os.path.exists(path):
+        z = np.load(path)
+        lp = synth.LP(int(z["m"]), int(z["n"]), z["row_ptr"], z["col_idx"], z["vals"], z["sense"],
+                      z["c"], z["q"], z["l"], z["u"], z["x_star"], None, "powerlaw")
+        return lp, desc
+    lp = synth.power_law_lp(seed=20250817 + seed_offset)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, m=lp.m, n=lp.n, row_ptr=lp.row_ptr, col_idx=lp.col_idx, vals=lp.vals,
+             sense=lp.sense, c=lp.c, q=lp.q, l=lp.l, u=lp.u, x_star=lp.x_star)
+    os.replace(tmp, path)
+    return lp, desc
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_estimate(lp, iters_to_tol, small_sample=False):
+    """Times the FP64 CPU oracle on a bounded sample of the workload and scales
+    it to a time-to-tolerance estimate (seconds): Ruiz (10 passes, timed in
+    full), 100 power iterations (per-iteration time from a short run), and
+    iters_to_tol PDHG iterations (per-iteration time from the difference of a
+    4- and a 12-iteration run, plus one KKT check per 64 iterations costed as
+    two iterations)."""
+    import oracle
+    oracle.build()
+    t = time.perf_counter()
+    oracle.ruiz(lp, 10, 1e-4)
+    t_ruiz = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.power_norm(lp, 1)
+    t1 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.power_norm(lp, 3)
+    t3 = time.perf_counter() - t
+    t_pow = max(t3 - t1, 0.0) / 2
+    a, b = (4, 12)
+    t = time.perf_counter()
+    oracle.solve(lp, tol=0.0, max_iters=a, check_every=a, ruiz_iters=0, power_iters=1)
+    ta = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.solve(lp, tol=0.0, max_iters=b, check_every=b, ruiz_iters=0, power_iters=1)
+    tb = time.perf_counter() - t
+    t_iter = max(tb - ta, 1e-9) / (b - a)
+    est = t_ruiz + 100 * t_pow + iters_to_tol * t_iter * (1 + 2 / 64)
+    sample = (f"Ruiz 10 passes ({t_ruiz:.2f} s), power iteration per-step {t_pow:.3f} s x 100, "
+              f"PDHG {t_iter:.3f} s/iteration from a {a}- vs {b}-iteration run, scaled to "
+              f"{iters_to_tol} iterations (+1 check per 64 iterations)")
+    return est, t_iter, sample
+
+
+def reference_iterations(tol):
+    path = os.path.join(ROOT, "oracle", "reference_runs.json")
+    try:
+        for r in json.load(open(path)):
+            if abs(r["tol"] - tol) < 1e-15 and r["status"] == 1:
+                return int(r["iters"]), "oracle run to tolerance (oracle/reference_runs.json)"
+    except Exception:
+        pass
+    return None, None
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    lp, desc = workload(args.workload)
+    iters, src = reference_iterations(args.tol)
+    if iters is None:
+        iters, src = 5000, "assumed 5000 iterations (no stored oracle run)"
+    vals = []
+    sample = ""
+    for s in range(args.warmup + args.steps):
+        est, t_iter, sample = oracle_estimate(lp, iters)
+        if s >= args.warmup:
+            vals.append(est)
+    v = float(statistics.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "tol": args.tol, "iterations_to_tol": iters,
+                       "iterations_source": src},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    from paper_2508_16806_gb300 import lp as L
+
+    L.load()
+    lp, desc = workload(args.workload, seed_offset=rank)
+    stream = torch.cuda.Stream()
+    prob = L.Problem(lp, device_copy=True, stream=stream)
+    opts = dict(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=2_000_000)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        prob.solve(**opts)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, _, info, _ = prob.solve(**opts)
+        infos.append(info)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    iters = statistics.mean(i["iters"] for i in infos)
+    launches = int(sum(i["kernel_launches"] for i in infos))
+    statuses = sorted({L.STATUS[i["status"]] for i in infos})
+
+    # plain FP64 path on the same LP (outside the timed region)
+    t0 = time.perf_counter()
+    _, _, i64, _ = prob.solve(tol=args.tol, precision=L.LP_PREC_FP64, max_iters=2_000_000)
+    torch.cuda.synchronize()
+    fp64_s = time.perf_counter() - t0
+
+    # per-kernel timing of one step attempt (CUDA events on the solver's stream)
+    peak, peak_src = measured_peak()
+    rows = {}
+    for prec, tag in ((L.LP_PREC_MIXED, "fp32"), (L.LP_PREC_FP64, "fp64")):
+        prob.solve(tol=args.tol, precision=prec, max_iters=256)
+        ms_k, by_k = prob.profile_step(prec, reps=30)
+        names = ["primal_update", "spmv_K_dual", "spmv_KT_step", "step_control"]
+        rows[tag] = {n: {"ms": a, "bytes": b, "gbs": (b / (a * 1e-3) / 1e9) if a > 0 else None}
+                     for n, a, b in zip(names, ms_k, by_k)}
+    dom_name = max(("spmv_K_dual", "spmv_KT_step"), key=lambda n: rows["fp32"][n]["ms"])
+    dom = rows["fp32"][dom_name]
+    iter_ms = sum(r["ms"] for r in rows["fp32"].values())
+    iter_bytes = sum(r["bytes"] for r in rows["fp32"].values())
+    traffic = NCU_TRAFFIC.get(dom_name)
+    roofline = {"bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": dom["gbs"] / peak, "traffic": traffic, "kernel": dom_name,
+                "peak_source": peak_src,
+                "bytes_per_launch": dom["bytes"], "ms_per_launch": dom["ms"]}
+
+    # end to end through the C ABI with host buffers (H2D of the LP, D2H of x, y)
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        h2d = (lp.row_ptr.nbytes + lp.col_idx.nbytes + lp.vals.nbytes + lp.sense.nbytes +
+               lp.c.nbytes + lp.q.nbytes + lp.l.nbytes + lp.u.nbytes)
+        d2h = 8 * (lp.n + lp.m)
+        times = []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            ph = L.Problem(lp, device_copy=False, stream=stream)
+            ph.solve(**opts)
+            ph.close()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        e2e = {"value": min(times), "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ref_iters, src = reference_iterations(args.tol)
+        if ref_iters is None:
+            ref_iters, src = int(i64["iters"]), "iterations of the GPU FP64 run"
+        est, t_iter, sample = oracle_estimate(lp, ref_iters)
+        cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": sample + f"; iteration count from the {src}",
+               "oracle_iters_per_s": 1.0 / t_iter}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "nnz": lp.nnz, "tol": args.tol,
+                       "precision": "FP32 matrix/iterates/SpMV accumulation, FP64 reductions",
+                       "step": "one lp_solve: Ruiz + power iteration + restarted adaptive PDHG "
+                               "to tol (setup included)",
+                       "l2": "inputs larger than L2 (FP32 K and K^T 160 MB + vectors)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "statuses": statuses, "iters_to_tol": iters,
+            "pdhg_iters_per_s": iters / (ms / 1e3),
+            "setup_s": statistics.mean(i["setup_s"] for i in infos),
+            "fp64_plain": {"time_to_tol_s": fp64_s, "iters": int(i64["iters"]),
+                           "status": L.STATUS[i64["status"]],
+                           "spmv_hbm_gbs": rows["fp64"][dom_name]["gbs"]},
+            "spmv_hbm_gbs": dom["gbs"],
+            "kernels": rows,
+            "iteration_gbs": iter_bytes / (iter_ms * 1e-3) / 1e9,
+            "roofline": roofline,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

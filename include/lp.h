@@ -143,6 +143,7 @@ typedef struct {
     double norm_K;               /* Algorithm 2 estimate of ||K~||_2 */
     double setup_s;              /* scaling + power iteration + casts (host wall clock) */
     double solve_s;              /* iterations (host wall clock) */
+    int64_t kernel_launches;     /* kernels this call launched (graph bodies included) */
     double* x;
     double* y;
     int32_t memory_space;        /* of x and y */

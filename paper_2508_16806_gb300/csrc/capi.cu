@@ -178,6 +178,7 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
         o->warm_memory_space != LP_MEM_DEVICE)
         return LP_INVALID_ARGUMENT;
     const double t0 = now_s();
+    const long long launches0 = h->launches;
     // setup: scaling (Algorithm 3), norm (Algorithm 2), step size and weight
     LP_TRY(setup_engine<double>(h, o));
     double normK = 0.0;
@@ -239,6 +240,7 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
         LP_TRY(extract_solution<double>(h, r->x, r->y, r->memory_space));
     }
     r->solve_s = now_s() - t1;
+    r->kernel_launches = h->launches - launches0;
     return r->status;
 }
 

@@ -57,6 +57,7 @@ struct Ctrl {
     int adaptive, pwu, restarts_on, check_every;
     int rejects;         // consecutive rejected attempts (a guard against a stuck loop)
     int pad0;
+    long long bodies;    // loop-body executions (for the launch count)
 };
 
 // ------------------------------------------------------------- device buffers
@@ -129,6 +130,7 @@ struct Handle {
     std::vector<DevBuf> allocs;
     Engine<double> e64;
     Engine<float> e32;
+    long long launches = 0;      // kernels launched by the host (graph bodies counted apart)
     int built_precision_mask = 0;
 };
 

@@ -335,6 +335,7 @@ lp_status sum_of_squares(Handle* h, const double* v, int64_t count, double* out_
     const int g = grid_for(count, kEW, kEWGrid);
     k_sumsq_part<<<g, kEW, 0, h->stream>>>(count, v, part);
     k_sum_final<<<1, kCtlNT, 0, h->stream>>>(part, g, part + kEWGrid);
+    h->launches += 2;
     LP_CUDA_TRY(cudaGetLastError());
     LP_CUDA_TRY(cudaMemcpyAsync(out_host, part + kEWGrid, sizeof(double),
                                 cudaMemcpyDeviceToHost, h->stream));
@@ -472,17 +473,22 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     LP_CUDA_TRY(cudaMemcpyAsync(E.val, h->val0, pad8(nnz) * sizeof(double),
                                 cudaMemcpyDeviceToDevice, st));
     k_fill<double><<<grid_for(m), 256, 0, st>>>(h->R, m, 1.0);
+    ++h->launches;
     k_fill<double><<<grid_for(n), 256, 0, st>>>(h->C, n, 1.0);
+    ++h->launches;
     double* rn = h->scratch;
     double* cn = h->scratch + m;
     unsigned long long* dev = reinterpret_cast<unsigned long long*>(h->scratch + m + n);
     for (int it = 0; it < o->ruiz_iters; ++it) {
         k_row_inf<<<grid_for(m * 32), 256, 0, st>>>(m, h->rp, E.val, rn);
+        ++h->launches;
         LP_CUDA_TRY(cudaMemsetAsync(cn, 0, sizeof(double) * (size_t)n, st));
         k_col_inf<<<grid_for(nnz, 256, 8192), 256, 0, st>>>(
             nnz, h->ci, E.val, reinterpret_cast<unsigned long long*>(cn));
+        ++h->launches;
         LP_CUDA_TRY(cudaMemsetAsync(dev, 0, sizeof(unsigned long long), st));
         k_ruiz_dev<<<grid_for(m + n, 256, 4096), 256, 0, st>>>(m, n, rn, cn, dev);
+        ++h->launches;
         LP_CUDA_TRY(cudaGetLastError());
         unsigned long long hdev = 0;
         LP_CUDA_TRY(cudaMemcpyAsync(&hdev, dev, sizeof(hdev), cudaMemcpyDeviceToHost, st));
@@ -491,21 +497,30 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
         std::memcpy(&dv, &hdev, sizeof(dv));
         if (dv <= o->ruiz_tol) break;
         k_ruiz_factors<<<grid_for(m), 256, 0, st>>>(m, rn, h->R);
+        ++h->launches;
         k_ruiz_factors<<<grid_for(n), 256, 0, st>>>(n, cn, h->C);
+        ++h->launches;
         k_scale_vals<<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, h->krow, h->ci, rn, cn, E.val);
+        ++h->launches;
         LP_CUDA_TRY(cudaGetLastError());
     }
     if (o->pock_chambolle) {
         k_pc_sums<<<grid_for(m + n), 256, 0, st>>>(m, n, h->rp, h->trp, h->tperm, E.val, rn, cn);
+        ++h->launches;
         k_ruiz_factors<<<grid_for(m), 256, 0, st>>>(m, rn, h->R);
+        ++h->launches;
         k_ruiz_factors<<<grid_for(n), 256, 0, st>>>(n, cn, h->C);
+        ++h->launches;
         k_scale_vals<<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, h->krow, h->ci, rn, cn, E.val);
+        ++h->launches;
         LP_CUDA_TRY(cudaGetLastError());
     }
     k_scale_vectors<<<grid_for(m + n), 256, 0, st>>>(m, n, h->R, h->C, h->c0, h->q0, h->l0, h->u0,
                                                      E.c, E.q, E.l, E.u);
+    ++h->launches;
     LP_CUDA_TRY(cudaMemsetAsync(E.tval, 0, pad8(nnz) * sizeof(double), st));
     k_gather_cast<double><<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, h->tperm, E.val, E.tval);
+    ++h->launches;
     LP_CUDA_TRY(cudaGetLastError());
 
     // Algorithm 2 on K~: b = 1; repeat b <- K~^T (K~ b), b <- b / ||b||; ||K~ b||
@@ -514,19 +529,26 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     double* part = h->scratch;  // partials of ||b||^2 (ntblk) / ||t||^2 (nblk)
     int* go = reinterpret_cast<int*>(h->scratch + std::max(E.nblk, E.ntblk) + 8);
     k_fill<double><<<grid_for(n), 256, 0, st>>>(b, n, 1.0);
+    ++h->launches;
     LP_CUDA_TRY(cudaMemsetAsync(go, 0, sizeof(int), st));
     k_fill<int><<<1, 32, 0, st>>>(go, 1, 1);
+    ++h->launches;
     for (int it = 0; it < o->power_iters; ++it) {
         EpiStore<double> e1{b, t, nullptr, nullptr, go};
         k_spmv<double, EpiStore<double>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e1);
+        ++h->launches;
         EpiStore<double> e2{t, b, nullptr, part, go};
         k_spmv<double, EpiStore<double>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, e2);
+        ++h->launches;
         k_pow_normalize<<<1, kCtlNT, 0, st>>>(n, b, part, E.ntblk, go);
+        ++h->launches;
         LP_CUDA_TRY(cudaGetLastError());
     }
     EpiStore<double> e3{b, t, nullptr, part, nullptr};
     k_spmv<double, EpiStore<double>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e3);
+    ++h->launches;
     k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.nblk, part + E.nblk + 4);
+    ++h->launches;
     LP_CUDA_TRY(cudaGetLastError());
     double s2 = 0.0;
     LP_CUDA_TRY(cudaMemcpyAsync(&s2, part + E.nblk + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -574,11 +596,17 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         const Engine<double>& D = h->e64;
         cudaStream_t st = h->stream;
         k_gather_cast<T><<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, nullptr, D.val, E.val);
+        ++h->launches;
         k_gather_cast<T><<<grid_for(nnz, 256, 8192), 256, 0, st>>>(nnz, h->tperm, D.val, E.tval);
+        ++h->launches;
         k_gather_cast<T><<<grid_for(n), 256, 0, st>>>(n, nullptr, D.c, E.c);
+        ++h->launches;
         k_gather_cast<T><<<grid_for(n), 256, 0, st>>>(n, nullptr, D.l, E.l);
+        ++h->launches;
         k_gather_cast<T><<<grid_for(n), 256, 0, st>>>(n, nullptr, D.u, E.u);
+        ++h->launches;
         k_gather_cast<T><<<grid_for(m), 256, 0, st>>>(m, nullptr, D.q, E.q);
+        ++h->launches;
         LP_CUDA_TRY(cudaGetLastError());
     }
     return LP_OK;

@@ -438,8 +438,10 @@ k_restart_apply(const Ctrl* __restrict__ ctrl, T* x0, T* x1, T* y0, T* y1, T* kx
     }
 }
 
-__global__ void k_set_cond(Ctrl* ctrl, cudaGraphConditionalHandle handle, int use_handle)
+__global__ void k_set_cond(Ctrl* ctrl, cudaGraphConditionalHandle handle, int use_handle,
+                           int in_body)
 {
+    if (in_body) ctrl->bodies += 1;
     ctrl->want_check = 0;
     ctrl->restart = 0;
     ctrl->skip = ctrl->done;
@@ -531,7 +533,7 @@ static void launch_attempt(Handle* h, Engine<T>& E, cudaStream_t st)
 
 template <typename T>
 static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphConditionalHandle hd,
-                         int use_handle)
+                         int use_handle, int in_body)
 {
     const int64_t m = h->m, n = h->n;
     k_check_prep<T><<<ew_grid(n + m), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.XS,
@@ -549,7 +551,7 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
     k_restart_apply<T><<<ew_grid(n + m), kEW, 0, st>>>(
         E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.KTY[0], E.KTY[1], E.XA, E.YA,
         E.KXA, E.KTYA, E.XANC, E.YANC, E.XS, E.YS, n, m);
-    k_set_cond<<<1, 1, 0, st>>>(E.ctrl, hd, use_handle);
+    k_set_cond<<<1, 1, 0, st>>>(E.ctrl, hd, use_handle, in_body);
 }
 
 template <typename T>
@@ -587,7 +589,7 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
         LP_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal));
         for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st);
-        launch_check<T>(h, E, st, hd, 1);
+        launch_check<T>(h, E, st, hd, 1, 1);
         cudaGraph_t captured = nullptr;
         LP_CUDA_TRY(cudaStreamEndCapture(st, &captured));
         LP_CUDA_TRY(cudaGraphInstantiate(&E.exec, graph, 0));
@@ -596,7 +598,7 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
         cudaGraphDestroy(graph);
         LP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st);
-        launch_check<T>(h, E, st, hd, 0);
+        launch_check<T>(h, E, st, hd, 0, 1);
         cudaGraph_t g2 = nullptr;
         LP_CUDA_TRY(cudaStreamEndCapture(st, &g2));
         LP_CUDA_TRY(cudaGraphInstantiate(&E.body_exec, g2, 0));
@@ -689,8 +691,9 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     LP_CUDA_TRY(cudaMemcpyAsync(E.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
 
     // the start-point check (KKT of z^0, anchor)
-    launch_check<T>(h, E, st, cudaGraphConditionalHandle{}, 0);
+    launch_check<T>(h, E, st, cudaGraphConditionalHandle{}, 0, 0);
     LP_CUDA_TRY(cudaGetLastError());
+    h->launches += 3 + 1 + 9;   // start state, its two products, the clock read, the start check
 
     const int slots = o->check_every + (o->adaptive_step ? 4 : 0);
     LP_TRY(build_graph<T>(h, E, o->check_every, slots));
@@ -707,6 +710,8 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
             LP_CUDA_TRY(cudaGraphLaunch(E.body_exec, st));
         }
     }
+    // loop bodies ran on the device: each is `slots` attempts of 4 launches + 9 check launches
+    h->launches += out->bodies * (long long)(slots * 4 + 9);
     if (trace_host && cap > 0) {
         const long long got = std::min<long long>(out->trace_len, cap);
         if (got > 0)
@@ -744,6 +749,7 @@ lp_status extract_solution_ex(Handle* h, double* x, double* y, int space, double
     }
     k_extract<T><<<ew_grid(n + m), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.XA, E.YA,
                                                   h->R, h->C, dx, dy, xs_dev, ys_dev, n, m);
+    ++h->launches;
     LP_CUDA_TRY(cudaGetLastError());
     if (tmp) {
         if (x) LP_CUDA_TRY(cudaMemcpyAsync(x, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, st));

@@ -69,6 +69,7 @@ class LpResult(C.Structure):
                 ("rel_pres", C.c_double), ("rel_dres", C.c_double),
                 ("omega", C.c_double), ("eta", C.c_double), ("norm_K", C.c_double),
                 ("setup_s", C.c_double), ("solve_s", C.c_double),
+                ("kernel_launches", C.c_int64),
                 ("x", C.c_void_p), ("y", C.c_void_p),
                 ("memory_space", C.c_int32), ("reserved", C.c_int32),
                 ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("trace_len", C.c_int64)]

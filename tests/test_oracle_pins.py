@@ -355,3 +355,21 @@ def test_unrolled_adjoint_matches_central_differences(oracle_mod):
             assert abs(fd - grad[idx]) / scale < 1e-5, (kind, idx, fd, grad[idx])
             checked += 1
     assert checked == 36
+
+
+def test_adaptive_step_amplifies_rounding(oracle_mod):
+    """Documents why iterate tracking with Algorithm 5 is checked over the first
+    check period only: moving eta_0 by one part in 1e15 leaves fixed-step
+    restarted PDHG within 1e-13 of its own run after 1000 iterations, while the
+    adaptive step rule carries the same change to > 1e-7."""
+    lp = synth.small_dense_lp()
+    vs, R, Cc, _ = oracle_mod.ruiz(lp, 10, 1e-4)
+    eta = 0.9 / oracle_mod.power_norm(lp, 100, vals=vs)
+    out = {}
+    for adaptive in (0, 1):
+        xa = oracle_mod.solve(lp, tol=1e-13, max_iters=1000, eta0=eta, adaptive_step=adaptive)[0]
+        xb = oracle_mod.solve(lp, tol=1e-13, max_iters=1000, eta0=eta * (1 + 1e-15),
+                              adaptive_step=adaptive)[0]
+        out[adaptive] = np.linalg.norm(xa - xb) / np.linalg.norm(xa)
+    assert out[0] < 1e-13
+    assert out[1] > 1e-7
