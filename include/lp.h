@@ -204,6 +204,33 @@ lp_status lp_grad(lp_handle h, const lp_opts* opts, int32_t K_iters, int32_t ckp
 lp_status lp_profile_step(lp_handle h, int32_t precision, int32_t reps, double* ms_out,
                           double* bytes_out);
 
+/* Termination quantities of one primal-dual pair (x, y) of the LP in desc,
+ * computed on the device WITHOUT allocating any device memory.  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc when they check a point: code that is capturing a stream into a CUDA
+ * graph, hosts that forbid device allocation after start-up (an allocation can
+ * block or synchronise the device), or plugins inside an application that owns
+ * all device memory.
+ * desc: every array in device memory (memory_space = LP_MEM_DEVICE); it is not
+ * copied and not validated beforehand, but every row pointer and column index is
+ * range-checked on the device (LP_INVALID_ARGUMENT if one is out of range).
+ * x[n], y[m]: device.  omega > 0: weight of KKT_omega.  out (host, 8 doubles):
+ * [0] c^T x  [1] q^T y + l^T lambda^+ + u^T lambda^-  [2] primal residual norm
+ * [3] dual residual norm  [4] rel_gap  [5] rel_pres  [6] rel_dres  [7] KKT_omega
+ * (the quantities of lp_result / lp_trace_rec, unscaled).  cuda_stream: a
+ * cudaStream_t or NULL; the call returns after that stream finished its work.
+ * Scratch: a fixed device array of LP_KKT_NOALLOC_MAX_DOUBLES doubles (8 MiB)
+ * compiled into the library, held by every GPU that loads the library until the
+ * process exits; problems with m + n + 1800 > LP_KKT_NOALLOC_MAX_DOUBLES are
+ * rejected with LP_INVALID_ARGUMENT.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call before
+ * any stream capture begins.  All calls share the array and every call
+ * overwrites it (what must start at zero is cleared by each call): calls whose
+ * work overlaps on the GPU race and must be serialised by the caller. */
+#define LP_KKT_NOALLOC_MAX_DOUBLES 1048576
+lp_status lp_kkt_noalloc(const lp_desc* desc, const double* x, const double* y, double omega,
+                         double* out, void* cuda_stream);
+
 /* Releases the handle and all its device memory.  NULL is ignored. */
 void lp_destroy(lp_handle h);
 

@@ -76,7 +76,8 @@ class LpResult(C.Structure):
 
 
 EXPORTS = ("lp_opts_default", "lp_create", "lp_solve", "lp_solve_batch", "lp_grad",
-           "lp_profile_step", "lp_destroy", "lp_status_string", "lp_abi_version")
+           "lp_profile_step", "lp_destroy", "lp_status_string", "lp_abi_version",
+           "lp_kkt_noalloc")
 
 _lib = None
 
@@ -116,6 +117,9 @@ def load(build_if_missing: bool = True):
     lib.lp_status_string.restype = C.c_char_p
     lib.lp_abi_version.argtypes = []
     lib.lp_abi_version.restype = C.c_int32
+    lib.lp_kkt_noalloc.argtypes = [P(LpDesc), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                   C.c_void_p]
+    lib.lp_kkt_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
@@ -163,6 +167,17 @@ def lp_profile_step(h, precision: int, reps: int):
     if s != 0:
         raise LpError(s, "lp_profile_step")
     return list(ms), list(by)
+
+
+def lp_kkt_noalloc(desc: LpDesc, x: int, y: int, omega: float, stream: int | None = None):
+    """Termination quantities of (x, y) (device pointers) without device
+    allocation; returns the 8 values of include/lp.h's lp_kkt_noalloc."""
+    out = (C.c_double * 8)()
+    s = load().lp_kkt_noalloc(C.byref(desc), x, y, omega, C.cast(out, C.c_void_p),
+                              C.c_void_p(stream or 0))
+    if s != 0:
+        raise LpError(s, "lp_kkt_noalloc")
+    return list(out)
 
 
 def lp_destroy(h) -> None:
