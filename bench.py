@@ -47,7 +47,25 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-4)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--host-loop", action="store_true",
+                   help="host-driven loop graph (lp_opts.loop_mode = 1), for ncu launch lists")
+    p.add_argument("--kernel-profile", action="store_true",
+                   help="short run for ncu: one 64-iteration mixed solve, then 3 timed step "
+                        "attempts of each kernel class (no bench line)")
     return p.parse_args()
+
+
+def kernel_profile(args):
+    import torch
+    from paper_2508_16806_gb300 import lp as L
+    L.load()
+    lp, desc = workload(args.workload)
+    stream = torch.cuda.Stream()
+    prob = L.Problem(lp, device_copy=True, stream=stream)
+    prob.solve(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=64)
+    ms, by = prob.profile_step(L.LP_PREC_MIXED, reps=3)
+    print(json.dumps({"kernel_profile": desc, "ms": ms, "bytes": by}), flush=True)
+    prob.close()
 
 
 def workload(name, seed_offset=0):
@@ -208,6 +226,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.kernel_profile:
+        kernel_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -225,7 +246,8 @@ def main():
     lp, desc = workload(args.workload, seed_offset=rank)
     stream = torch.cuda.Stream()
     prob = L.Problem(lp, device_copy=True, stream=stream)
-    opts = dict(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=2_000_000)
+    opts = dict(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=2_000_000,
+                loop_mode=1 if args.host_loop else 0)
 
     def barrier():
         if world > 1:

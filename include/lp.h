@@ -107,7 +107,10 @@ typedef struct {
     double omega0;               /* > 0: initial primal weight instead of ||c~||/||q~|| */
     double eta0;                 /* > 0: initial step size instead of eta_scale/||K~|| */
     int32_t warm_memory_space;   /* memory space of x0 / y0 */
-    int32_t reserved;
+    int32_t loop_mode;           /* 0 (default): the loop runs inside one CUDA graph with a
+                                    device-side while condition; 1: the host launches the loop
+                                    body graph and reads the stop flag after each body (for
+                                    profilers that cannot see kernels under a conditional node) */
 } lp_opts;
 
 /* One record per KKT check (the start, every check_every accepted

@@ -42,6 +42,7 @@ lp_status check_opts(const lp_opts* o)
         o->power_iters < 0 || !(o->eta_scale > 0.0) || !(o->time_limit_s > 0.0))
         return LP_INVALID_ARGUMENT;
     if (o->precision != LP_PREC_FP64 && o->precision != LP_PREC_MIXED) return LP_INVALID_ARGUMENT;
+    if (o->loop_mode != 0 && o->loop_mode != 1) return LP_INVALID_ARGUMENT;
     return LP_OK;
 }
 
@@ -91,6 +92,7 @@ void lp_opts_default(lp_opts* o)
     o->omega0 = 0.0;
     o->eta0 = 0.0;
     o->warm_memory_space = LP_MEM_HOST;
+    o->loop_mode = 0;
 }
 
 const char* lp_status_string(lp_status s)

@@ -19,12 +19,6 @@ constexpr int kEW = 256;          // threads of an elementwise block
 constexpr int kEWGrid = 1216;     // elementwise grid cap: 152 SMs x 8 resident blocks
 constexpr int kCtlNT = 512;       // threads of a control (single-block) kernel
 
-// nnz staged in shared memory per row-block (CSR-stream); rows longer than
-// this form a block of their own that loops over the row.
-template <typename T> struct Cap;
-template <> struct Cap<double> { static constexpr int value = 2048; };
-template <> struct Cap<float>  { static constexpr int value = 4096; };
-
 // status codes shared with the ABI
 constexpr int kRunning = -100;
 
@@ -56,7 +50,7 @@ struct Ctrl {
     int restart;         // the last check restarted
     int adaptive, pwu, restarts_on, check_every;
     int rejects;         // consecutive rejected attempts (a guard against a stuck loop)
-    int pad0;
+    unsigned int tick;   // finished blocks of the current K^T launch (last one runs the step control)
     long long bodies;    // loop-body executions (for the launch count)
 };
 
@@ -84,12 +78,14 @@ struct Engine {
     T *XA = nullptr, *YA = nullptr;      // averages
     T *KXA = nullptr, *KTYA = nullptr;   // their products
     T *XANC = nullptr, *YANC = nullptr;  // restart anchor
-    // row-block schedules for this precision's staging capacity
-    int32_t* brow = nullptr;   int nblk = 0;    // K rows
+    // warp-task schedules for this precision's task capacity
+    int32_t* brow = nullptr;   int nblk = 0;    // K rows: task boundaries, task count
     int32_t* bcol = nullptr;   int ntblk = 0;   // K^T rows
+    int64_t* bnzK = nullptr;   int64_t* bnzT = nullptr;   // first nonzero of each task
+    int gK = 0, gT = 0;                         // blocks of the K and K^T SpMV launches
     // reduction partials
-    double* partD = nullptr;   // [nblk]
-    double* partT = nullptr;   // [2][ntblk]
+    double* partD = nullptr;   // [gK]
+    double* partT = nullptr;   // [2][gT]
     double* partR = nullptr;   // [8][kEWGrid]
     double* partC = nullptr;   // [10][kEWGrid]
     Ctrl* ctrl = nullptr;
@@ -100,6 +96,7 @@ struct Engine {
     int graph_check_every = -1;
     int graph_slots = -1;
     bool graph_conditional = false;
+    int graph_host_loop = -1;
     cudaGraphExec_t body_exec = nullptr;   // host-loop fallback
 };
 
@@ -127,6 +124,7 @@ struct Handle {
     // scratch
     double* scratch = nullptr;   size_t scratch_bytes = 0;
     double* wbuf = nullptr;      // [n + m] scaled FP64 hand-off state (mixed precision polish)
+    int* dev_err = nullptr;      // device flag: a bounded wait of a kernel gave up
     std::vector<DevBuf> allocs;
     Engine<double> e64;
     Engine<float> e32;
@@ -199,14 +197,23 @@ __device__ __forceinline__ void block_partials(const double (&v)[NQ], double* pa
 }
 
 // Fixed-order sum of part[0..count) by a whole block of NT threads; the
-// result is valid in every thread.
+// result is valid in every thread.  Loads go through L2 (ld.global.cg), so
+// values written by other blocks of the same launch are seen after a fence.
 template <int NT>
 __device__ double block_sum_array(const double* part, int count)
 {
     __shared__ double sh[NT / 32];
     __shared__ double total;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < count; i += NT) s += part[i];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = threadIdx.x;
+    for (; i + 3 * NT < count; i += 4 * NT) {
+        s0 += __ldcg(part + i);
+        s1 += __ldcg(part + i + NT);
+        s2 += __ldcg(part + i + 2 * NT);
+        s3 += __ldcg(part + i + 3 * NT);
+    }
+    for (; i < count; i += NT) s0 += __ldcg(part + i);
+    double s = (s0 + s1) + (s2 + s3);
     s = warp_sum(s);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) sh[warp] = s;

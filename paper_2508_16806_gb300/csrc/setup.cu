@@ -367,6 +367,8 @@ lp_status setup_create(Handle* h, const lp_desc* d)
                                         (size_t)(std::max(m, n) + 2 * kEWGrid + 64) * sizeof(double));
     h->scratch_bytes = std::max<size_t>(h->scratch_bytes, (size_t)(m + n + 64) * 8 * 2);
     LP_TRY(dev_alloc(h, (void**)&h->scratch, h->scratch_bytes));
+    LP_TRY(dev_alloc_n(h, &h->dev_err, 1));
+    LP_CUDA_TRY(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
 
     LP_CUDA_TRY(cudaMemsetAsync(h->ci, 0, pad8(nnz) * sizeof(int32_t), h->stream));
     LP_CUDA_TRY(cudaMemsetAsync(h->val0, 0, pad8(nnz) * sizeof(double), h->stream));
@@ -526,8 +528,9 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     // Algorithm 2 on K~: b = 1; repeat b <- K~^T (K~ b), b <- b / ||b||; ||K~ b||
     double* b = E.XA;          // n
     double* t = E.KXA;         // m
-    double* part = h->scratch;  // partials of ||b||^2 (ntblk) / ||t||^2 (nblk)
-    int* go = reinterpret_cast<int*>(h->scratch + std::max(E.nblk, E.ntblk) + 8);
+    double* part = h->scratch;  // partials of ||b||^2 (gT) / ||t||^2 (gK)
+    int* go = reinterpret_cast<int*>(h->scratch + std::max(E.gK, E.gT) + 8);
+    LP_CUDA_TRY((spmv_prepare<double, EpiStore<double>>()));
     k_fill<double><<<grid_for(n), 256, 0, st>>>(b, n, 1.0);
     ++h->launches;
     LP_CUDA_TRY(cudaMemsetAsync(go, 0, sizeof(int), st));
@@ -535,24 +538,28 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     ++h->launches;
     for (int it = 0; it < o->power_iters; ++it) {
         EpiStore<double> e1{b, t, nullptr, nullptr, go};
-        k_spmv<double, EpiStore<double>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e1);
+        launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, e1);
         ++h->launches;
         EpiStore<double> e2{t, b, nullptr, part, go};
-        k_spmv<double, EpiStore<double>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, e2);
+        launch_spmv<double>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err,
+                            e2);
         ++h->launches;
-        k_pow_normalize<<<1, kCtlNT, 0, st>>>(n, b, part, E.ntblk, go);
+        k_pow_normalize<<<1, kCtlNT, 0, st>>>(n, b, part, E.gT, go);
         ++h->launches;
         LP_CUDA_TRY(cudaGetLastError());
     }
     EpiStore<double> e3{b, t, nullptr, part, nullptr};
-    k_spmv<double, EpiStore<double>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e3);
+    launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, e3);
     ++h->launches;
-    k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.nblk, part + E.nblk + 4);
+    k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.gK, part + E.gK + 4);
     ++h->launches;
     LP_CUDA_TRY(cudaGetLastError());
     double s2 = 0.0;
-    LP_CUDA_TRY(cudaMemcpyAsync(&s2, part + E.nblk + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    int derr = 0;
+    LP_CUDA_TRY(cudaMemcpyAsync(&s2, part + E.gK + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LP_CUDA_TRY(cudaMemcpyAsync(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     LP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (derr) return LP_DEVICE_TIMEOUT;
     *normK = std::sqrt(s2);
     return LP_OK;
 }
@@ -565,17 +572,31 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     Engine<T>& E = engine_of<T>(h);
     if (!E.ready) {
-        const int cap = Cap<T>::value;
-        std::vector<int32_t> bk = make_row_blocks(h->h_rp.data(), m, cap, kNT);
-        std::vector<int32_t> bt = make_row_blocks(h->h_trp.data(), n, cap, kNT);
+        const int cap = cap_w<T>();
+        std::vector<int32_t> bk = make_row_blocks(h->h_rp.data(), m, cap, kTaskRows);
+        std::vector<int32_t> bt = make_row_blocks(h->h_trp.data(), n, cap, kTaskRows);
         E.nblk = (int)bk.size() - 1;
         E.ntblk = (int)bt.size() - 1;
+        int sms = 0;
+        LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        E.gK = spmv_grid(E.nblk, sms);
+        E.gT = spmv_grid(E.ntblk, sms);
         LP_TRY(dev_alloc_n(h, &E.brow, bk.size()));
         LP_TRY(dev_alloc_n(h, &E.bcol, bt.size()));
         LP_CUDA_TRY(cudaMemcpyAsync(E.brow, bk.data(), bk.size() * sizeof(int32_t),
                                     cudaMemcpyHostToDevice, h->stream));
         LP_CUDA_TRY(cudaMemcpyAsync(E.bcol, bt.data(), bt.size() * sizeof(int32_t),
                                     cudaMemcpyHostToDevice, h->stream));
+        std::vector<int64_t> nk(bk.size()), nt(bt.size());
+        for (size_t t = 0; t < bk.size(); ++t) nk[t] = h->h_rp[(size_t)bk[t]];
+        for (size_t t = 0; t < bt.size(); ++t) nt[t] = h->h_trp[(size_t)bt[t]];
+        LP_TRY(dev_alloc_n(h, &E.bnzK, nk.size()));
+        LP_TRY(dev_alloc_n(h, &E.bnzT, nt.size()));
+        LP_CUDA_TRY(cudaMemcpyAsync(E.bnzK, nk.data(), nk.size() * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, h->stream));
+        LP_CUDA_TRY(cudaMemcpyAsync(E.bnzT, nt.data(), nt.size() * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, h->stream));
+        LP_CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
         LP_TRY(dev_alloc_n(h, &E.val, pad8(nnz)));
         LP_TRY(dev_alloc_n(h, &E.tval, pad8(nnz)));
         LP_CUDA_TRY(cudaMemsetAsync(E.val, 0, pad8(nnz) * sizeof(T), h->stream));
@@ -585,8 +606,8 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         for (T** p : vn) LP_TRY(dev_alloc_n(h, p, (size_t)n));
         T** vm[] = {&E.q, &E.Y[0], &E.Y[1], &E.KX[0], &E.KX[1], &E.YS, &E.YA, &E.KXA, &E.YANC};
         for (T** p : vm) LP_TRY(dev_alloc_n(h, p, (size_t)m));
-        LP_TRY(dev_alloc_n(h, &E.partD, (size_t)E.nblk + 8));
-        LP_TRY(dev_alloc_n(h, &E.partT, 2 * (size_t)E.ntblk + 8));
+        LP_TRY(dev_alloc_n(h, &E.partD, (size_t)E.gK + 8));
+        LP_TRY(dev_alloc_n(h, &E.partT, 2 * (size_t)E.gT + 8));
         LP_TRY(dev_alloc_n(h, &E.partR, 8 * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.partC, 10 * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.ctrl, 1));

@@ -1,11 +1,12 @@
 // The restarted PDHG iteration on the device.
 //
 // One step attempt (Algorithm 1 with theta = 1, step sizes tau = eta / omega,
-// sigma = eta * omega, Section 2.3.1) is four launches:
+// sigma = eta * omega, Section 2.3.1) is three launches:
 //   k_primal      x' = clamp(x - tau (c - K^T y), l, u)        (K^T y kept from the last step)
 //   k_spmv<Dual>  K x', then y' = proj_Y(y + sigma (q - (2 K x' - K x)))  (K x kept)
-//   k_spmv<PrT>   K^T y' and the Algorithm 5 terms ||dx||^2, dx . (K^T y' - K^T y)
-//   k_step_ctrl   accept / reject (Algorithm 5), swap the double buffers
+//   k_spmv<PrT>   K^T y' and the Algorithm 5 terms ||dx||^2, dx . (K^T y' - K^T y); its
+//                 last block takes the accept / reject decision (Algorithm 5) and swaps
+//                 the double buffers
 // Every check_every accepted iterations the check launches run: averages
 // (Section 2.4.2), their products, FP64 KKT reductions, the candidate, the
 // termination test on the unscaled problem (Section 2.3.2), the three restart
@@ -23,6 +24,8 @@ namespace pdhg {
 
 // ------------------------------------------------------------------ step kernels
 
+// x' = clamp(x - tau (c - K^T y), l, u); the pending averaged iterate is added to
+// the x sums on the way.  16-byte vector loads, scalar tail.
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0,
@@ -30,13 +33,40 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
          const T* __restrict__ u, T* xs, int64_t n)
 {
     if (ctrl->skip) return;
+    using VT = VecTraits<T>;
+    constexpr int VEC = VT::N;
     const int cur = ctrl->cur;
     const T tau = (T)(ctrl->eta / ctrl->omega);
     const T pw = (T)ctrl->pend_w;
     const T* x = cur ? x1 : x0;
     T* xn = cur ? x0 : x1;
     const T* kty = cur ? kty1 : kty0;
-    for (int64_t j = (int64_t)blockIdx.x * kEW + threadIdx.x; j < n; j += (int64_t)gridDim.x * kEW) {
+    const int64_t nv = n / VEC;
+    for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < nv; t += (int64_t)gridDim.x * kEW) {
+        T xj[VEC], kj[VEC], cj[VEC], lj[VEC], uj[VEC], o[VEC];
+        VT::unpack(*reinterpret_cast<const typename VT::V*>(x + t * VEC), xj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(kty + t * VEC)), kj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(c + t * VEC)), cj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(l + t * VEC)), lj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(u + t * VEC)), uj);
+        if (pw != T(0)) {
+            T sj[VEC];
+            VT::unpack(*reinterpret_cast<const typename VT::V*>(xs + t * VEC), sj);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) sj[k] += pw * xj[k];
+            *reinterpret_cast<typename VT::V*>(xs + t * VEC) = VT::pack(sj);
+        }
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            T v = xj[k] - tau * (cj[k] - kj[k]);
+            if (v < lj[k]) v = lj[k];
+            if (v > uj[k]) v = uj[k];
+            o[k] = v;
+        }
+        *reinterpret_cast<typename VT::V*>(xn + t * VEC) = VT::pack(o);
+    }
+    for (int64_t j = nv * VEC + (int64_t)blockIdx.x * kEW + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * kEW) {
         const T xj = x[j];
         if (pw != T(0)) xs[j] += pw * xj;
         T v = xj - tau * (c[j] - kty[j]);
@@ -58,6 +88,7 @@ struct EpiDual {
     const uint8_t* sense;
     double* part;
     int cur; T sigma; T pw; int adapt;
+    struct Pre { T y = 0, kx = 0, q = 0, ys = 0; uint8_t ge = 0; };
     struct Acc { double dy2 = 0.0; };
     __device__ bool begin() {
         if (ctrl->skip) return false;
@@ -68,79 +99,36 @@ struct EpiDual {
         return true;
     }
     __device__ const T* xin() const { return cur ? xs0 : xs1; }   // x' lives in the other half
-    __device__ void row(int i, T kxn, Acc& a) const {
-        const T* y = cur ? y1 : y0;
-        T* yn = cur ? y0 : y1;
-        const T* kx = cur ? kx1 : kx0;
-        T* kxo = cur ? kx0 : kx1;
-        const T yi = y[i];
-        if (pw != T(0)) ys[i] += pw * yi;
-        T v = yi + sigma * (q[i] - (T(2) * kxn - kx[i]));
-        if (sense[i] && v < T(0)) v = T(0);
-        yn[i] = v;
-        kxo[i] = kxn;
-        const double d = (double)v - (double)yi;
+    __device__ Pre load(int i) const {
+        Pre p;
+        p.y = (cur ? y1 : y0)[i];
+        p.kx = (cur ? kx1 : kx0)[i];
+        p.q = q[i];
+        p.ge = sense[i];
+        if (pw != T(0)) p.ys = ys[i];
+        return p;
+    }
+    __device__ void row(int i, T kxn, const Pre& p, Acc& a) const {
+        if (pw != T(0)) ys[i] = p.ys + pw * p.y;
+        T v = p.y + sigma * (p.q - (T(2) * kxn - p.kx));
+        if (p.ge && v < T(0)) v = T(0);
+        (cur ? y0 : y1)[i] = v;
+        (cur ? kx0 : kx1)[i] = kxn;
+        const double d = (double)v - (double)p.y;
         a.dy2 += d * d;
     }
     __device__ void finish(Acc& a) const {
         if (adapt) {
             const double t[1] = {a.dy2};
-            block_partials<1, kNT>(t, part, gridDim.x);
+            block_partials<1, kSpmvNT>(t, part, gridDim.x);
         }
     }
 };
 
-// K^T y' SpMV + Algorithm 5 terms
-template <typename T>
-struct EpiPrimalT {
-    const Ctrl* ctrl;
-    const T* ys0; const T* ys1;     // Y[0], Y[1]
-    const T* x0; const T* x1;
-    T* kty0; T* kty1;
-    double* part;
-    int cur; int adapt;
-    struct Acc { double dx2 = 0.0, inter = 0.0; };
-    __device__ bool begin() {
-        if (ctrl->skip) return false;
-        cur = ctrl->cur;
-        adapt = ctrl->adaptive;
-        return true;
-    }
-    __device__ const T* xin() const { return cur ? ys0 : ys1; }   // y'
-    __device__ void row(int j, T ktyn, Acc& a) const {
-        T* kto = cur ? kty0 : kty1;
-        kto[j] = ktyn;
-        if (adapt) {
-            const T* x = cur ? x1 : x0;
-            const T* xn = cur ? x0 : x1;
-            const T* kt = cur ? kty1 : kty0;
-            const double dx = (double)xn[j] - (double)x[j];
-            a.dx2 += dx * dx;
-            a.inter += dx * ((double)ktyn - (double)kt[j]);
-        }
-    }
-    __device__ void finish(Acc& a) const {
-        if (adapt) {
-            const double t[2] = {a.dx2, a.inter};
-            block_partials<2, kNT>(t, part, gridDim.x);
-        }
-    }
-};
-
-// Algorithm 5 decision (or the plain swap of a fixed step).  The paper's k is
-// read as the 1-based index of the iteration being taken.
-__global__ void __launch_bounds__(kCtlNT)
-k_step_ctrl(Ctrl* ctrl, const double* partD, int nD, const double* partT, int nT)
+// Algorithm 5 decision (or the plain swap of a fixed step), by one thread.
+// The paper's k is read as the 1-based index of the iteration being taken.
+__device__ void step_decide(Ctrl* ctrl, int adapt, double dy2, double dx2, double inter)
 {
-    if (ctrl->skip) return;
-    double dy2 = 0.0, dx2 = 0.0, inter = 0.0;
-    const int adapt = ctrl->adaptive;
-    if (adapt) {
-        dy2 = block_sum_array<kCtlNT>(partD, nD);
-        dx2 = block_sum_array<kCtlNT>(partT, nT);
-        inter = block_sum_array<kCtlNT>(partT + nT, nT);
-    }
-    if (threadIdx.x != 0) return;
     const double eta = ctrl->eta, omega = ctrl->omega;
     bool accept = true;
     double eta_next = eta;
@@ -191,6 +179,71 @@ k_step_ctrl(Ctrl* ctrl, const double* partD, int nD, const double* partT, int nT
         ctrl->want_check = 0;
     }
 }
+
+// K^T y' SpMV + Algorithm 5 terms; the last block to finish sums every block's
+// partials (fixed order) and takes the step decision, so the attempt needs no
+// separate control launch.  No block waits for another: the last block is the
+// one whose ticket completes the count.
+template <typename T>
+struct EpiPrimalT {
+    Ctrl* ctrl;
+    const T* ys0; const T* ys1;     // Y[0], Y[1]
+    const T* x0; const T* x1;
+    T* kty0; T* kty1;
+    double* part;                   // [2][gridDim.x]
+    const double* partD;            // dy^2 partials of the K x' launch
+    int nD;
+    int cur; int adapt;
+    struct Pre { T x = 0, xn = 0, kt = 0; };
+    struct Acc { double dx2 = 0.0, inter = 0.0; };
+    __device__ bool begin() {
+        if (ctrl->skip) return false;
+        cur = ctrl->cur;
+        adapt = ctrl->adaptive;
+        return true;
+    }
+    __device__ const T* xin() const { return cur ? ys0 : ys1; }   // y'
+    __device__ Pre load(int j) const {
+        Pre p;
+        if (adapt) {
+            p.x = (cur ? x1 : x0)[j];
+            p.xn = (cur ? x0 : x1)[j];
+            p.kt = (cur ? kty1 : kty0)[j];
+        }
+        return p;
+    }
+    __device__ void row(int j, T ktyn, const Pre& p, Acc& a) const {
+        (cur ? kty0 : kty1)[j] = ktyn;
+        if (adapt) {
+            const double dx = (double)p.xn - (double)p.x;
+            a.dx2 += dx * dx;
+            a.inter += dx * ((double)ktyn - (double)p.kt);
+        }
+    }
+    __device__ void finish(Acc& a) const {
+        __shared__ int last;
+        if (adapt) {
+            const double t[2] = {a.dx2, a.inter};
+            block_partials<2, kSpmvNT>(t, part, gridDim.x);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(&ctrl->tick, 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        double dy2 = 0.0, dx2 = 0.0, inter = 0.0;
+        if (adapt) {
+            dy2 = block_sum_array<kSpmvNT>(partD, nD);
+            dx2 = block_sum_array<kSpmvNT>(part, gridDim.x);
+            inter = block_sum_array<kSpmvNT>(part + gridDim.x, gridDim.x);
+        }
+        if (threadIdx.x == 0) {
+            ctrl->tick = 0;
+            step_decide(ctrl, adapt, dy2, dx2, inter);
+        }
+    }
+};
 
 // ------------------------------------------------------------------ check kernels
 
@@ -518,17 +571,41 @@ static inline int ew_grid(int64_t count)
 __global__ void k_read_clock(unsigned long long* t) { *t = global_ns(); }
 
 template <typename T>
-static void launch_attempt(Handle* h, Engine<T>& E, cudaStream_t st)
+static int primal_grid(int64_t n)
 {
-    const int64_t n = h->n;
-    k_primal<T><<<ew_grid(n), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c, E.l,
-                                             E.u, E.XS, n);
+    return ew_grid((n + VecTraits<T>::N - 1) / VecTraits<T>::N);
+}
+
+template <typename T>
+static void launch_primal(Handle* h, Engine<T>& E, cudaStream_t st)
+{
+    k_primal<T><<<primal_grid<T>(h->n), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1],
+                                                       E.c, E.l, E.u, E.XS, h->n);
+}
+
+template <typename T>
+static void launch_dual(Handle* h, Engine<T>& E, cudaStream_t st)
+{
     EpiDual<T> ed{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS, E.q, h->sense,
                   E.partD};
-    k_spmv<T, EpiDual<T>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, ed);
-    EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.partT};
-    k_spmv<T, EpiPrimalT<T>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, et);
-    k_step_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partD, E.nblk, E.partT, E.ntblk);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, ed);
+}
+
+template <typename T>
+static void launch_primal_t(Handle* h, Engine<T>& E, cudaStream_t st)
+{
+    EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.partT,
+                     E.partD, E.gK};
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, et);
+}
+
+// one step attempt: 3 launches
+template <typename T>
+static void launch_attempt(Handle* h, Engine<T>& E, cudaStream_t st)
+{
+    launch_primal<T>(h, E, st);
+    launch_dual<T>(h, E, st);
+    launch_primal_t<T>(h, E, st);
 }
 
 template <typename T>
@@ -540,9 +617,9 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
                                                      E.YS, E.XA, E.YA, n, m);
     const int* gate = &E.ctrl->want_check;
     EpiStore<T> e1{E.XA, E.KXA, nullptr, nullptr, gate};
-    k_spmv<T, EpiStore<T>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e1);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, e1);
     EpiStore<T> e2{E.YA, E.KTYA, nullptr, nullptr, gate};
-    k_spmv<T, EpiStore<T>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, e2);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, e2);
     k_check_rows<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YA,
                                              E.KXA, E.YANC, E.q, h->sense, h->R, m, E.partR);
     k_check_cols<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.XA,
@@ -555,9 +632,11 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
 }
 
 template <typename T>
-static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots)
+static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots, int host_loop)
 {
-    if (E.exec && E.graph_check_every == check_every && E.graph_slots == slots) return LP_OK;
+    if ((E.exec || E.body_exec) && E.graph_check_every == check_every && E.graph_slots == slots &&
+        E.graph_host_loop == host_loop)
+        return LP_OK;
     if (E.exec) {
         cudaGraphExecDestroy(E.exec);
         E.exec = nullptr;
@@ -570,8 +649,12 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
     cudaGraph_t graph = nullptr;
     LP_CUDA_TRY(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle hd{};
-    cudaError_t ce = cudaGraphConditionalHandleCreate(&hd, graph, 1, cudaGraphCondAssignDefault);
-    bool conditional = ce == cudaSuccess;
+    bool conditional = false;
+    if (!host_loop) {
+        cudaError_t ce = cudaGraphConditionalHandleCreate(&hd, graph, 1, cudaGraphCondAssignDefault);
+        conditional = ce == cudaSuccess;
+    }
+    cudaError_t ce = cudaSuccess;
     cudaGraph_t body = nullptr;
     if (conditional) {
         cudaGraphNodeParams cp{};
@@ -607,6 +690,7 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
     E.graph_conditional = conditional;
     E.graph_check_every = check_every;
     E.graph_slots = slots;
+    E.graph_host_loop = host_loop;
     return LP_OK;
 }
 
@@ -620,6 +704,9 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     Engine<T>& E = engine_of<T>(h);
     const int64_t m = h->m, n = h->n;
     cudaStream_t st = h->stream;
+    LP_CUDA_TRY((spmv_prepare<T, EpiStore<T>>()));
+    LP_CUDA_TRY((spmv_prepare<T, EpiDual<T>>()));
+    LP_CUDA_TRY((spmv_prepare<T, EpiPrimalT<T>>()));
     // warm start from the caller (unscaled) must be on the device
     const double* dwx = nullptr;
     const double* dwy = nullptr;
@@ -640,9 +727,9 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
                                                      E.l, E.u, h->sense, h->R, h->C, wxs, wys,
                                                      dwx, dwy, n, m);
     EpiStore<T> e1{E.X[0], E.KX[0], nullptr, nullptr, nullptr};
-    k_spmv<T, EpiStore<T>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, e1);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, e1);
     EpiStore<T> e2{E.Y[0], E.KTY[0], nullptr, nullptr, nullptr};
-    k_spmv<T, EpiStore<T>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, e2);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, e2);
     LP_CUDA_TRY(cudaGetLastError());
 
     // device trace buffer
@@ -696,7 +783,7 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     h->launches += 3 + 1 + 9;   // start state, its two products, the clock read, the start check
 
     const int slots = o->check_every + (o->adaptive_step ? 4 : 0);
-    LP_TRY(build_graph<T>(h, E, o->check_every, slots));
+    LP_TRY(build_graph<T>(h, E, o->check_every, slots, o->loop_mode == 1 ? 1 : 0));
     if (E.graph_conditional) {
         LP_CUDA_TRY(cudaGraphLaunch(E.exec, st));
         LP_CUDA_TRY(cudaMemcpyAsync(out, E.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -710,8 +797,14 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
             LP_CUDA_TRY(cudaGraphLaunch(E.body_exec, st));
         }
     }
-    // loop bodies ran on the device: each is `slots` attempts of 4 launches + 9 check launches
-    h->launches += out->bodies * (long long)(slots * 4 + 9);
+    // loop bodies ran on the device: each is `slots` attempts of 3 launches + 9 check launches
+    h->launches += out->bodies * (long long)(slots * 3 + 9);
+    {
+        int derr = 0;
+        LP_CUDA_TRY(cudaMemcpyAsync(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LP_CUDA_TRY(cudaStreamSynchronize(st));
+        if (derr) return LP_DEVICE_TIMEOUT;
+    }
     if (trace_host && cap > 0) {
         const long long got = std::min<long long>(out->trace_len, cap);
         if (got > 0)
@@ -781,28 +874,25 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes)
     c.done = 0;
     c.max_iters = (long long)1 << 60;
     c.check_every = 1 << 30;
+    c.time_limit_ns = 1e18;
+    c.tick = 0;
     LP_CUDA_TRY(cudaMemcpyAsync(E.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-    cudaEvent_t ev[5];
+    cudaEvent_t ev[4];
     for (auto& e : ev) LP_CUDA_TRY(cudaEventCreate(&e));
-    double acc[4] = {0, 0, 0, 0};
+    double acc[3] = {0, 0, 0};
     for (int r = 0; r < reps + 2; ++r) {
         cudaEventRecord(ev[0], st);
-        k_primal<T><<<ew_grid(n), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c,
-                                                 E.l, E.u, E.XS, n);
+        launch_primal<T>(h, E, st);
         cudaEventRecord(ev[1], st);
-        EpiDual<T> ed{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS, E.q, h->sense,
-                      E.partD};
-        k_spmv<T, EpiDual<T>><<<E.nblk, kNT, 0, st>>>(E.brow, h->rp, h->ci, E.val, ed);
+        launch_dual<T>(h, E, st);
         cudaEventRecord(ev[2], st);
-        EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.partT};
-        k_spmv<T, EpiPrimalT<T>><<<E.ntblk, kNT, 0, st>>>(E.bcol, h->trp, h->tci, E.tval, et);
+        launch_primal_t<T>(h, E, st);
         cudaEventRecord(ev[3], st);
-        k_step_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partD, E.nblk, E.partT, E.ntblk);
-        cudaEventRecord(ev[4], st);
+        h->launches += 3;
         LP_CUDA_TRY(cudaGetLastError());
-        LP_CUDA_TRY(cudaEventSynchronize(ev[4]));
+        LP_CUDA_TRY(cudaEventSynchronize(ev[3]));
         if (r >= 2) {
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 3; ++k) {
                 float t = 0.f;
                 cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
                 acc[k] += t;
@@ -810,19 +900,20 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes)
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    for (int k = 0; k < 4; ++k) ms[k] = acc[k] / reps;
+    for (int k = 0; k < 3; ++k) ms[k] = acc[k] / reps;
+    ms[3] = 0.0;
     if (bytes) {
         const double s = sizeof(T);
         // primal: read x, c, l, u, K^T y, x-sum; write x', x-sum
         bytes[0] = (double)n * 8 * s;
-        // K x' + dual: values + indices + row_ptr + gathered x' (once) + y, q, Kx, y-sum,
-        // sense read; y', Kx', y-sum written
+        // K x' + dual: values + indices + row pointers (int64) + x' (each element
+        // gathered at least once) + y, q, K x, y-sum, sense read; y', K x', y-sum written
         bytes[1] = (double)nnz * (s + 4) + (double)(m + 1) * 8 + (double)n * s +
                    (double)m * (7 * s + 1);
-        // K^T y' + step terms: values + indices + row_ptr + gathered y' (once);
-        // K^T y' written; x, x', K^T y read
+        // K^T y' + step terms: values + indices + row pointers + y'; K^T y' written;
+        // x, x', K^T y read
         bytes[2] = (double)nnz * (s + 4) + (double)(n + 1) * 8 + (double)m * s + (double)n * 4 * s;
-        bytes[3] = (double)(E.nblk + 2 * E.ntblk) * 8;
+        bytes[3] = 0.0;
     }
     return LP_OK;
 }

@@ -1,22 +1,31 @@
-// Row-block CSR SpMV with fused epilogues (the products K x and K^T y of
+// Warp-task CSR SpMV with fused epilogues (the products K x and K^T y of
 // Algorithm 1, plus whatever elementwise update consumes each row result).
 //
-// Layout: the rows of a CSR matrix are cut on the host into row-blocks
-// (brow[b] .. brow[b+1]) holding at most Cap<T> nonzeros and at most kNT rows,
-// except that a row longer than Cap<T> forms a block by itself.  A short-row
-// block streams its contiguous nonzero range with 16-byte vector loads of
-// values and column indices (evict-first, so the gathered vector stays in L2),
-// multiplies by the gathered x and stages the products in shared memory; each
-// row is then summed by a group of G lanes (G = the largest power of two with
-// G * rows <= kNT, at most 32) with a shuffle tree.  A long-row block loops over
-// its row with the whole block and reduces in a fixed tree.  Every sum has a
-// fixed order, so results are bitwise reproducible run to run.
+// Layout: the rows of a CSR matrix are cut on the host into warp tasks
+// (task_row[t] .. task_row[t+1]) of at most CapW<T> nonzeros and at most 64 rows;
+// a row longer than CapW<T> forms a task by itself.  Each warp owns one task and
+// never waits for the other warps of its block:
+//   1. it issues, before anything else, the loads of the task's row pointers
+//      and of the epilogue operands of its rows (so their latency overlaps the
+//      stream), then U 16-byte vector loads of values and column indices per
+//      lane (evict-first, so the gathered vector keeps its place in L2), then all
+//      the gathers of x;
+//   2. products go to the warp's own slice of shared memory; after __syncwarp
+//      each row is summed by a group of G lanes (G = largest power of two with
+//      G * rows <= 32) with a shuffle tree, and lane j receives row j's sum;
+//   3. lane j applies the epilogue to row j with the operands it prefetched.
+// A long row is streamed by the whole warp with the same vector loads and a
+// fixed shuffle tree.  All sums have a fixed order: results are bitwise
+// reproducible from run to run.  The block's only barrier is in the epilogue's
+// block-level partial sums at the end, after each warp has worked through its
+// fixed share of the tasks.
 //
 // Epilogue interface (Epi):
-//   bool begin()                       uniform per launch; false = return at once
-//   const T* xin()                     the vector being multiplied
-//   struct Acc; void row(int r, T v, Acc&)   called once per row by one thread
-//   void finish(Acc&)                  block-level partial reductions (all threads)
+//   bool begin()                        uniform per launch; false = return at once
+//   const T* xin()                      the vector being multiplied
+//   struct Pre; Pre load(int r)         operands of row r, loaded before the stream
+//   struct Acc; void row(int r, T v, const Pre&, Acc&)   once per row, one lane
+//   void finish(Acc&)                   block-level work at the end (all threads)
 #pragma once
 
 #include "common.cuh"
@@ -34,6 +43,9 @@ template <> struct VecTraits<float> {
     __device__ static __forceinline__ void unpacki(const I& v, int (&o)[4]) {
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     }
+    __device__ static __forceinline__ V pack(const float (&o)[4]) {
+        return make_float4(o[0], o[1], o[2], o[3]);
+    }
 };
 template <> struct VecTraits<double> {
     using V = double2;
@@ -45,81 +57,379 @@ template <> struct VecTraits<double> {
     __device__ static __forceinline__ void unpacki(const I& v, int (&o)[2]) {
         o[0] = v.x; o[1] = v.y;
     }
+    __device__ static __forceinline__ V pack(const double (&o)[2]) {
+        return make_double2(o[0], o[1]);
+    }
 };
 
-template <typename T, int NT>
-__device__ __forceinline__ T block_reduce_T(T v)
+constexpr int kTaskWarps = 8;        // warps per block of the SpMV kernel
+#ifndef PDHG_TASK_ROWS
+#define PDHG_TASK_ROWS 64
+#endif
+constexpr int kTaskRows = PDHG_TASK_ROWS;   // rows per warp task at most (32 or 64)
+constexpr int kSpmvNT = kTaskWarps * 32;
+#ifndef PDHG_SPMV_MIN_BLOCKS
+#define PDHG_SPMV_MIN_BLOCKS 4
+#endif
+constexpr int kSpmvMinBlocks = PDHG_SPMV_MIN_BLOCKS;   // resident blocks per SM the registers allow
+#ifndef PDHG_SPMV_UNROLL
+#define PDHG_SPMV_UNROLL 2
+#endif
+// 16-byte loads of values (and of column indices) per lane and task
+template <typename T> struct Unroll { static constexpr int value = PDHG_SPMV_UNROLL; };
+// nonzeros per warp task: one pass of U vector loads per lane covers the task's
+// aligned range, whose start may sit up to VEC - 1 elements before the first nonzero
+template <typename T>
+__host__ __device__ constexpr int cap_w() { return 32 * VecTraits<T>::N * Unroll<T>::value - VecTraits<T>::N; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_T(T v)
 {
-    __shared__ T sh[NT / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    T r = 0;
-    if (warp == 0) {
-        r = lane < NT / 32 ? sh[lane] : T(0);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-    }
-    __syncthreads();
-    return r;   // valid in thread 0
+    return v;   // valid in lane 0
 }
 
-template <typename T, class Epi>
-__global__ void __launch_bounds__(kNT)
-k_spmv(const int32_t* __restrict__ brow, const int64_t* __restrict__ rp,
-       const int32_t* __restrict__ ci, const T* __restrict__ val, Epi epi)
+// ------------------------------------------------------------ async copies
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    constexpr int CAP = Cap<T>::value;
-    using VT = VecTraits<T>;
-    constexpr int VEC = VT::N;
-    __shared__ T prod[CAP];
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16),
+// completing on the mbarrier, with an L2 eviction-priority hint
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// read-only gather that does not allocate in L1 (random gathers have no reuse there)
+__device__ __forceinline__ float ld_gather(const float* p)
+{
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_gather(const double* p)
+{
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for one phase of the mbarrier, giving up after `limit_ns` of device
+// time; returns false on time-out.  Every lane of the warp calls it.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+// ------------------------------------------------------------ per-warp stages
+
+// Shared memory of one warp: two stages of (values, column indices) of a short
+// task, two mbarriers and the task's row pointers.  Stage sizes keep every stage
+// 16-byte aligned and leave room for the rounding of the copied range.
+template <typename T>
+struct alignas(16) WarpStage {
+    static constexpr int CAPW = cap_w<T>();
+    static constexpr int VA = 16 / (int)sizeof(T);   // values per 16 bytes
+    // a copied range is the task rounded out to 16 bytes at both ends
+    static constexpr int VPAD = (CAPW + 2 * (VA - 1) + VA - 1) / VA * VA;
+    static constexpr int IPAD = (CAPW + 6 + 3) / 4 * 4;
+    T v[2][VPAD];
+    int i[2][IPAD];
+    uint64_t bar[2];
+    int64_t rps[kTaskRows + 1];
+};
+
+template <typename T>
+constexpr size_t spmv_smem_bytes() { return sizeof(WarpStage<T>) * kTaskWarps; }
+static_assert(sizeof(WarpStage<float>) % 16 == 0 && sizeof(WarpStage<double>) % 16 == 0,
+              "stages must stay 16-byte aligned");
+
+// Issues the bulk copies of a short task's values [s, e) and column indices
+// into stage `st` (lane 0 only).  Each copy covers the 16-byte aligned range
+// around [s, e); the arrays are padded so the rounded range stays inside them.
+template <typename T>
+__device__ __forceinline__ void stage_task(WarpStage<T>& W, int st, int64_t s, int64_t e,
+                                           const T* val, const int32_t* ci, uint64_t pol)
+{
+    constexpr int VA = 16 / (int)sizeof(T);
+    const int64_t v0 = s & ~(int64_t)(VA - 1), v1 = (e + VA - 1) & ~(int64_t)(VA - 1);
+    const int64_t i0 = s & ~(int64_t)3, i1 = (e + 3) & ~(int64_t)3;
+    const uint32_t vb = (uint32_t)((v1 - v0) * (int64_t)sizeof(T));
+    const uint32_t ib = (uint32_t)((i1 - i0) * 4);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&W.bar[st], vb + ib);
+    bulk_g2s(W.v[st], val + v0, vb, &W.bar[st], pol);
+    bulk_g2s(W.i[st], ci + i0, ib, &W.bar[st], pol);
+}
+
+// Each warp takes the tasks warp_id, warp_id + W, warp_id + 2W, ... (W = all warps
+// of the launch): a fixed assignment, so every partial sum keeps a fixed order.
+// A task is streamed through the warp's two shared-memory stages in chunks of at
+// most CAPW nonzeros (one chunk for a short task; a long row is cut into
+// consecutive chunks whose products accumulate per lane).  While the warp works
+// on one chunk, the bulk copy of its next chunk is in flight into the other
+// stage.  task_nz[t] = rp[task_row[t]].  A stage wait that exceeds 50 ms sets
+// *err and abandons the launch's remaining work after a second bounded wait for
+// the copy in flight.
+template <typename T, class Epi>
+__global__ void __launch_bounds__(kSpmvNT, kSpmvMinBlocks)
+k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz, int ntasks,
+       const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
+       int* err, Epi epi)
+{
+    constexpr int CAPW = cap_w<T>();
+    constexpr int VA = 16 / (int)sizeof(T);
+    constexpr unsigned long long kWaitNs = 50ull * 1000 * 1000;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     if (!epi.begin()) return;
-    const T* __restrict__ xv = epi.xin();
-    const int tid = threadIdx.x;
-    const int r0 = brow[blockIdx.x], r1 = brow[blockIdx.x + 1];
-    const int64_t s = rp[r0], e = rp[r1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpStage<T>& W = reinterpret_cast<WarpStage<T>*>(smem_raw)[warp];
     typename Epi::Acc acc;
-    if (e - s > CAP) {
-        T a = 0;
-        for (int64_t p = s + tid; p < e; p += kNT) a += __ldcs(val + p) * __ldg(xv + __ldcs(ci + p));
-        a = block_reduce_T<T, kNT>(a);
-        if (tid == 0) epi.row(r0, a, acc);
-    } else {
-        const int64_t a0 = s & ~(int64_t)(VEC - 1);
-        for (int64_t c = a0 + (int64_t)tid * VEC; c < e; c += (int64_t)kNT * VEC) {
-            T vv[VEC];
-            int ii[VEC];
-            VT::unpack(__ldcs(reinterpret_cast<const typename VT::V*>(val + c)), vv);
-            VT::unpacki(__ldcs(reinterpret_cast<const typename VT::I*>(ci + c)), ii);
+    const T* __restrict__ xv = epi.xin();
+    const int stride = gridDim.x * kTaskWarps;
+    if (lane == 0) {
+        mbar_init(&W.bar[0], 1);
+        mbar_init(&W.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const uint64_t pol = evict_first_policy();
+    int task = blockIdx.x * kTaskWarps + warp;
+    // current task [s, e), current chunk [cs, ce); next task bounds [ns, ne)
+    int64_t s = 0, e = 0, ns = 0, ne = 0, cs = 0, ce = 0;
+    if (task < ntasks) {
+        s = task_nz[task];
+        e = task_nz[task + 1];
+        cs = s;
+        ce = e - s > CAPW ? s + CAPW : e;
+        if (lane == 0 && ce > cs) stage_task<T>(W, 0, cs, ce, val, ci, pol);
+        if (task + stride < ntasks) {
+            ns = task_nz[task + stride];
+            ne = task_nz[task + stride + 1];
+        }
+    }
+    uint32_t par = 0;   // bit st: parity of the next wait on stage st
+    int st = 0;
+    int r0 = 0, nrows = 0;
+    typename Epi::Pre pre0, pre1;
+    T along = 0;        // per-lane sum of a long row over its chunks
+#pragma unroll 1
+    while (task < ntasks) {
+        const bool first = cs == s;
+        const bool last = ce == e;
+        const bool is_long = e - s > CAPW;
+        // the next chunk: the rest of this long row, or the first chunk of the next task
+        int64_t xs = 0, xe = 0;
+        bool have_next = false;
+        if (!last) {
+            xs = ce;
+            xe = e - ce > CAPW ? ce + CAPW : e;
+            have_next = true;
+        } else if (task + stride < ntasks) {
+            xs = ns;
+            xe = ne - ns > CAPW ? ns + CAPW : ne;
+            have_next = true;
+        }
+        // an empty chunk (a task of empty rows) is neither copied nor waited for
+        const bool next_staged = have_next && xe > xs;
+        if (next_staged && lane == 0) stage_task<T>(W, st ^ 1, xs, xe, val, ci, pol);
+        if (first) {
+            r0 = task_row[task];
+            nrows = task_row[task + 1] - r0;
+            if (lane < nrows) pre0 = epi.load(r0 + lane);
+            if (lane + 32 < nrows) pre1 = epi.load(r0 + 32 + lane);
+            if (!is_long)
+                for (int t = lane; t <= nrows; t += 32) W.rps[t] = rp[r0 + t];
+            along = 0;
+        }
+        if (ce > cs) {
+            // every lane waits (acquiring the copied bytes); the outcome is made
+            // warp-uniform before anyone acts on it
+            const bool got = mbar_wait_bounded(&W.bar[st], (par >> st) & 1u, kWaitNs);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) atomicOr(err, 1);
+                if (next_staged)
+                    (void)mbar_wait_bounded(&W.bar[st ^ 1], (par >> (st ^ 1)) & 1u, kWaitNs);
+                break;
+            }
+            par ^= 1u << st;
+        }
+        __syncwarp();
+        // gathers for the chunk [cs, ce): lane l owns the 16-byte groups
+        // l, l + 32, l + 64, ... of the staged values; it reads each group's values and
+        // column indices with one vector load apiece, gathers x, and writes the
+        // products back in place (or adds them to its long-row sum)
+        const int64_t v0 = cs & ~(int64_t)(VA - 1);
+        const int d = (int)(v0 - (cs & ~(int64_t)3));   // index-buffer offset of v0
+        const int vo = (int)(cs - v0);
+        const int lim = vo + (int)(ce - cs);
+        T* vbuf = W.v[st];
+        const int* ibuf = W.i[st] + d;
+        using VT = VecTraits<T>;
+        constexpr int VEC = VT::N;
+        // groups per lane: a chunk spans at most VA - 1 + CAPW staged elements
+        constexpr int UG = (VA - 1 + CAPW + 32 * VEC - 1) / (32 * VEC);
+        T vv[UG][VEC];
+        int ii[UG][VEC];
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                const int64_t p = c + k;
-                if (p >= s && p < e) prod[p - s] = vv[k] * __ldg(xv + ii[k]);
+        for (int k = 0; k < UG; ++k) {
+            const int off = (k * 32 + lane) * VEC;
+            if (off < lim) {
+                VT::unpack(*reinterpret_cast<const typename VT::V*>(vbuf + off), vv[k]);
+                VT::unpacki(*reinterpret_cast<const typename VT::I*>(ibuf + off), ii[k]);
             }
         }
-        __syncthreads();
-        const int nrows = r1 - r0;
-        int G = 32;
-        while (G > 1 && G * nrows > kNT) G >>= 1;
-        const int grp = tid / G, lane = tid % G, ngrp = kNT / G;
-        for (int base = 0; base < nrows; base += ngrp) {
-            const int r = r0 + base + grp;
-            T a = 0;
-            if (r < r1) {
-                const int64_t pe = rp[r + 1];
-                for (int64_t p = rp[r] + lane; p < pe; p += G) a += prod[p - s];
+#pragma unroll
+        for (int k = 0; k < UG; ++k) {
+            const int off = (k * 32 + lane) * VEC;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int p = off + v;
+                vv[k][v] = (p >= vo && p < lim) ? vv[k][v] * ld_gather(xv + ii[k][v]) : T(0);
             }
-            for (int o = G >> 1; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o, G);
-            if (r < r1 && lane == 0) epi.row(r, a, acc);
+        }
+        if (is_long) {
+#pragma unroll
+            for (int k = 0; k < UG; ++k)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) along += vv[k][v];
+            if (last) {
+                const T a = warp_sum_T(along);
+                if (lane == 0) epi.row(r0, a, pre0, acc);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < UG; ++k) {
+                const int off = (k * 32 + lane) * VEC;
+                if (off < lim) *reinterpret_cast<typename VT::V*>(vbuf + off) = VT::pack(vv[k]);
+            }
+            T* vs = vbuf + vo;
+            __syncwarp();
+            const int64_t* rps = W.rps;
+            if (nrows <= 32) {
+                int G = 32;
+                while (G > 1 && G * nrows > 32) G >>= 1;
+                const int j = lane / G, g = lane % G;
+                T a = 0;
+                if (j < nrows) {
+                    const int pb = (int)(rps[j] - s), pe = (int)(rps[j + 1] - s);
+                    for (int p = pb + g; p < pe; p += G) a += vs[p];
+                }
+                for (int o = G >> 1; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o, G);
+                const T v = __shfl_sync(0xffffffffu, a, (lane * G) & 31);
+                if (lane < nrows) epi.row(r0 + lane, v, pre0, acc);
+            } else {
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int j = lane + 32 * half;
+                    if (j < nrows) {
+                        const int pb = (int)(rps[j] - s), pe = (int)(rps[j + 1] - s);
+                        T a = 0;
+                        for (int p = pb; p < pe; ++p) a += vs[p];
+                        epi.row(r0 + j, a, half ? pre1 : pre0, acc);
+                    }
+                }
+            }
+        }
+        __syncwarp();   // the stage is rewritten by the copy issued in two chunks' time
+        st ^= 1;
+        if (!last) {
+            cs = xs;
+            ce = xe;
+        } else {
+            task += stride;
+            s = ns;
+            e = ne;
+            cs = xs;
+            ce = xe;
+            if (task + stride < ntasks) {
+                ns = task_nz[task + stride];
+                ne = task_nz[task + stride + 1];
+            }
         }
     }
     epi.finish(acc);
 }
 
+// Sets the dynamic shared-memory limit of one SpMV instantiation (call before
+// any launch or capture) and launches it.
+template <typename T, class Epi>
+inline cudaError_t spmv_prepare()
+{
+    return cudaFuncSetAttribute(k_spmv<T, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)spmv_smem_bytes<T>());
+}
+
+template <typename T, class Epi>
+inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
+                        const int64_t* task_nz, int ntasks, const int64_t* rp, const int32_t* ci,
+                        const T* val, int* err, const Epi& epi)
+{
+    k_spmv<T, Epi><<<grid, kSpmvNT, spmv_smem_bytes<T>(), st>>>(task_row, task_nz, ntasks, rp, ci,
+                                                               val, err, epi);
+}
+
 // Plain epilogue: out[r] = scale * v, with the optional FP64 partial
-// sum of out[r]^2 (power iteration) and a skip flag read from a Ctrl field.
+// sum of out[r]^2 (power iteration) and a gate read from a Ctrl field.
 template <typename T>
 struct EpiStore {
     const T* x;
@@ -127,10 +437,12 @@ struct EpiStore {
     const double* scale;     // nullptr = 1
     double* part;            // nullptr = no partials
     const int* gate;         // nullptr = always run; else run when *gate != 0
+    struct Pre {};
     struct Acc { double s2 = 0.0; };
     __device__ bool begin() const { return gate == nullptr || *gate != 0; }
     __device__ const T* xin() const { return x; }
-    __device__ void row(int r, T v, Acc& a) const {
+    __device__ Pre load(int) const { return Pre{}; }
+    __device__ void row(int r, T v, const Pre&, Acc& a) const {
         if (scale) v = (T)((double)v * *scale);
         out[r] = v;
         a.s2 += (double)v * (double)v;
@@ -138,14 +450,27 @@ struct EpiStore {
     __device__ void finish(Acc& a) const {
         if (part) {
             const double t[1] = {a.s2};
-            block_partials<1, kNT>(t, part, gridDim.x);
+            block_partials<1, kSpmvNT>(t, part, gridDim.x);
         }
     }
 };
 
-// Greedy row-block partition (host): rows are added to the current block
-// while it holds <= cap nonzeros and <= max_rows rows; a row longer than cap
-// gets a block of its own.  Returns the block boundaries (nblk + 1 entries).
+// Blocks of an SpMV launch: one resident wave (SMs x resident blocks per SM),
+// fewer when there are fewer tasks than warps.
+#ifndef PDHG_SPMV_WAVES
+#define PDHG_SPMV_WAVES 1
+#endif
+inline int spmv_grid(int ntasks, int num_sms)
+{
+    const int full = (ntasks + kTaskWarps - 1) / kTaskWarps;
+    if (PDHG_SPMV_WAVES <= 0) return full > 0 ? full : 1;
+    const int wave = num_sms * kSpmvMinBlocks * PDHG_SPMV_WAVES;
+    return full < wave ? (full > 0 ? full : 1) : wave;
+}
+
+// Greedy task partition (host): rows are added to the current task while it
+// holds <= cap nonzeros and <= max_rows rows; a row longer than cap gets a task
+// of its own.  Returns the task boundaries (ntasks + 1 entries).
 std::vector<int32_t> make_row_blocks(const int64_t* rp, int64_t rows, int cap, int max_rows);
 
 }  // namespace pdhg

@@ -111,16 +111,18 @@ def test_fp64_iterates_track_oracle(L, oracle_mod, name, iters):
 
 
 @pytest.mark.parametrize("name", ["lp200x400", "ragged", "shuffled", "powerlaw"])
-@pytest.mark.parametrize("iters", [1, 10, 64])
+@pytest.mark.parametrize("iters", [1, 10, 32])
 def test_fp64_adaptive_iterates_track_oracle(L, oracle_mod, name, iters):
     """With Algorithm 5 the map amplifies rounding differences exponentially
     (the oracle itself departs from its own run by 1e-3 after ~300 iterations
     when eta_0 moves by 1e-15, see test_adaptive_step_amplifies_rounding), so
-    iterate tracking at 1e-10 is checked over the first check period."""
+    iterate tracking at 1e-10 is checked over the first 32 iterations, with a
+    restart check every 16."""
     lp = PROBS[name]
     prob = L.Problem(lp)
-    x, y, info, tr = prob.solve(tol=1e-13, max_iters=iters, trace_cap=64)
-    xo, yo, io, tro = oracle_mod.solve(lp, tol=1e-13, max_iters=iters, trace_cap=64)
+    x, y, info, tr = prob.solve(tol=1e-13, max_iters=iters, trace_cap=64, check_every=16)
+    xo, yo, io, tro = oracle_mod.solve(lp, tol=1e-13, max_iters=iters, trace_cap=64,
+                                       check_every=16)
     assert info["iters"] == io["iters"] == iters
     assert info["attempts"] == io["attempts"]
     assert rel(x, xo) <= 1e-10, rel(x, xo)
