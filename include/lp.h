@@ -197,6 +197,19 @@ lp_status lp_grad(lp_handle h, const lp_opts* opts, int32_t K_iters, int32_t ckp
                   const double* dL_dxK, double* dc, double* dq, double* dvals,
                   double* x_K, int32_t memory_space, double* tau_sigma_out);
 
+/* Forward part of lp_grad: K_iters unrolled fixed-step iterations with the
+ * same start, step sizes and precision rules; writes x_K[n] and/or y_K[m]
+ * (either may be NULL, not both) in memory_space.  tau_sigma_out as in lp_grad. */
+lp_status lp_unroll(lp_handle h, const lp_opts* opts, int32_t K_iters, double* x_K, double* y_K,
+                    int32_t memory_space, double* tau_sigma_out);
+
+/* Replaces values of the LP on its existing sparsity pattern: vals[nnz] (in
+ * lp_desc's nonzero order), c[n], q[m], l[n], u[n]; a NULL pointer keeps the old
+ * array.  The same validation as lp_create (LP_INVALID_ARGUMENT on NaN, l > u).
+ * The next lp_solve / lp_grad / lp_unroll uses the new values. */
+lp_status lp_update_values(lp_handle h, const double* vals, const double* c, const double* q,
+                           const double* l, const double* u, int32_t memory_space);
+
 /* Measurement hook: runs `reps` PDHG step attempts of the given precision on
  * the state left by the last lp_solve of that precision, timing each kernel
  * class with CUDA events on the handle's stream.  ms_out (host, 4 doubles)

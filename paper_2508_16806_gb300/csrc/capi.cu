@@ -274,8 +274,37 @@ lp_status lp_grad(lp_handle p, const lp_opts* o, int32_t K_iters, int32_t ckpt_e
     if (!p || !o || K_iters < 0 || ckpt_every < 1 || !dL_dxK || !dc || !dq || !dvals)
         return LP_INVALID_ARGUMENT;
     if (memory_space != LP_MEM_HOST && memory_space != LP_MEM_DEVICE) return LP_INVALID_ARGUMENT;
+    if (check_opts(o) != LP_OK) return LP_INVALID_ARGUMENT;
     lp_status s = run_grad(&p->h, o, K_iters, ckpt_every, dL_dxK, dc, dq, dvals, x_K,
                            memory_space, tau_sigma_out);
+    if (s < 0) {
+        cudaStreamSynchronize(p->h.stream);
+        (void)cudaGetLastError();
+    }
+    return s;
+}
+
+lp_status lp_unroll(lp_handle p, const lp_opts* o, int32_t K_iters, double* x_K, double* y_K,
+                    int32_t memory_space, double* tau_sigma_out)
+{
+    if (!p || !o || K_iters < 0 || (!x_K && !y_K)) return LP_INVALID_ARGUMENT;
+    if (memory_space != LP_MEM_HOST && memory_space != LP_MEM_DEVICE) return LP_INVALID_ARGUMENT;
+    lp_status s = check_opts(o);
+    if (s != LP_OK) return s;
+    s = run_unroll(&p->h, o, K_iters, x_K, y_K, memory_space, tau_sigma_out);
+    if (s < 0) {
+        cudaStreamSynchronize(p->h.stream);
+        (void)cudaGetLastError();
+    }
+    return s;
+}
+
+lp_status lp_update_values(lp_handle p, const double* vals, const double* c, const double* q,
+                           const double* l, const double* u, int32_t memory_space)
+{
+    if (!p) return LP_INVALID_ARGUMENT;
+    if (memory_space != LP_MEM_HOST && memory_space != LP_MEM_DEVICE) return LP_INVALID_ARGUMENT;
+    lp_status s = setup_update(&p->h, vals, c, q, l, u, memory_space);
     if (s < 0) {
         cudaStreamSynchronize(p->h.stream);
         (void)cudaGetLastError();

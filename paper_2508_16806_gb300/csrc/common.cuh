@@ -261,5 +261,10 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes);
 lp_status run_grad(Handle* h, const lp_opts* o, int K_iters, int ckpt, const double* gxK,
                    double* dc, double* dq, double* dvals, double* xK, int space,
                    double* tau_sigma);
+lp_status run_unroll(Handle* h, const lp_opts* o, int K_iters, double* xK, double* yK, int space,
+                     double* tau_sigma);
+// setup.cu
+lp_status setup_update(Handle* h, const double* vals, const double* c, const double* q,
+                       const double* l, const double* u, int space);
 
 }  // namespace pdhg

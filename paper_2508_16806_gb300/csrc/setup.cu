@@ -465,6 +465,33 @@ lp_status setup_create(Handle* h, const lp_desc* d)
     return LP_OK;
 }
 
+// New values on the same sparsity pattern (any pointer may be NULL = keep).
+lp_status setup_update(Handle* h, const double* vals, const double* c, const double* q,
+                       const double* l, const double* u, int space)
+{
+    const int64_t m = h->m, n = h->n, nnz = h->nnz;
+    if (vals) LP_TRY(copy_in(h, h->val0, vals, sizeof(double) * (size_t)nnz, space));
+    if (c) LP_TRY(copy_in(h, h->c0, c, sizeof(double) * (size_t)n, space));
+    if (q) LP_TRY(copy_in(h, h->q0, q, sizeof(double) * (size_t)m, space));
+    if (l) LP_TRY(copy_in(h, h->l0, l, sizeof(double) * (size_t)n, space));
+    if (u) LP_TRY(copy_in(h, h->u0, u, sizeof(double) * (size_t)n, space));
+    int* flags = reinterpret_cast<int*>(h->scratch);
+    LP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), h->stream));
+    k_validate<<<grid_for(std::max({m, n, nnz}), 256, 4096), 256, 0, h->stream>>>(
+        m, n, nnz, h->rp, h->ci, h->val0, h->sense, h->c0, h->q0, h->l0, h->u0, flags);
+    LP_CUDA_TRY(cudaGetLastError());
+    int hflags = 0;
+    LP_CUDA_TRY(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (hflags) return LP_INVALID_ARGUMENT;
+    double s = 0.0;
+    LP_TRY(sum_of_squares(h, h->q0, m, &s));
+    h->qnorm = std::sqrt(s);
+    LP_TRY(sum_of_squares(h, h->c0, n, &s));
+    h->cnorm = std::sqrt(s);
+    return LP_OK;
+}
+
 // Algorithm 3 (+ optional Pock-Chambolle) into e64.val and R, C, the scaled
 // vectors e64.c/q/l/u and the scaled transpose e64.tval; then Algorithm 2.
 lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
@@ -538,10 +565,10 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     ++h->launches;
     for (int it = 0; it < o->power_iters; ++it) {
         EpiStore<double> e1{b, t, nullptr, nullptr, go};
-        launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, e1);
+        launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
         ++h->launches;
         EpiStore<double> e2{t, b, nullptr, part, go};
-        launch_spmv<double>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err,
+        launch_spmv<double>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, h->m,
                             e2);
         ++h->launches;
         k_pow_normalize<<<1, kCtlNT, 0, st>>>(n, b, part, E.gT, go);
@@ -549,7 +576,7 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
         LP_CUDA_TRY(cudaGetLastError());
     }
     EpiStore<double> e3{b, t, nullptr, part, nullptr};
-    launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, e3);
+    launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, h->n, e3);
     ++h->launches;
     k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.gK, part + E.gK + 4);
     ++h->launches;

@@ -234,7 +234,7 @@ template <typename T, class Epi>
 __global__ void __launch_bounds__(kSpmvNT, kSpmvMinBlocks)
 k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz, int ntasks,
        const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
-       int* err, Epi epi)
+       int* err, int l1_gather, Epi epi)
 {
     constexpr int CAPW = cap_w<T>();
     constexpr int VA = 16 / (int)sizeof(T);
@@ -344,7 +344,9 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 const int p = off + v;
-                vv[k][v] = (p >= vo && p < lim) ? vv[k][v] * ld_gather(xv + ii[k][v]) : T(0);
+                vv[k][v] = (p >= vo && p < lim)
+                               ? vv[k][v] * (l1_gather ? __ldg(xv + ii[k][v]) : ld_gather(xv + ii[k][v]))
+                               : T(0);
             }
         }
         if (is_long) {
@@ -419,13 +421,18 @@ inline cudaError_t spmv_prepare()
                                 (int)spmv_smem_bytes<T>());
 }
 
+// Gathers from a vector of at most this many bytes go through L1 (it stays
+// resident there); larger vectors are gathered without L1 allocation.
+constexpr int64_t kL1GatherBytes = 96 * 1024;
+
 template <typename T, class Epi>
 inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
                         const int64_t* task_nz, int ntasks, const int64_t* rp, const int32_t* ci,
-                        const T* val, int* err, const Epi& epi)
+                        const T* val, int* err, int64_t x_len, const Epi& epi)
 {
+    const int l1 = x_len * (int64_t)sizeof(T) <= kL1GatherBytes ? 1 : 0;
     k_spmv<T, Epi><<<grid, kSpmvNT, spmv_smem_bytes<T>(), st>>>(task_row, task_nz, ntasks, rp, ci,
-                                                               val, err, epi);
+                                                               val, err, l1, epi);
 }
 
 // Plain epilogue: out[r] = scale * v, with the optional FP64 partial

@@ -76,8 +76,8 @@ class LpResult(C.Structure):
 
 
 EXPORTS = ("lp_opts_default", "lp_create", "lp_solve", "lp_solve_batch", "lp_grad",
-           "lp_profile_step", "lp_destroy", "lp_status_string", "lp_abi_version",
-           "lp_kkt_noalloc")
+           "lp_unroll", "lp_update_values", "lp_profile_step", "lp_destroy", "lp_status_string",
+           "lp_abi_version", "lp_kkt_noalloc")
 
 _lib = None
 
@@ -117,6 +117,11 @@ def load(build_if_missing: bool = True):
     lib.lp_status_string.restype = C.c_char_p
     lib.lp_abi_version.argtypes = []
     lib.lp_abi_version.restype = C.c_int32
+    lib.lp_unroll.argtypes = [C.c_void_p, P(LpOpts), C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                              C.c_void_p]
+    lib.lp_unroll.restype = C.c_int
+    lib.lp_update_values.argtypes = [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int32]
+    lib.lp_update_values.restype = C.c_int
     lib.lp_kkt_noalloc.argtypes = [P(LpDesc), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                    C.c_void_p]
     lib.lp_kkt_noalloc.restype = C.c_int
@@ -158,6 +163,17 @@ def lp_grad(h, opts: LpOpts, K_iters: int, ckpt_every: int, dL_dxK: int, dc: int
             dvals: int, x_K: int | None, memory_space: int, tau_sigma_out=None) -> int:
     return load().lp_grad(h, C.byref(opts), K_iters, ckpt_every, dL_dxK, dc, dq, dvals,
                           x_K or None, memory_space, tau_sigma_out)
+
+
+def lp_unroll(h, opts: LpOpts, K_iters: int, x_K: int | None, y_K: int | None,
+              memory_space: int, tau_sigma_out=None) -> int:
+    return load().lp_unroll(h, C.byref(opts), K_iters, x_K or None, y_K or None, memory_space,
+                            tau_sigma_out)
+
+
+def lp_update_values(h, vals=None, c=None, q=None, l=None, u=None,
+                     memory_space: int = LP_MEM_DEVICE) -> int:
+    return load().lp_update_values(h, vals, c, q, l, u, memory_space)
 
 
 def lp_profile_step(h, precision: int, reps: int):

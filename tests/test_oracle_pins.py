@@ -324,7 +324,8 @@ def test_iteration_limit_status(oracle_mod):
 def test_unrolled_adjoint_matches_central_differences(oracle_mod):
     """Reverse-mode gradient of ||x_K - x_target||^2 through K fixed-step
     iterations equals central finite differences (h = 1e-6, FP64) for entries
-    whose projection masks do not flip under +-h."""
+    whose projection masks do not flip under +-h (at a flip the loss has a kink
+    and the two one-sided derivatives differ)."""
     lp, xt = synth.adjoint_lp(50, 100, 8, seed=20250820)
     eta = 0.9 / oracle_mod.power_norm(lp, 200)
     omega = 1.0
@@ -340,6 +341,17 @@ def test_unrolled_adjoint_matches_central_differences(oracle_mod):
     h = 1e-6
     rng = np.random.default_rng(0)
     checked = 0
+
+    def masks(lp_):
+        xs_, ys_ = oracle_mod.unrolled_forward(lp_, tau, sigma, Kit)
+        out = []
+        for t in range(Kit):
+            vx = xs_[t] - tau * (lp_.c - oracle_mod.spmv_t(lp_, ys_[t]))
+            vy = ys_[t] + sigma * (lp_.q - oracle_mod.spmv(lp_, 2 * xs_[t + 1] - xs_[t]))
+            out.append(np.concatenate([(lp_.l < vx) & (vx < lp_.u), (lp_.sense == 0) | (vy > 0)]))
+        return np.array(out)
+
+    m0 = masks(lp)
     for kind, grad, n_ in (("c", dc, lp.n), ("q", dq, lp.m), ("vals", dv, lp.nnz)):
         for idx in rng.choice(n_, 12, replace=False):
             lps = []
@@ -350,11 +362,15 @@ def test_unrolled_adjoint_matches_central_differences(oracle_mod):
                 arr[idx] += sgn * h
                 setattr(cp, kind, arr)
                 lps.append(cp)
+            # a projection kink between the two evaluations makes the loss
+            # non-differentiable there (one-sided derivatives differ): skip it
+            if not all(np.array_equal(m0, masks(q_)) for q_ in lps):
+                continue
             fd = (loss(lps[0]) - loss(lps[1])) / (2 * h)
             scale = max(abs(fd), abs(grad[idx]), 1e-3)
             assert abs(fd - grad[idx]) / scale < 1e-5, (kind, idx, fd, grad[idx])
             checked += 1
-    assert checked == 36
+    assert checked >= 30
 
 
 def test_adaptive_step_amplifies_rounding(oracle_mod):
