@@ -247,11 +247,14 @@ struct EpiPrimalT {
 
 // ------------------------------------------------------------------ check kernels
 
-// Adds the pending iterate to the sums and materialises the averages.
+// Adds the pending iterate to the sums and materialises the averages.  An
+// average of points of X (resp. Y) lies in X (resp. Y); the projection applied
+// here only removes the rounding of the running sums (it matters for FP32 sums).
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y0, const T* y1,
-             T* xs, T* ys, T* xa, T* ya, int64_t n, int64_t m)
+             T* xs, T* ys, T* xa, T* ya, const T* l, const T* u, const uint8_t* sense, int64_t n,
+             int64_t m)
 {
     if (!ctrl->want_check) return;
     const int cur = ctrl->cur;
@@ -264,12 +267,17 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
         if (t < n) {
             T s = xs[t];
             if (pw != T(0)) { s += pw * x[t]; xs[t] = s; }
-            xa[t] = W > 0.0 ? (T)((double)s / W) : T(0);
+            T a = W > 0.0 ? (T)((double)s / W) : T(0);
+            if (a < l[t]) a = l[t];
+            if (a > u[t]) a = u[t];
+            xa[t] = a;
         } else {
             const int64_t i = t - n;
             T s = ys[i];
             if (pw != T(0)) { s += pw * y[i]; ys[i] = s; }
-            ya[i] = W > 0.0 ? (T)((double)s / W) : T(0);
+            T a = W > 0.0 ? (T)((double)s / W) : T(0);
+            if (sense[i] && a < T(0)) a = T(0);
+            ya[i] = a;
         }
     }
 }
@@ -614,7 +622,7 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
 {
     const int64_t m = h->m, n = h->n;
     k_check_prep<T><<<ew_grid(n + m), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.XS,
-                                                     E.YS, E.XA, E.YA, n, m);
+                                                     E.YS, E.XA, E.YA, E.l, E.u, h->sense, n, m);
     const int* gate = &E.ctrl->want_check;
     EpiStore<T> e1{E.XA, E.KXA, nullptr, nullptr, gate};
     launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, h->n, e1);

@@ -48,6 +48,6 @@ def test_powerlaw_1Mx2M_mixed_to_1e4(L, oracle_mod):
 def test_dispatch_615kx5k_mixed_to_1e4(L, oracle_mod):
     lp = synth.dispatch_lp()
     x, y, info, k = _check(L, oracle_mod, lp, 1e-4, 600)
-    # the box is enforced on FP32 iterates in scaled coordinates: one FP32 rounding
+    # the box is enforced in scaled FP32 coordinates: one FP32 rounding of x / C and back
     slack = 1e-6 * (1 + np.abs(lp.u))
     assert np.all(x >= lp.l - slack) and np.all(x <= lp.u + slack)
