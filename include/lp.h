@@ -177,10 +177,24 @@ lp_status lp_create(const lp_desc* desc, void* cuda_stream, lp_handle* out);
 lp_status lp_solve(lp_handle h, const lp_opts* opts, lp_result* res);
 
 /* Solves count independent LPs with the same options; results[i] belongs to
- * hs[i].  Returns LP_OK when every solve returned a non-negative status (the
- * per-LP outcomes are in results[i].status), else the first negative error. */
+ * hs[i] (lp_batch_create + lp_batch_solve + lp_batch_destroy).  Returns LP_OK
+ * when every LP has an outcome (in results[i].status), else a negative error. */
 lp_status lp_solve_batch(const lp_handle* hs, int32_t count, const lp_opts* opts,
                          lp_result* results);
+
+/* A batch: the LPs of count handles stacked into one block-diagonal problem on
+ * the device (copied from the handles; later changes to them are not seen).
+ * Solving it runs every LP's restarted PDHG together: one launch per kernel covers
+ * all LPs (warp tasks never span two LPs), while Ruiz stopping, the spectral norm,
+ * eta_0, omega_0, step sizes, restarts, primal weights and termination stay per LP
+ * exactly as in lp_solve; an LP that finishes stops consuming work.  The loop runs
+ * in one CUDA graph (device-side while condition) until every LP is done.
+ * LP_PREC_MIXED runs FP32 iterations with FP64 reductions to opts->tol (no FP64
+ * polish phase); traces and warm starts are not supported (ignored). */
+typedef struct lp_batch_s* lp_batch;
+lp_status lp_batch_create(const lp_handle* hs, int32_t count, void* cuda_stream, lp_batch* out);
+lp_status lp_batch_solve(lp_batch b, const lp_opts* opts, lp_result* results);
+void lp_batch_destroy(lp_batch b);
 
 /* Gradient of a loss L(x_K) through K_iters unrolled fixed-step PDHG
  * iterations (Algorithm 1, theta = 1, unscaled problem, start x = proj_X(0),

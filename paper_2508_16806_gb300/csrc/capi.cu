@@ -10,10 +10,6 @@
 
 using namespace pdhg;
 
-struct lp_problem_s {
-    Handle h;
-};
-
 namespace {
 
 double now_s()
@@ -259,12 +255,13 @@ lp_status lp_solve(lp_handle p, const lp_opts* o, lp_result* r)
 
 lp_status lp_solve_batch(const lp_handle* hs, int32_t count, const lp_opts* o, lp_result* rs)
 {
-    if (!hs || !rs || count < 0) return LP_INVALID_ARGUMENT;
-    for (int32_t i = 0; i < count; ++i) {
-        lp_status s = lp_solve(hs[i], o, &rs[i]);
-        if (s < 0) return s;
-    }
-    return LP_OK;
+    if (!hs || !rs || count < 1 || !o) return LP_INVALID_ARGUMENT;
+    lp_batch b = nullptr;
+    lp_status s = lp_batch_create(hs, count, hs[0] ? (void*)hs[0]->h.stream : nullptr, &b);
+    if (s != LP_OK) return s;
+    s = lp_batch_solve(b, o, rs);
+    lp_batch_destroy(b);
+    return s < 0 ? s : LP_OK;
 }
 
 lp_status lp_grad(lp_handle p, const lp_opts* o, int32_t K_iters, int32_t ckpt_every,

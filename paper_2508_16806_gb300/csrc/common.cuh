@@ -52,6 +52,7 @@ struct Ctrl {
     int rejects;         // consecutive rejected attempts (a guard against a stuck loop)
     unsigned int tick;   // finished blocks of the current K^T launch (last one runs the step control)
     long long bodies;    // loop-body executions (for the launch count)
+    long long t_done_ns; // device clock when the loop finished for this LP
 };
 
 // ------------------------------------------------------------- device buffers
@@ -131,6 +132,15 @@ struct Handle {
     long long launches = 0;      // kernels launched by the host (graph bodies counted apart)
     int built_precision_mask = 0;
 };
+
+}  // namespace pdhg
+
+// The opaque handle of the C ABI.
+struct lp_problem_s {
+    pdhg::Handle h;
+};
+
+namespace pdhg {
 
 template <typename T> Engine<T>& engine_of(Handle* h);
 template <> inline Engine<double>& engine_of<double>(Handle* h) { return h->e64; }
@@ -235,6 +245,19 @@ __device__ __forceinline__ unsigned long long global_ns()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// ------------------------------------------------------------ setup kernels
+// (defined in setup.cu; the batched solver launches them too)
+__global__ void k_row_inf(int64_t m, const int64_t* rp, const double* v, double* rn);
+__global__ void k_col_inf(int64_t nnz, const int32_t* ci, const double* v, unsigned long long* cn);
+__global__ void k_ruiz_factors(int64_t count, double* nrm, double* acc);
+__global__ void k_scale_vals(int64_t nnz, const int32_t* krow, const int32_t* ci, const double* r,
+                             const double* s, double* v);
+__global__ void k_pc_sums(int64_t m, int64_t n, const int64_t* rp, const int64_t* trp,
+                          const int32_t* tperm, const double* v, double* rs, double* cs);
+__global__ void k_scale_vectors(int64_t m, int64_t n, const double* R, const double* C,
+                                const double* c0, const double* q0, const double* l0,
+                                const double* u0, double* c, double* q, double* l, double* u);
 
 // ------------------------------------------------------------ entry points
 // setup.cu

@@ -51,6 +51,7 @@ __global__ void k_g_primal(const T* x, const T* kty, const T* c, const T* l, con
 // K x' + dual step of the unrolled forward, with the dual mask
 template <typename T>
 struct EpiGDual {
+    PDHG_SINGLE_LP_TASK_HOOKS
     const T* x;          // x' (being multiplied)
     const T* y;          // y
     const T* kx;         // K x
@@ -108,6 +109,7 @@ __global__ void k_g_gvx(const uint8_t* mx, T* gx, const T* gxbar, const double* 
 // reverse: gy <- gv_y + tau K gv_x (epilogue of the K gv_x product)
 template <typename T>
 struct EpiGy {
+    PDHG_SINGLE_LP_TASK_HOOKS
     const T* gvx;        // being multiplied
     const T* gvy;
     const double* coef;  // [0] = tau

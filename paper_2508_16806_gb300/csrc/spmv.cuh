@@ -23,9 +23,13 @@
 // Epilogue interface (Epi):
 //   bool begin()                        uniform per launch; false = return at once
 //   const T* xin()                      the vector being multiplied
+//   bool live(int task)                 false: skip the task (a finished LP of a batch)
+//   void task_start(int task)           per-task state, before its rows' operands load
 //   struct Pre; Pre load(int r)         operands of row r, loaded before the stream
 //   struct Acc; void row(int r, T v, const Pre&, Acc&)   once per row, one lane
+//   void task_done(int task, Acc&)      after a task's last row (all lanes)
 //   void finish(Acc&)                   block-level work at the end (all threads)
+// PDHG_SINGLE_LP_TASK_HOOKS supplies the no-op task hooks of a single LP.
 #pragma once
 
 #include "common.cuh"
@@ -244,7 +248,7 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStage<T>& W = reinterpret_cast<WarpStage<T>*>(smem_raw)[warp];
     typename Epi::Acc acc;
-    const T* __restrict__ xv = epi.xin();
+    const T* __restrict__ xv = epi.xin();   // re-read per task: a batch's LPs differ
     const int stride = gridDim.x * kTaskWarps;
     if (lane == 0) {
         mbar_init(&W.bar[0], 1);
@@ -253,7 +257,14 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
     }
     __syncwarp();
     const uint64_t pol = evict_first_policy();
-    int task = blockIdx.x * kTaskWarps + warp;
+    // the warp's tasks are t0, t0 + stride, ...; tasks the epilogue declares dead
+    // (a finished LP of a batch) are passed over
+    auto next_live = [&](int t) {
+        while (t < ntasks && !epi.live(t)) t += stride;
+        return t;
+    };
+    int task = next_live(blockIdx.x * kTaskWarps + warp);
+    int nt = ntasks;    // the next live task after `task`
     // current task [s, e), current chunk [cs, ce); next task bounds [ns, ne)
     int64_t s = 0, e = 0, ns = 0, ne = 0, cs = 0, ce = 0;
     if (task < ntasks) {
@@ -262,9 +273,10 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         cs = s;
         ce = e - s > CAPW ? s + CAPW : e;
         if (lane == 0 && ce > cs) stage_task<T>(W, 0, cs, ce, val, ci, pol);
-        if (task + stride < ntasks) {
-            ns = task_nz[task + stride];
-            ne = task_nz[task + stride + 1];
+        nt = next_live(task + stride);
+        if (nt < ntasks) {
+            ns = task_nz[nt];
+            ne = task_nz[nt + 1];
         }
     }
     uint32_t par = 0;   // bit st: parity of the next wait on stage st
@@ -284,7 +296,7 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
             xs = ce;
             xe = e - ce > CAPW ? ce + CAPW : e;
             have_next = true;
-        } else if (task + stride < ntasks) {
+        } else if (nt < ntasks) {
             xs = ns;
             xe = ne - ns > CAPW ? ns + CAPW : ne;
             have_next = true;
@@ -293,6 +305,8 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         const bool next_staged = have_next && xe > xs;
         if (next_staged && lane == 0) stage_task<T>(W, st ^ 1, xs, xe, val, ci, pol);
         if (first) {
+            epi.task_start(task);
+            xv = epi.xin();
             r0 = task_row[task];
             nrows = task_row[task + 1] - r0;
             if (lane < nrows) pre0 = epi.load(r0 + lane);
@@ -398,14 +412,18 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
             cs = xs;
             ce = xe;
         } else {
-            task += stride;
+            epi.task_done(task, acc);
+            task = nt;
             s = ns;
             e = ne;
             cs = xs;
             ce = xe;
-            if (task + stride < ntasks) {
-                ns = task_nz[task + stride];
-                ne = task_nz[task + stride + 1];
+            if (task < ntasks) {
+                nt = next_live(task + stride);
+                if (nt < ntasks) {
+                    ns = task_nz[nt];
+                    ne = task_nz[nt + 1];
+                }
             }
         }
     }
@@ -435,10 +453,19 @@ inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
                                                                val, err, l1, epi);
 }
 
+// The task hooks of an epilogue that serves a single LP: every task is live,
+// no per-task state.
+#define PDHG_SINGLE_LP_TASK_HOOKS                                   \
+    __device__ bool live(int) const { return true; }               \
+    __device__ void task_start(int) {}                              \
+    template <class A>                                              \
+    __device__ void task_done(int, A&) const {}
+
 // Plain epilogue: out[r] = scale * v, with the optional FP64 partial
 // sum of out[r]^2 (power iteration) and a gate read from a Ctrl field.
 template <typename T>
 struct EpiStore {
+    PDHG_SINGLE_LP_TASK_HOOKS
     const T* x;
     T* out;
     const double* scale;     // nullptr = 1

@@ -77,7 +77,8 @@ class LpResult(C.Structure):
 
 EXPORTS = ("lp_opts_default", "lp_create", "lp_solve", "lp_solve_batch", "lp_grad",
            "lp_unroll", "lp_update_values", "lp_profile_step", "lp_destroy", "lp_status_string",
-           "lp_abi_version", "lp_kkt_noalloc")
+           "lp_abi_version", "lp_kkt_noalloc", "lp_batch_create", "lp_batch_solve",
+           "lp_batch_destroy")
 
 _lib = None
 
@@ -122,6 +123,12 @@ def load(build_if_missing: bool = True):
     lib.lp_unroll.restype = C.c_int
     lib.lp_update_values.argtypes = [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int32]
     lib.lp_update_values.restype = C.c_int
+    lib.lp_batch_create.argtypes = [P(C.c_void_p), C.c_int32, C.c_void_p, P(C.c_void_p)]
+    lib.lp_batch_create.restype = C.c_int
+    lib.lp_batch_solve.argtypes = [C.c_void_p, P(LpOpts), C.c_void_p]
+    lib.lp_batch_solve.restype = C.c_int
+    lib.lp_batch_destroy.argtypes = [C.c_void_p]
+    lib.lp_batch_destroy.restype = None
     lib.lp_kkt_noalloc.argtypes = [P(LpDesc), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                    C.c_void_p]
     lib.lp_kkt_noalloc.restype = C.c_int
@@ -194,6 +201,24 @@ def lp_kkt_noalloc(desc: LpDesc, x: int, y: int, omega: float, stream: int | Non
     if s != 0:
         raise LpError(s, "lp_kkt_noalloc")
     return list(out)
+
+
+def lp_batch_create(handles, stream: int | None = None) -> C.c_void_p:
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h
+                                        for h in handles])
+    b = C.c_void_p()
+    s = load().lp_batch_create(arr, len(handles), C.c_void_p(stream or 0), C.byref(b))
+    if s != 0:
+        raise LpError(s, "lp_batch_create")
+    return b
+
+
+def lp_batch_solve(b, opts: LpOpts, results) -> int:
+    return load().lp_batch_solve(b, C.byref(opts), C.cast(results, C.c_void_p))
+
+
+def lp_batch_destroy(b) -> None:
+    load().lp_batch_destroy(b)
 
 
 def lp_destroy(h) -> None:
@@ -306,3 +331,49 @@ class Problem:
 
     def profile_step(self, precision: int = LP_PREC_FP64, reps: int = 20):
         return lp_profile_step(self.handle, precision, reps)
+
+
+class Batch:
+    """A batch of LPs (``synth.LP`` list) solved together by lp_batch_solve."""
+
+    def __init__(self, lps, device_copy: bool = True):
+        torch = _torch()
+        self.problems = [Problem(lp, device_copy=device_copy) for lp in lps]
+        self.stream = torch.cuda.Stream()
+        self.handle = lp_batch_create([p.handle for p in self.problems], self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            lp_batch_destroy(self.handle)
+            self.handle = None
+        for p in getattr(self, "problems", []):
+            p.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, **opts):
+        """Returns a list of (x, y, info) per LP."""
+        o = lp_opts_default(**opts)
+        B = len(self.problems)
+        res = (LpResult * B)()
+        xs, ys = [], []
+        for k, p in enumerate(self.problems):
+            x = np.empty(p.n)
+            y = np.empty(p.m)
+            xs.append(x)
+            ys.append(y)
+            res[k].x, res[k].y = x.ctypes.data, y.ctypes.data
+            res[k].memory_space = LP_MEM_HOST
+        s = lp_batch_solve(self.handle, o, res)
+        if s < 0:
+            raise LpError(s, "lp_batch_solve")
+        out = []
+        for k in range(B):
+            info = {f: getattr(res[k], f) for f, _ in LpResult._fields_
+                    if f not in ("x", "y", "trace", "reserved", "memory_space", "trace_cap")}
+            out.append((xs[k], ys[k], info))
+        return out

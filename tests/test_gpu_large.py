@@ -51,3 +51,19 @@ def test_dispatch_615kx5k_mixed_to_1e4(L, oracle_mod):
     # the box is enforced in scaled FP32 coordinates: one FP32 rounding of x / C and back
     slack = 1e-6 * (1 + np.abs(lp.u))
     assert np.all(x >= lp.l - slack) and np.all(x <= lp.u + slack)
+
+
+def test_batch_512_mixed_to_1e4(L, oracle_mod):
+    """The 512-LP batch (m log-uniform on 500..50,000, n = 2m, 5-20 nonzeros per
+    row): every LP reaches 1e-4; a sample is re-checked by the oracle in FP64."""
+    lps = synth.batch_lps()
+    batch = L.Batch(lps)
+    out = batch.solve(tol=1e-4, precision=L.LP_PREC_MIXED, time_limit_s=600)
+    batch.close()
+    statuses = [info["status"] for _, _, info in out]
+    assert all(s == L.LP_OPTIMAL for s in statuses), statuses
+    rng = np.random.default_rng(0)
+    for k in rng.choice(len(lps), 8, replace=False):
+        x, y, info = out[k]
+        kk = oracle_mod.kkt(lps[k], x, y)
+        assert max(kk["rel_gap"], kk["rel_pres"], kk["rel_dres"]) <= 1.5e-4
