@@ -234,11 +234,11 @@ __device__ __forceinline__ void stage_task(WarpStage<T>& W, int st, int64_t s, i
 // stage.  task_nz[t] = rp[task_row[t]].  A stage wait that exceeds 50 ms sets
 // *err and abandons the launch's remaining work after a second bounded wait for
 // the copy in flight.
-template <typename T, class Epi>
+template <typename T, class Epi, bool L1G>
 __global__ void __launch_bounds__(kSpmvNT, kSpmvMinBlocks)
 k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz, int ntasks,
        const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
-       int* err, int l1_gather, Epi epi)
+       int* err, Epi epi)
 {
     constexpr int CAPW = cap_w<T>();
     constexpr int VA = 16 / (int)sizeof(T);
@@ -310,7 +310,7 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
             r0 = task_row[task];
             nrows = task_row[task + 1] - r0;
             if (lane < nrows) pre0 = epi.load(r0 + lane);
-            if (lane + 32 < nrows) pre1 = epi.load(r0 + 32 + lane);
+            if (kTaskRows > 32 && lane + 32 < nrows) pre1 = epi.load(r0 + 32 + lane);
             if (!is_long)
                 for (int t = lane; t <= nrows; t += 32) W.rps[t] = rp[r0 + t];
             along = 0;
@@ -358,9 +358,12 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 const int p = off + v;
-                vv[k][v] = (p >= vo && p < lim)
-                               ? vv[k][v] * (l1_gather ? __ldg(xv + ii[k][v]) : ld_gather(xv + ii[k][v]))
-                               : T(0);
+                if (p >= vo && p < lim) {
+                    if constexpr (L1G) vv[k][v] *= __ldg(xv + ii[k][v]);
+                    else vv[k][v] *= ld_gather(xv + ii[k][v]);
+                } else {
+                    vv[k][v] = T(0);
+                }
             }
         }
         if (is_long) {
@@ -393,7 +396,7 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
                 for (int o = G >> 1; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o, G);
                 const T v = __shfl_sync(0xffffffffu, a, (lane * G) & 31);
                 if (lane < nrows) epi.row(r0 + lane, v, pre0, acc);
-            } else {
+            } else if (kTaskRows > 32) {
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     const int j = lane + 32 * half;
@@ -435,7 +438,11 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
 template <typename T, class Epi>
 inline cudaError_t spmv_prepare()
 {
-    return cudaFuncSetAttribute(k_spmv<T, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_spmv<T, Epi, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)spmv_smem_bytes<T>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_spmv<T, Epi, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)spmv_smem_bytes<T>());
 }
 
@@ -448,9 +455,13 @@ inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
                         const int64_t* task_nz, int ntasks, const int64_t* rp, const int32_t* ci,
                         const T* val, int* err, int64_t x_len, const Epi& epi)
 {
-    const int l1 = x_len * (int64_t)sizeof(T) <= kL1GatherBytes ? 1 : 0;
-    k_spmv<T, Epi><<<grid, kSpmvNT, spmv_smem_bytes<T>(), st>>>(task_row, task_nz, ntasks, rp, ci,
-                                                               val, err, l1, epi);
+    if (x_len * (int64_t)sizeof(T) <= kL1GatherBytes)
+        k_spmv<T, Epi, true><<<grid, kSpmvNT, spmv_smem_bytes<T>(), st>>>(task_row, task_nz, ntasks,
+                                                                         rp, ci, val, err, epi);
+    else
+        k_spmv<T, Epi, false><<<grid, kSpmvNT, spmv_smem_bytes<T>(), st>>>(task_row, task_nz,
+                                                                          ntasks, rp, ci, val, err,
+                                                                          epi);
 }
 
 // The task hooks of an epilogue that serves a single LP: every task is live,
