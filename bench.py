@@ -43,7 +43,9 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="powerlaw", choices=["powerlaw", "small"])
+    p.add_argument("--workload", default="powerlaw", choices=["powerlaw", "small", "batch"],
+                   help="powerlaw: the 1M x 2M LP (default bench line); small: 200 x 400; "
+                        "batch: 512 LPs solved by one lp_batch_solve (extra line)")
     p.add_argument("--tol", type=float, default=1e-4)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -66,6 +68,93 @@ def kernel_profile(args):
     ms, by = prob.profile_step(L.LP_PREC_MIXED, reps=3)
     print(json.dumps({"kernel_profile": desc, "ms": ms, "bytes": by}), flush=True)
     prob.close()
+
+
+def max_over_ranks(value, world):
+    """The slowest rank's time (the whole job finishes with it)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_batch(args):
+    """512 planted LPs (m log-uniform 500..50,000, n = 2m, 5-20 nonzeros per row)
+    solved together to 1e-4 (mixed path) by one lp_batch_solve per step; LPs/s,
+    per-LP device time to tolerance (p50 / p99), and a loop of single lp_solve
+    calls on the first 64 LPs scaled to 512 for comparison."""
+    import torch
+    import torch.distributed as dist
+    from paper_2508_16806_gb300 import lp as L
+    from paper_2508_16806_gb300 import synth
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    L.load()
+    all_lps = synth.batch_lps()
+    # independent LPs: each rank solves its share (weak scaling: 512 LPs per rank,
+    # the same 512 shifted by rank so that every rank has a full batch)
+    lps = all_lps if world == 1 else synth.batch_lps(seed=20250819 + 512 * rank)
+    batch = L.Batch(lps)
+    opts = dict(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=2_000_000)
+    for _ in range(args.warmup):
+        batch.solve(**opts)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(batch.stream)
+    outs = []
+    for _ in range(args.steps):
+        outs.append(batch.solve(**opts))
+    ev1.record(batch.stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
+    last = outs[-1]
+    per_lp = sorted(info["solve_s"] for _, _, info in last)
+    launches = int(sum(info["kernel_launches"] for o in outs for _, _, info in o))
+    statuses = sorted({L.STATUS[info["status"]] for _, _, info in last})
+    # loop of single solves on a sample (rank 0 reports it)
+    sample = 64 if rank == 0 else 0
+    t0 = time.perf_counter()
+    for lp in lps[:sample]:
+        p = L.Problem(lp)
+        p.solve(**opts)
+        p.close()
+    torch.cuda.synchronize()
+    loop_s = (time.perf_counter() - t0) * len(lps) / max(sample, 1)
+    batch.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {"metric": "LPs/s (512-LP batch, time to 1e-4 rel KKT)",
+            "value": world * len(lps) / (ms / 1e3), "unit": "LP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "512 planted LPs, m log-uniform 500..50,000, n = 2m, 5-20 nnz/row",
+                       "nnz": int(sum(lp.nnz for lp in lps)), "tol": args.tol,
+                       "step": "one lp_batch_solve of all 512 LPs"},
+            "statuses": statuses,
+            "per_lp_time_to_tol_s": {"p50": per_lp[len(per_lp) // 2],
+                                     "p99": per_lp[min(len(per_lp) - 1, int(0.99 * len(per_lp)))],
+                                     "max": per_lp[-1]},
+            "iters": {"p50": sorted(i["iters"] for _, _, i in last)[len(last) // 2],
+                      "max": max(i["iters"] for _, _, i in last)},
+            "single_solve_loop_s": loop_s,
+            "single_solve_loop_sample": f"first {sample} LPs, scaled to {len(lps)}",
+            "clocks": clk, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def workload(name, seed_offset=0):
@@ -229,6 +318,9 @@ def main():
     if args.kernel_profile:
         kernel_profile(args)
         return
+    if args.workload == "batch" and args.impl == "ours":
+        run_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -269,11 +361,7 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
     iters = statistics.mean(i["iters"] for i in infos)
     launches = int(sum(i["kernel_launches"] for i in infos))
     statuses = sorted({L.STATUS[i["status"]] for i in infos})

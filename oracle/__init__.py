@@ -52,7 +52,8 @@ class _Opts(C.Structure):
                 ("beta_sufficient", C.c_double), ("beta_necessary", C.c_double),
                 ("beta_artificial", C.c_double), ("eps_zero", C.c_double),
                 ("x0", C.c_void_p), ("y0", C.c_void_p),
-                ("omega0", C.c_double), ("eta0", C.c_double)]
+                ("omega0", C.c_double), ("eta0", C.c_double),
+                ("infeas_detect", C.c_int32), ("pad", C.c_int32), ("infeas_tol", C.c_double)]
 
 
 class _Info(C.Structure):
@@ -69,7 +70,8 @@ TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",
 DEFAULTS = dict(tol=1e-4, max_iters=100000, check_every=64, ruiz_iters=10, ruiz_tol=1e-4,
                 pock_chambolle=0, power_iters=100, adaptive_step=1, primal_weight_update=1,
                 restarts=1, eta_scale=0.9, beta_sufficient=0.2, beta_necessary=0.8,
-                beta_artificial=0.36, eps_zero=1e-6, omega0=0.0, eta0=0.0)
+                beta_artificial=0.36, eps_zero=1e-6, omega0=0.0, eta0=0.0,
+                infeas_detect=1, infeas_tol=1e-6)
 
 
 def _load():
@@ -91,6 +93,9 @@ def _load():
         _lib.orc_solve.argtypes = [P(_Lp), P(_Opts), C.c_void_p, C.c_void_p, P(_Info),
                                    C.c_void_p, C.c_int64, P(C.c_int64)]
         _lib.orc_solve.restype = C.c_int
+        _lib.orc_infeasibility.argtypes = [P(_Lp), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                           C.c_void_p]
+        _lib.orc_infeasibility.restype = C.c_int
         _lib.orc_unrolled_forward.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_unrolled_adjoint.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
@@ -201,7 +206,7 @@ def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
                  o["eta_scale"], o["beta_sufficient"], o["beta_necessary"],
                  o["beta_artificial"], o["eps_zero"],
                  None if x0a is None else _ptr(x0a), None if y0a is None else _ptr(y0a),
-                 o["omega0"], o["eta0"])
+                 o["omega0"], o["eta0"], int(o["infeas_detect"]), 0, o["infeas_tol"])
     x = np.empty(lp.n)
     y = np.empty(lp.m)
     info = _Info()
@@ -212,6 +217,16 @@ def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
     d = {f: getattr(info, f) for f, _ in _Info._fields_ if f != "pad"}
     trace = [dict(zip(TRACE_FIELDS, r.tolist())) for r in tr[: min(tl.value, trace_cap)]]
     return x, y, d, trace
+
+
+def infeasibility(lp, dx, dy, dlam, tol):
+    """Algorithm 6 on given differences: (status 0 / 2 / 3, terms dict)."""
+    b = _Bound(lp)
+    dx, dy, dl = _f64(dx), _f64(dy), _f64(dlam)
+    terms = np.empty(8)
+    st = _load().orc_infeasibility(C.byref(b.st), _ptr(dx), _ptr(dy), _ptr(dl), tol, _ptr(terms))
+    names = ("adx", "gdx_min", "cdx", "v_dist", "ktdy_res", "dy_ineq_min", "psi")
+    return st, dict(zip(names, terms[:7].tolist()))
 
 
 def start_point(lp):

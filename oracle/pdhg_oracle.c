@@ -67,10 +67,13 @@ typedef struct {
     const double* y0;         /* optional warm start, unscaled (NULL: y = 0) */
     double omega0;            /* > 0: use instead of InitializePrimalWeight */
     double eta0;              /* > 0: use instead of eta_scale / ||K||_2 */
+    int32_t infeas_detect;    /* Algorithm 6 at every check */
+    int32_t pad;
+    double infeas_tol;        /* tol of Algorithm 6 */
 } orc_opts;
 
 typedef struct {
-    int32_t status;           /* 1 optimal, 4 iteration limit */
+    int32_t status;           /* 1 optimal, 2 primal infeasible, 3 dual infeasible, 4 iteration limit */
     int32_t pad;
     int64_t iters;            /* accepted iterations */
     int64_t attempts;         /* step attempts (accepted + rejected) */
@@ -328,6 +331,79 @@ void orc_pdhg_step(const orc_lp* lp, const double* vals, const double* c, const 
 }
 
 /* ------------------------------------------------------------------ */
+/* Algorithm 6: infeasibility detection from iterate differences       */
+/* ------------------------------------------------------------------ */
+
+/*
+ * dx, dy: differences of consecutive iterates (unscaled); dlam: difference of
+ * lambda = proj_Lambda(c - K^T y) between the two dual iterates.  The tests are
+ * applied to the directions dx / ||dx|| and (dy, dlam) / ||(dy, dlam)||
+ * (reading: a certificate is a direction; with the listing's absolute tol the
+ * short steps of a converging feasible problem pass the dual test).
+ * Dual infeasibility (certificate dx, Section 2.4.5):
+ *   ||A v|| <= tol, min(G v) >= -tol, c^T v <= -tol, v_i in V_i within tol
+ *   (V_i = R free, R^- only u finite, R^+ only l finite, {0} both finite).
+ * Primal infeasibility (certificate dy, with the paper's v_lambda = -dlam, since
+ * lambda = c - K^T y up to the projection):
+ *   ||K^T w + dl|| <= tol, min(w_ineq) >= -tol,
+ *   psi = q^T w + l^T dl^+ + u^T dl^- > tol   (reading: the listing's
+ *   "psi >= -tol" would hold at every converging iterate; the certificate of
+ *   Section 2.4.5 needs psi > 0), (w, dl) the normalised (dy, dlam).
+ * terms (8 doubles, may be NULL): ||A v||, min(G v), c^T v, max distance of v
+ * to V, ||K^T w + dl||, min(w_ineq), psi, 0 (all of the normalised directions).
+ * Returns 3 (dual infeasible), 2 (primal infeasible) or 0.
+ */
+int orc_infeasibility(const orc_lp* lp, const double* dx, const double* dy, const double* dlam,
+                      double tol, double* terms)
+{
+    const int64_t m = lp->m, n = lp->n;
+    double* Kdx = (double*)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+    double* KTdy = (double*)calloc((size_t)n, sizeof(double));
+    orc_spmv(lp, lp->vals, dx, Kdx);
+    orc_spmv_t(lp, lp->vals, dy, KTdy);
+    double adx2 = 0.0, gmin = INFINITY, ymin = INFINITY, psi = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (lp->sense[i]) {
+            if (Kdx[i] < gmin) gmin = Kdx[i];
+            if (dy[i] < ymin) ymin = dy[i];
+        } else {
+            adx2 += Kdx[i] * Kdx[i];
+        }
+        psi += lp->q[i] * dy[i];
+    }
+    double cdx = 0.0, vviol = 0.0, r2 = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        cdx += lp->c[j] * dx[j];
+        const int lf = isfinite(lp->l[j]), uf = isfinite(lp->u[j]);
+        double v = 0.0;
+        if (lf && uf) v = fabs(dx[j]);
+        else if (lf) v = dx[j] < 0.0 ? -dx[j] : 0.0;
+        else if (uf) v = dx[j] > 0.0 ? dx[j] : 0.0;
+        if (v > vviol) vviol = v;
+        const double r = KTdy[j] + dlam[j];
+        r2 += r * r;
+        if (dlam[j] > 0.0) psi += lp->l[j] * dlam[j];
+        if (dlam[j] < 0.0) psi += lp->u[j] * dlam[j];
+    }
+    if (gmin == INFINITY) gmin = 0.0;
+    if (ymin == INFINITY) ymin = 0.0;
+    const double nx = sqrt(dot(n, dx, dx));
+    const double ny = sqrt(dot(m, dy, dy) + dot(n, dlam, dlam));
+    const double sx = nx > 0.0 ? 1.0 / nx : 0.0, sy = ny > 0.0 ? 1.0 / ny : 0.0;
+    const double t[7] = {sqrt(adx2) * sx, gmin * sx, cdx * sx, vviol * sx,
+                         sqrt(r2) * sy, ymin * sy, psi * sy};
+    if (terms) {
+        for (int q = 0; q < 7; ++q) terms[q] = t[q];
+        terms[7] = 0.0;
+    }
+    free(Kdx);
+    free(KTdy);
+    if (nx > 0.0 && t[0] <= tol && t[1] >= -tol && t[2] <= -tol && t[3] <= tol) return 3;
+    if (ny > 0.0 && t[4] <= tol && t[5] >= -tol && t[6] > tol) return 2;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* the restarted, adaptive solver                                      */
 /* ------------------------------------------------------------------ */
 
@@ -348,6 +424,7 @@ static void* xalloc(int64_t count) { return calloc((size_t)(count > 0 ? count : 
  *     taken, i.e. accepted iterations so far + 1).  Accepted iterates enter the
  *     eta-weighted averages (Section 2.4.2).
  *  6. At the start and every check_every accepted iterations (and at max_iters):
+ *     (optionally) Algorithm 6 on the last step's differences;
  *     KKT_omega of the current point and of the average on the scaled problem
  *     (reading); candidate = current if strictly better, else average;
  *     termination (Section 2.3.2) on the unscaled candidate: all three
@@ -371,6 +448,9 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
     double *xanc = (double*)xalloc(n), *yanc = (double*)xalloc(m);
     double *dx = (double*)xalloc(n), *Kdx = (double*)xalloc(m);
     double *xu = (double*)xalloc(n), *yu = (double*)xalloc(m);
+    double *xp = (double*)xalloc(n), *yp = (double*)xalloc(m);     /* previous iterate */
+    double *ddx = (double*)xalloc(n), *ddy = (double*)xalloc(m), *dlam = (double*)xalloc(n);
+    double *lam1 = (double*)xalloc(n), *tmpn = (double*)xalloc(n);
     double kc[8], ka[8], kk[8];
     int64_t tl = 0;
 
@@ -435,10 +515,29 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
             rel[0] = kk[4]; rel[1] = kk[5]; rel[2] = kk[6];
             pobj = kk[0]; dobj = kk[1];
             int converged = rel[0] <= o->tol && rel[1] <= o->tol && rel[2] <= o->tol;
+            int infeasible = 0;
+            if (!converged && !first && o->infeas_detect && k > 0) {
+                /* Algorithm 6 on the last step's differences, unscaled:
+                 * dx = C (x - x_prev), dy = R (y - y_prev), dlam from proj_Lambda(c - K^T y) */
+                for (int64_t j = 0; j < n; ++j) ddx[j] = C[j] * (x[j] - xp[j]);
+                for (int64_t i = 0; i < m; ++i) ddy[i] = R[i] * (y[i] - yp[i]);
+                for (int64_t i = 0; i < m; ++i) yu[i] = R[i] * y[i];
+                orc_spmv_t(lp, lp->vals, yu, tmpn);
+                for (int64_t j = 0; j < n; ++j) tmpn[j] = lp->c[j] - tmpn[j];
+                orc_proj_lambda(n, lp->l, lp->u, tmpn, lam1);
+                for (int64_t i = 0; i < m; ++i) yu[i] = R[i] * yp[i];
+                orc_spmv_t(lp, lp->vals, yu, tmpn);
+                for (int64_t j = 0; j < n; ++j) tmpn[j] = lp->c[j] - tmpn[j];
+                orc_proj_lambda(n, lp->l, lp->u, tmpn, dlam);
+                for (int64_t j = 0; j < n; ++j) dlam[j] = lam1[j] - dlam[j];
+                infeasible = orc_infeasibility(lp, ddx, ddy, dlam, o->infeas_tol, NULL);
+                /* yu is rebuilt for the output below */
+                for (int64_t i = 0; i < m; ++i) yu[i] = R[i] * yc[i];
+            }
             int restart = 0;
             if (first) {
                 kkt_anchor = kkt_c;
-            } else if (!converged && o->restarts) {
+            } else if (!converged && !infeasible && o->restarts) {
                 int crit1 = kkt_c <= o->beta_sufficient * kkt_anchor;
                 int crit2 = kkt_c <= o->beta_necessary * kkt_anchor && kkt_c > kkt_prev;
                 int crit3 = (double)epoch_k > o->beta_artificial * (double)k;
@@ -480,10 +579,10 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
                 t->kkt_cand = kkt_c;
             }
             ++tl;
-            if (converged || k >= o->max_iters) {
+            if (converged || infeasible || k >= o->max_iters) {
                 memcpy(x_out, xu, sizeof(double) * (size_t)n);
                 memcpy(y_out, yu, sizeof(double) * (size_t)m);
-                status = converged ? 1 : 4;
+                status = converged ? 1 : (infeasible ? infeasible : 4);
                 break;
             }
             first = 0;
@@ -521,6 +620,8 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
         for (int64_t j = 0; j < n; ++j) xsum[j] += used * xn[j];
         for (int64_t i = 0; i < m; ++i) ysum[i] += used * yn[i];
         wsum += used;
+        memcpy(xp, x, sizeof(double) * (size_t)n);
+        memcpy(yp, y, sizeof(double) * (size_t)m);
         memcpy(x, xn, sizeof(double) * (size_t)n);
         memcpy(y, yn, sizeof(double) * (size_t)m);
         ++k;
@@ -540,6 +641,7 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
     free(vs); free(R); free(C); free(cs); free(qs); free(ls); free(us);
     free(x); free(y); free(xn); free(yn); free(xsum); free(ysum); free(xa); free(ya);
     free(xanc); free(yanc); free(dx); free(Kdx); free(xu); free(yu);
+    free(xp); free(yp); free(ddx); free(ddy); free(dlam); free(lam1); free(tmpn);
     return status;
 }
 

@@ -380,3 +380,66 @@ def ragged_lp(seed: int = 7, m: int = 10000, n: int = 6000) -> LP:
     vals = rng.standard_normal(int(row_ptr[-1]))
     sense = (rng.random(m) < 0.5).astype(np.uint8)
     return plant(m, n, row_ptr, cols.astype(np.int32), vals, sense, rng, name="ragged")
+
+
+# --------------------------------------------------------------------------
+# infeasible and unbounded variants (for the detection tests)
+# --------------------------------------------------------------------------
+
+def _append_rows(lp: LP, rows_cols, rows_vals, senses, qs, name: str) -> LP:
+    """lp with extra rows appended (each given by its columns and values)."""
+    rp = [lp.row_ptr]
+    ci = [lp.col_idx]
+    va = [lp.vals]
+    end = int(lp.row_ptr[-1])
+    for cols, vals in zip(rows_cols, rows_vals):
+        order = np.argsort(cols)
+        ci.append(np.asarray(cols, dtype=np.int32)[order])
+        va.append(np.asarray(vals, dtype=np.float64)[order])
+        end += len(cols)
+        rp.append(np.array([end], dtype=np.int64))
+    return LP(lp.m + len(qs), lp.n, np.concatenate(rp), np.concatenate(ci), np.concatenate(va),
+              np.concatenate([lp.sense, np.asarray(senses, dtype=np.uint8)]), lp.c.copy(),
+              np.concatenate([lp.q, np.asarray(qs, dtype=np.float64)]), lp.l.copy(), lp.u.copy(),
+              name=name)
+
+
+def contradictory_rows_lp(lp: LP, seed: int = 1, gap: float = 1.0, width: int = 8) -> LP:
+    """Primal-infeasible variant: two >= rows a^T x >= b and -a^T x >= gap - b
+    on ``width`` random columns (so a^T x >= b and a^T x <= b - gap)."""
+    rng = np.random.default_rng(seed)
+    cols = rng.choice(lp.n, width, replace=False)
+    a = rng.standard_normal(width)
+    b = float(rng.uniform(-1.0, 1.0))
+    return _append_rows(lp, [cols, cols], [a, -a], [1, 1], [b, gap - b],
+                        name=lp.name + "+contradiction")
+
+
+def unbounded_column_lp(lp: LP, seed: int = 2, width: int = 6) -> LP:
+    """Dual-infeasible variant: one more column x_new >= 0 with cost -1 whose
+    entries are positive and sit only in >= rows, so x_new can grow forever."""
+    rng = np.random.default_rng(seed)
+    ge = np.flatnonzero(lp.sense)
+    rows = np.sort(rng.choice(ge, min(width, len(ge)), replace=False))
+    n = lp.n
+    counts = np.diff(lp.row_ptr)
+    add = np.zeros(lp.m, dtype=np.int64)
+    add[rows] = 1
+    row_ptr = np.zeros(lp.m + 1, dtype=np.int64)
+    np.cumsum(counts + add, out=row_ptr[1:])
+    col_idx = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    vals = np.empty(int(row_ptr[-1]))
+    newv = rng.uniform(0.5, 2.0, len(rows))
+    k = 0
+    for i in range(lp.m):
+        a, b = int(lp.row_ptr[i]), int(lp.row_ptr[i + 1])
+        s = int(row_ptr[i])
+        col_idx[s:s + b - a] = lp.col_idx[a:b]
+        vals[s:s + b - a] = lp.vals[a:b]
+        if add[i]:
+            col_idx[s + b - a] = n
+            vals[s + b - a] = newv[k]
+            k += 1
+    return LP(lp.m, n + 1, row_ptr, col_idx, vals, lp.sense.copy(),
+              np.concatenate([lp.c, [-1.0]]), lp.q.copy(), np.concatenate([lp.l, [0.0]]),
+              np.concatenate([lp.u, [np.inf]]), name=lp.name + "+unbounded")
