@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define LP_ABI_VERSION 1
+#define LP_ABI_VERSION 2
 
 typedef struct lp_problem_s* lp_handle;
 
@@ -111,6 +111,12 @@ typedef struct {
                                     device-side while condition; 1: the host launches the loop
                                     body graph and reads the stop flag after each body (for
                                     profilers that cannot see kernels under a conditional node) */
+    int32_t infeas_detect;       /* 1 (default): Algorithm 6 (Section 2.4.5) at every KKT check on
+                                    the last step's differences; a solve that finds a certificate
+                                    stops with LP_PRIMAL_INFEASIBLE or LP_DUAL_INFEASIBLE */
+    int32_t reserved_opts;       /* must be 0 */
+    double infeas_tol;           /* tolerance of Algorithm 6, applied to the differences
+                                    normalised to unit length (default 1e-6) */
 } lp_opts;
 
 /* One record per KKT check (the start, every check_every accepted

@@ -55,7 +55,7 @@ struct BatchSched {
     int32_t *lpK = nullptr, *lpT = nullptr;          // task -> LP
     int32_t *t0K = nullptr, *t0T = nullptr;          // LP -> first task [B + 1]
     double *partK = nullptr, *partT = nullptr;       // per-task step partials [1 | 2][nt]
-    double *partR = nullptr, *partC = nullptr;       // per-task check partials [8 | 10][nt]
+    double *partR = nullptr, *partC = nullptr;       // per-task check partials [kRowQ | kColQ][nt]
     int gK = 0, gT = 0;
 };
 
@@ -334,6 +334,15 @@ __device__ __forceinline__ double warp_range_sum(const double* part, int a, int 
     return warp_sum(s);   // lane 0
 }
 
+// maximum of part[a..b) (0 when empty) by one warp; the result is valid in lane 0
+__device__ double warp_range_max(const double* part, int a, int b)
+{
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = a + lane; i < b; i += 32) s = fmax(s, __ldcg(part + i));
+    return warp_max(s);   // lane 0
+}
+
 // one warp per LP: Algorithm 5 decision from the LP's task partials
 __global__ void kb_step_ctrl(Ctrl* ctrl, int B, const int32_t* t0K, const int32_t* t0T,
                              const double* partK, const double* partT, int ntT)
@@ -397,9 +406,13 @@ __global__ void kb_check_rows(const Ctrl* ctrl, const int32_t* taskK, const int3
     if (t >= ntK) return;
     const Ctrl& C = ctrl[lpK[t]];
     if (!C.want_check) return;
+    const bool inf = infeas_active(C);
     const T* y = C.cur ? y1 : y0;
     const T* kx = C.cur ? kx1 : kx0;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const T* yp = C.cur ? y0 : y1;
+    const T* kxp = C.cur ? kx0 : kx1;
+    double v[kRowQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    InfeasRow ir;
     for (int i = taskK[t] + lane; i < taskK[t + 1]; i += 32) {
         const double qi = (double)q[i], Ri = R[i];
         const bool ge = sense[i] != 0;
@@ -418,10 +431,16 @@ __global__ void kb_check_rows(const Ctrl* ctrl, const int32_t* taskK, const int3
         const double yv = (double)ya[i];
         v[6] += qi * yv;
         v[7] += (yv - yan) * (yv - yan);
+        if (inf) ir.add((double)kx[i], (double)kxp[i], yc, (double)yp[i], qi, Ri, ge);
     }
+    v[8] = ir.adx2;
+    v[9] = ir.dy2;
+    v[10] = ir.psi;
+    v[11] = ir.gneg;
+    v[12] = ir.yneg;
 #pragma unroll
-    for (int qq = 0; qq < 8; ++qq) {
-        const double s = warp_sum(v[qq]);
+    for (int qq = 0; qq < kRowQ; ++qq) {
+        const double s = qq < kRowSums ? warp_sum(v[qq]) : warp_max(v[qq]);
         if (lane == 0) part[(size_t)qq * ntK + t] = s;
     }
 }
@@ -438,9 +457,13 @@ __global__ void kb_check_cols(const Ctrl* ctrl, const int32_t* taskT, const int3
     if (t >= ntT) return;
     const Ctrl& CC = ctrl[lpT[t]];
     if (!CC.want_check) return;
+    const bool inf = infeas_active(CC);
     const T* x = CC.cur ? x1 : x0;
     const T* kty = CC.cur ? kty1 : kty0;
-    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const T* xp = CC.cur ? x0 : x1;
+    const T* ktyp = CC.cur ? kty0 : kty1;
+    double v[kColQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    InfeasCol ic;
     for (int j = taskT[t] + lane; j < taskT[t + 1]; j += 32) {
         const double cj = (double)c[j], lj = (double)l[j], uj = (double)u[j], Cj = Cs[j];
         const bool lf = isfinite(lj), uf = isfinite(uj);
@@ -448,11 +471,7 @@ __global__ void kb_check_cols(const Ctrl* ctrl, const int32_t* taskT, const int3
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const double vj = cj - (double)(side ? ktya[j] : kty[j]);
-            double lam;
-            if (!lf && !uf) lam = 0.0;
-            else if (!lf) lam = vj < 0.0 ? vj : 0.0;
-            else if (!uf) lam = vj > 0.0 ? vj : 0.0;
-            else lam = vj;
+            const double lam = proj_lambda(vj, lf, uf);
             const double d = vj - lam;
             const double xv = (double)(side ? xa[j] : x[j]);
             double lt = 0.0;
@@ -464,10 +483,19 @@ __global__ void kb_check_cols(const Ctrl* ctrl, const int32_t* taskT, const int3
             v[5 * side + 3] += lt;
             v[5 * side + 4] += (xv - xan) * (xv - xan);
         }
+        if (inf)
+            ic.add((double)x[j], (double)xp[j], (double)kty[j], (double)ktyp[j], cj, lj, uj, Cj,
+                   lf, uf);
     }
+    v[10] = ic.dx2;
+    v[11] = ic.cdx;
+    v[12] = ic.r2;
+    v[13] = ic.dl2;
+    v[14] = ic.psi;
+    v[15] = ic.vviol;
 #pragma unroll
-    for (int qq = 0; qq < 10; ++qq) {
-        const double s = warp_sum(v[qq]);
+    for (int qq = 0; qq < kColQ; ++qq) {
+        const double s = qq < kColSums ? warp_sum(v[qq]) : warp_max(v[qq]);
         if (lane == 0) part[(size_t)qq * ntT + t] = s;
     }
 }
@@ -480,10 +508,13 @@ __global__ void kb_check_ctrl(Ctrl* ctrl, int B, const int32_t* t0K, const int32
     if (k >= B) return;
     Ctrl* c = ctrl + k;
     if (!c->want_check) return;
-    double r[8], cc[10];
-    for (int q = 0; q < 8; ++q) r[q] = warp_range_sum(partR + (size_t)q * ntK, t0K[k], t0K[k + 1]);
-    for (int q = 0; q < 10; ++q)
-        cc[q] = warp_range_sum(partC + (size_t)q * ntT, t0T[k], t0T[k + 1]);
+    double r[kRowQ], cc[kColQ];
+    for (int q = 0; q < kRowQ; ++q)
+        r[q] = q < kRowSums ? warp_range_sum(partR + (size_t)q * ntK, t0K[k], t0K[k + 1])
+                            : warp_range_max(partR + (size_t)q * ntK, t0K[k], t0K[k + 1]);
+    for (int q = 0; q < kColQ; ++q)
+        cc[q] = q < kColSums ? warp_range_sum(partC + (size_t)q * ntT, t0T[k], t0T[k + 1])
+                             : warp_range_max(partC + (size_t)q * ntT, t0T[k], t0T[k + 1]);
     if ((threadIdx.x & 31) == 0) check_decide(c, r, cc, nullptr);
 }
 
@@ -700,8 +731,8 @@ lp_status build_sched(BatchHandle* bh)
     LP_TRY(up64(&S.nzT, nT));
     LP_TRY(dev_alloc_n(h, &S.partK, (size_t)S.ntK + 8));
     LP_TRY(dev_alloc_n(h, &S.partT, 2 * (size_t)S.ntT + 8));
-    LP_TRY(dev_alloc_n(h, &S.partR, 8 * (size_t)S.ntK + 8));
-    LP_TRY(dev_alloc_n(h, &S.partC, 10 * (size_t)S.ntT + 8));
+    LP_TRY(dev_alloc_n(h, &S.partR, kRowQ * (size_t)S.ntK + 8));
+    LP_TRY(dev_alloc_n(h, &S.partC, kColQ * (size_t)S.ntT + 8));
     LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
     // vectors and scaled data of this precision
     Engine<T>& E = engine_of<T>(h);
@@ -964,6 +995,8 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
     tmpl.adaptive = o->adaptive_step ? 1 : 0;
     tmpl.pwu = o->primal_weight_update ? 1 : 0;
     tmpl.restarts_on = o->restarts ? 1 : 0;
+    tmpl.infeas = o->infeas_detect ? 1 : 0;
+    tmpl.infeas_tol = o->infeas_tol;
     tmpl.check_every = o->check_every;
     unsigned long long* tns = reinterpret_cast<unsigned long long*>(bh->lpd + 6 * B);
     kb_read_clock<<<1, 1, 0, st>>>(tns);

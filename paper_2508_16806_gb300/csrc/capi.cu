@@ -39,6 +39,8 @@ lp_status check_opts(const lp_opts* o)
         return LP_INVALID_ARGUMENT;
     if (o->precision != LP_PREC_FP64 && o->precision != LP_PREC_MIXED) return LP_INVALID_ARGUMENT;
     if (o->loop_mode != 0 && o->loop_mode != 1) return LP_INVALID_ARGUMENT;
+    if (o->infeas_detect != 0 && o->infeas_detect != 1) return LP_INVALID_ARGUMENT;
+    if (o->infeas_detect && !(o->infeas_tol > 0.0)) return LP_INVALID_ARGUMENT;
     return LP_OK;
 }
 
@@ -89,6 +91,8 @@ void lp_opts_default(lp_opts* o)
     o->eta0 = 0.0;
     o->warm_memory_space = LP_MEM_HOST;
     o->loop_mode = 0;
+    o->infeas_detect = 1;
+    o->infeas_tol = 1e-6;
 }
 
 const char* lp_status_string(lp_status s)

@@ -18,6 +18,9 @@ constexpr int kNT = 256;          // threads of an SpMV row-block
 constexpr int kEW = 256;          // threads of an elementwise block
 constexpr int kEWGrid = 1216;     // elementwise grid cap: 152 SMs x 8 resident blocks
 constexpr int kCtlNT = 512;       // threads of a control (single-block) kernel
+// KKT-check reductions: row side 11 sums + 2 maxima, column side 15 sums + 1 maximum
+constexpr int kRowSums = 11, kRowMax = 2, kRowQ = kRowSums + kRowMax;
+constexpr int kColSums = 15, kColMax = 1, kColQ = kColSums + kColMax;
 
 // status codes shared with the ABI
 constexpr int kRunning = -100;
@@ -38,6 +41,7 @@ struct Ctrl {
     double tol, beta_s, beta_n, beta_a, eps_zero;
     double qnorm, cnorm;         // ||q||_2, ||c||_2 of the unscaled problem
     double time_limit_ns;
+    double infeas_tol;   // Algorithm 6 tolerance (normalised directions)
     // counters
     long long k, attempts, epoch_k, restarts, max_iters, t0_ns, trace_len, trace_cap;
     int cur;             // which half of each double buffer holds the current iterate
@@ -49,6 +53,7 @@ struct Ctrl {
     int cand_avg;        // candidate of the last check is the average
     int restart;         // the last check restarted
     int adaptive, pwu, restarts_on, check_every;
+    int infeas;          // Algorithm 6 at every check
     int rejects;         // consecutive rejected attempts (a guard against a stuck loop)
     unsigned int tick;   // finished blocks of the current K^T launch (last one runs the step control)
     long long bodies;    // loop-body executions (for the launch count)
@@ -87,8 +92,8 @@ struct Engine {
     // reduction partials
     double* partD = nullptr;   // [gK]
     double* partT = nullptr;   // [2][gT]
-    double* partR = nullptr;   // [8][kEWGrid]
-    double* partC = nullptr;   // [10][kEWGrid]
+    double* partR = nullptr;   // [kRowQ][kEWGrid]
+    double* partC = nullptr;   // [kColQ][kEWGrid]
     Ctrl* ctrl = nullptr;
     lp_trace_rec* trace = nullptr;  // device trace ring
     long long trace_cap = 0;
@@ -204,6 +209,58 @@ __device__ __forceinline__ void block_partials(const double (&v)[NQ], double* pa
             if (lane == 0) part[(size_t)q * stride + blockIdx.x] = t;
         }
     }
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block maxima of NQ per-thread values into part[q * stride + blockIdx.x].
+template <int NQ, int NT>
+__device__ __forceinline__ void block_partials_max(const double (&v)[NQ], double* part, int stride)
+{
+    __shared__ double sh[NQ][NT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double t = warp_max(v[q]);
+        if (lane == 0) sh[q][warp] = t;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = lane < NT / 32 ? sh[q][lane] : -INFINITY;
+            t = warp_max(t);
+            if (lane == 0) part[(size_t)q * stride + blockIdx.x] = t;
+        }
+    }
+}
+
+// Maximum of part[0..count) by a whole block (valid in every thread).
+template <int NT>
+__device__ double block_max_array(const double* part, int count)
+{
+    __shared__ double sh[NT / 32];
+    __shared__ double total;
+    double s = -INFINITY;
+    for (int i = threadIdx.x; i < count; i += NT) s = fmax(s, __ldcg(part + i));
+    s = warp_max(s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        double t = lane < NT / 32 ? sh[lane] : -INFINITY;
+        t = warp_max(t);
+        if (lane == 0) total = t;
+    }
+    __syncthreads();
+    double r = total;
+    __syncthreads();
+    return r;
 }
 
 // Fixed-order sum of part[0..count) by a whole block of NT threads; the

@@ -8,6 +8,80 @@
 
 namespace pdhg {
 
+// lambda = proj_Lambda(v) (Section 2.3.1): Lambda_j = {0}, R^-, R^+ or R by
+// which of l_j, u_j is finite.
+__device__ __forceinline__ double proj_lambda(double v, bool lf, bool uf)
+{
+    if (!lf && !uf) return 0.0;
+    if (!lf) return v < 0.0 ? v : 0.0;
+    if (!uf) return v > 0.0 ? v : 0.0;
+    return v;
+}
+
+// Algorithm 6 terms of one row from the current and the previous iterate.
+// With K~ = R K C, y = R y~ and x = C x~: (K dx)_i = (K~ dx~)_i / R_i,
+// dy_i = R_i dy~_i and q_i dy_i = q~_i dy~_i, so the unscaled directions come
+// from the stored scaled iterates and products.
+struct InfeasRow {
+    double adx2 = 0.0;   // ||A dx||^2 (equality rows)
+    double dy2 = 0.0;    // ||dy||^2
+    double psi = 0.0;    // q^T dy
+    double gneg = 0.0;   // max(0, max -(G dx)_i)  (>= rows)
+    double yneg = 0.0;   // max(0, max -dy_i)      (>= rows)
+    __device__ void add(double kx, double kxp, double y, double yp, double q, double R, bool ge)
+    {
+        const double adx = (kx - kxp) / R;
+        const double dys = y - yp;
+        const double dy = R * dys;
+        if (ge) {
+            gneg = fmax(gneg, -adx);
+            yneg = fmax(yneg, -dy);
+        } else {
+            adx2 += adx * adx;
+        }
+        dy2 += dy * dy;
+        psi += q * dys;
+    }
+};
+
+// Algorithm 6 terms of one column: dx_j = C_j dx~_j, c_j dx_j = c~_j dx~_j,
+// (K^T dy)_j = (K~^T dy~)_j / C_j, dlambda_j = dlambda~_j / C_j and
+// l_j dlambda_j = l~_j dlambda~_j (lambda~ = proj_Lambda(c~ - K~^T y~)).
+struct InfeasCol {
+    double dx2 = 0.0;    // ||dx||^2
+    double cdx = 0.0;    // c^T dx
+    double r2 = 0.0;     // ||K^T dy + dlambda||^2
+    double dl2 = 0.0;    // ||dlambda||^2
+    double psi = 0.0;    // l^T dlambda^+ + u^T dlambda^-
+    double vviol = 0.0;  // max distance of dx_j to V_j
+    __device__ void add(double x, double xp, double kty, double ktyp, double c, double l,
+                        double u, double C, bool lf, bool uf)
+    {
+        const double dxs = x - xp;
+        const double dx = C * dxs;
+        dx2 += dx * dx;
+        cdx += c * dxs;
+        double v = 0.0;
+        if (lf && uf) v = fabs(dx);
+        else if (lf) v = dx < 0.0 ? -dx : 0.0;
+        else if (uf) v = dx > 0.0 ? dx : 0.0;
+        vviol = fmax(vviol, v);
+        const double dls = proj_lambda(c - kty, lf, uf) - proj_lambda(c - ktyp, lf, uf);
+        const double dl = dls / C;
+        const double r = (kty - ktyp) / C + dl;
+        r2 += r * r;
+        dl2 += dl * dl;
+        if (dls > 0.0) psi += l * dls;
+        if (dls < 0.0) psi += u * dls;
+    }
+};
+
+// Whether the check kernels evaluate Algorithm 6 for this control block.
+__device__ __forceinline__ bool infeas_active(const Ctrl& c)
+{
+    return c.infeas && !c.first && c.k > 0;
+}
+
 // Algorithm 5 decision (or the plain swap of a fixed step), by one thread.
 // The paper's k is read as the 1-based index of the iteration being taken.
 __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, double dx2, double inter)
@@ -66,8 +140,8 @@ __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, d
 // KKT_omega (Section 2.4.2) of the current point and of the average, the
 // restart candidate, the termination test on the unscaled problem (Section
 // 2.3.2), the three restart criteria (Section 2.4.2) and Algorithm 4, by one
-// thread.  r[8] and cc[10] are the row- and column-side sums of k_check_rows /
-// k_check_cols.
+// thread.  r[kRowQ] and cc[kColQ] are the row- and column-side reductions of
+// k_check_rows / k_check_cols.
 __device__ __forceinline__ void check_decide(Ctrl* ctrl, const double* r, const double* cc,
                                              lp_trace_rec* trace)
 {
@@ -92,10 +166,25 @@ __device__ __forceinline__ void check_decide(Ctrl* ctrl, const double* r, const 
     const double rel_dres = dres_u / (1.0 + ctrl->cnorm);
     const int converged = rel_gap <= ctrl->tol && rel_pres <= ctrl->tol && rel_dres <= ctrl->tol;
     const int first = ctrl->first;
+    // Algorithm 6 on the last step's differences, as normalised directions:
+    // row side r[8] ||A dx||^2, r[9] ||dy||^2, r[10] q^T dy, r[11] max(-G dx), r[12] max(-dy_ineq);
+    // column side cc[10] ||dx||^2, cc[11] c^T dx, cc[12] ||K^T dy + dlam||^2, cc[13] ||dlam||^2,
+    // cc[14] l^T dlam^+ + u^T dlam^-, cc[15] max distance of dx to V
+    int infeasible = 0;
+    if (!converged && infeas_active(*ctrl)) {
+        const double t = ctrl->infeas_tol;
+        const double nx = sqrt(cc[10]), ny = sqrt(r[9] + cc[13]);
+        if (nx > 0.0 && sqrt(r[8]) / nx <= t && -r[11] / nx >= -t && cc[11] / nx <= -t &&
+            cc[15] / nx <= t)
+            infeasible = LP_DUAL_INFEASIBLE;
+        else if (ny > 0.0 && sqrt(cc[12]) / ny <= t && -r[12] / ny >= -t &&
+                 (r[10] + cc[14]) / ny > t)
+            infeasible = LP_PRIMAL_INFEASIBLE;
+    }
     int restart = 0;
     if (first) {
         ctrl->kkt_anchor = kkt_cand;
-    } else if (!converged && ctrl->restarts_on) {
+    } else if (!converged && !infeasible && ctrl->restarts_on) {
         const int c1 = kkt_cand <= ctrl->beta_s * ctrl->kkt_anchor;
         const int c2 = kkt_cand <= ctrl->beta_n * ctrl->kkt_anchor && kkt_cand > ctrl->kkt_prev;
         const int c3 = (double)ctrl->epoch_k > ctrl->beta_a * (double)ctrl->k;
@@ -153,6 +242,9 @@ __device__ __forceinline__ void check_decide(Ctrl* ctrl, const double* r, const 
         ctrl->done = 1;
     } else if (converged) {
         ctrl->status = LP_OPTIMAL;
+        ctrl->done = 1;
+    } else if (infeasible) {
+        ctrl->status = infeasible;
         ctrl->done = 1;
     } else if (ctrl->k >= ctrl->max_iters) {
         ctrl->status = LP_ITERATION_LIMIT;

@@ -635,8 +635,8 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         for (T** p : vm) LP_TRY(dev_alloc_n(h, p, (size_t)m));
         LP_TRY(dev_alloc_n(h, &E.partD, (size_t)E.gK + 8));
         LP_TRY(dev_alloc_n(h, &E.partT, 2 * (size_t)E.gT + 8));
-        LP_TRY(dev_alloc_n(h, &E.partR, 8 * (size_t)kEWGrid));
-        LP_TRY(dev_alloc_n(h, &E.partC, 10 * (size_t)kEWGrid));
+        LP_TRY(dev_alloc_n(h, &E.partR, kRowQ * (size_t)kEWGrid));
+        LP_TRY(dev_alloc_n(h, &E.partC, kColQ * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.ctrl, 1));
         E.ready = true;
     }

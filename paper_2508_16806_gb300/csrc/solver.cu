@@ -233,6 +233,8 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
 // Row side of the KKT terms for the current point and the average:
 // [0] sum r_s^2  [1] sum (r_s / R)^2  [2] q~^T y  [3] ||y - y_anchor||^2   (current)
 // [4..7] the same for the average.  r = q~ - K~ x, clamped at 0 on >= rows.
+// [8..10] ||A dx||^2, ||dy||^2, q^T dy and the maxima [11] -(G dx), [12] -dy_ineq
+// of Algorithm 6 on the last step (zero unless the check runs it).
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_check_rows(const Ctrl* __restrict__ ctrl, const T* y0, const T* y1, const T* kx0,
@@ -241,9 +243,13 @@ k_check_rows(const Ctrl* __restrict__ ctrl, const T* y0, const T* y1, const T* k
 {
     if (!ctrl->want_check) return;
     const int cur = ctrl->cur;
+    const bool inf = infeas_active(*ctrl);
     const T* y = cur ? y1 : y0;
     const T* kx = cur ? kx1 : kx0;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const T* yp = cur ? y0 : y1;
+    const T* kxp = cur ? kx0 : kx1;
+    double v[kRowSums] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    InfeasRow ir;
     for (int64_t i = (int64_t)blockIdx.x * kEW + threadIdx.x; i < m; i += (int64_t)gridDim.x * kEW) {
         const double qi = (double)q[i], Ri = R[i];
         const bool ge = sense[i] != 0;
@@ -262,13 +268,22 @@ k_check_rows(const Ctrl* __restrict__ ctrl, const T* y0, const T* y1, const T* k
         const double yv = (double)ya[i];
         v[6] += qi * yv;
         v[7] += (yv - ya_) * (yv - ya_);
+        if (inf) ir.add((double)kx[i], (double)kxp[i], yc, (double)yp[i], qi, Ri, ge);
     }
-    block_partials<8, kEW>(v, part, gridDim.x);
+    v[8] = ir.adx2;
+    v[9] = ir.dy2;
+    v[10] = ir.psi;
+    const double mx[kRowMax] = {ir.gneg, ir.yneg};
+    block_partials<kRowSums, kEW>(v, part, gridDim.x);
+    block_partials_max<kRowMax, kEW>(mx, part + (size_t)kRowSums * gridDim.x, gridDim.x);
 }
 
 // Column side: [0] sum d_s^2  [1] sum (d_s / C)^2  [2] c~^T x
 // [3] l~^T lambda^+ + u~^T lambda^-  [4] ||x - x_anchor||^2  (current), [5..9] average;
 // d = v - lambda, v = c~ - K~^T y, lambda = proj_Lambda(v).
+// [10..14] ||dx||^2, c^T dx, ||K^T dy + dlambda||^2, ||dlambda||^2,
+// l^T dlambda^+ + u^T dlambda^- and the maximum [15] distance of dx to V
+// (Algorithm 6 on the last step; zero unless the check runs it).
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_check_cols(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* kty0,
@@ -277,9 +292,13 @@ k_check_cols(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* k
 {
     if (!ctrl->want_check) return;
     const int cur = ctrl->cur;
+    const bool inf = infeas_active(*ctrl);
     const T* x = cur ? x1 : x0;
     const T* kty = cur ? kty1 : kty0;
-    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const T* xp = cur ? x0 : x1;
+    const T* ktyp = cur ? kty0 : kty1;
+    double v[kColSums] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    InfeasCol ic;
     for (int64_t j = (int64_t)blockIdx.x * kEW + threadIdx.x; j < n; j += (int64_t)gridDim.x * kEW) {
         const double cj = (double)c[j], lj = (double)l[j], uj = (double)u[j], Cj = C[j];
         const bool lf = isfinite(lj), uf = isfinite(uj);
@@ -287,11 +306,7 @@ k_check_cols(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* k
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const double vj = cj - (double)(side ? ktya[j] : kty[j]);
-            double lam;
-            if (!lf && !uf) lam = 0.0;
-            else if (!lf) lam = vj < 0.0 ? vj : 0.0;
-            else if (!uf) lam = vj > 0.0 ? vj : 0.0;
-            else lam = vj;
+            const double lam = proj_lambda(vj, lf, uf);
             const double d = vj - lam;
             const double xv = (double)(side ? xa[j] : x[j]);
             double lt = 0.0;
@@ -303,8 +318,18 @@ k_check_cols(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* k
             v[5 * side + 3] += lt;
             v[5 * side + 4] += (xv - xan) * (xv - xan);
         }
+        if (inf)
+            ic.add((double)x[j], (double)xp[j], (double)kty[j], (double)ktyp[j], cj, lj, uj, Cj,
+                   lf, uf);
     }
-    block_partials<10, kEW>(v, part, gridDim.x);
+    v[10] = ic.dx2;
+    v[11] = ic.cdx;
+    v[12] = ic.r2;
+    v[13] = ic.dl2;
+    v[14] = ic.psi;
+    const double mx[kColMax] = {ic.vviol};
+    block_partials<kColSums, kEW>(v, part, gridDim.x);
+    block_partials_max<kColMax, kEW>(mx, part + (size_t)kColSums * gridDim.x, gridDim.x);
 }
 
 // KKT_omega (Section 2.4.2), candidate, termination (Section 2.3.2, unscaled),
@@ -314,9 +339,18 @@ k_check_ctrl(Ctrl* ctrl, const double* partR, const double* partC, int nparts,
              lp_trace_rec* trace)
 {
     if (!ctrl->want_check) return;
-    double r[8], cc[10];
-    for (int q = 0; q < 8; ++q) r[q] = block_sum_array<kCtlNT>(partR + (size_t)q * nparts, nparts);
-    for (int q = 0; q < 10; ++q) cc[q] = block_sum_array<kCtlNT>(partC + (size_t)q * nparts, nparts);
+    double r[kRowQ], cc[kColQ];
+    const int nr = infeas_active(*ctrl) ? kRowSums : 8, nc = infeas_active(*ctrl) ? kColSums : 10;
+    for (int q = 0; q < kRowQ; ++q) r[q] = 0.0;
+    for (int q = 0; q < kColQ; ++q) cc[q] = 0.0;
+    for (int q = 0; q < nr; ++q) r[q] = block_sum_array<kCtlNT>(partR + (size_t)q * nparts, nparts);
+    for (int q = 0; q < nc; ++q) cc[q] = block_sum_array<kCtlNT>(partC + (size_t)q * nparts, nparts);
+    if (nr > 8) {
+        for (int q = kRowSums; q < kRowQ; ++q)
+            r[q] = block_max_array<kCtlNT>(partR + (size_t)q * nparts, nparts);
+        for (int q = kColSums; q < kColQ; ++q)
+            cc[q] = block_max_array<kCtlNT>(partC + (size_t)q * nparts, nparts);
+    }
     if (threadIdx.x != 0) return;
     check_decide(ctrl, r, cc, trace);
 }
@@ -633,6 +667,8 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     c.adaptive = o->adaptive_step ? 1 : 0;
     c.pwu = o->primal_weight_update ? 1 : 0;
     c.restarts_on = o->restarts ? 1 : 0;
+    c.infeas = o->infeas_detect ? 1 : 0;
+    c.infeas_tol = o->infeas_tol;
     c.check_every = o->check_every;
     {
         // the time origin is the device clock read now

@@ -76,6 +76,12 @@ constexpr int kSpmvNT = kTaskWarps * 32;
 #define PDHG_SPMV_MIN_BLOCKS 4
 #endif
 constexpr int kSpmvMinBlocks = PDHG_SPMV_MIN_BLOCKS;   // resident blocks per SM the registers allow
+#ifndef PDHG_SPMV_CARVEOUT
+#define PDHG_SPMV_CARVEOUT -1
+#endif
+// Preferred shared-memory carveout of the SpMV kernels in percent of the
+// unified L1/shared capacity (-1: the driver's choice).
+constexpr int kSpmvCarveout = PDHG_SPMV_CARVEOUT;
 #ifndef PDHG_SPMV_UNROLL
 #define PDHG_SPMV_UNROLL 2
 #endif
@@ -442,8 +448,14 @@ inline cudaError_t spmv_prepare()
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)spmv_smem_bytes<T>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_spmv<T, Epi, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)spmv_smem_bytes<T>());
+    e = cudaFuncSetAttribute(k_spmv<T, Epi, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)spmv_smem_bytes<T>());
+    if (e != cudaSuccess || kSpmvCarveout < 0) return e;
+    e = cudaFuncSetAttribute(k_spmv<T, Epi, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             kSpmvCarveout);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_spmv<T, Epi, false>,
+                                cudaFuncAttributePreferredSharedMemoryCarveout, kSpmvCarveout);
 }
 
 // Gathers from a vector of at most this many bytes go through L1 (it stays

@@ -50,7 +50,9 @@ class LpOpts(C.Structure):
                 ("polish_switch_tol", C.c_double),
                 ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("omega0", C.c_double), ("eta0", C.c_double),
-                ("warm_memory_space", C.c_int32), ("loop_mode", C.c_int32)]
+                ("warm_memory_space", C.c_int32), ("loop_mode", C.c_int32),
+                ("infeas_detect", C.c_int32), ("reserved_opts", C.c_int32),
+                ("infeas_tol", C.c_double)]
 
 
 TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",
