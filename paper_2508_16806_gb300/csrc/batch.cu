@@ -217,7 +217,7 @@ struct EpiBDual {
     double* part;
     int cur = 0; T sigma = 0; T pw = 0; int adapt = 0;
     struct Pre { T y = 0, kx = 0, q = 0, ys = 0; uint8_t ge = 0; };
-    struct Acc { double dy2 = 0.0; };
+    struct Acc { T dy2 = T(0); };   // per-lane sums in T, reduced in FP64
     __device__ bool begin() const { return true; }
     __device__ const T* xin() const { return cur ? xs0 : xs1; }   // x' of the task's LP
     __device__ bool live(int t) const { return !ctrl[task_lp[t]].skip; }
@@ -243,13 +243,13 @@ struct EpiBDual {
         if (p.ge && v < T(0)) v = T(0);
         (cur ? y0 : y1)[i] = v;
         (cur ? kx0 : kx1)[i] = kxn;
-        const double d = (double)v - (double)p.y;
+        const T d = v - p.y;
         a.dy2 += d * d;
     }
     __device__ void task_done(int t, Acc& a) const {
-        const double s = warp_sum(a.dy2);
+        const double s = warp_sum((double)a.dy2);
         if (adapt && (threadIdx.x & 31) == 0) part[t] = s;
-        a.dy2 = 0.0;
+        a.dy2 = T(0);
     }
     __device__ void finish(Acc&) const {}
 };
@@ -266,7 +266,7 @@ struct EpiBPrimalT {
     int ntasks;
     int cur = 0; int adapt = 0;
     struct Pre { T x = 0, xn = 0, kt = 0; };
-    struct Acc { double dx2 = 0.0, inter = 0.0; };
+    struct Acc { T dx2 = T(0), inter = T(0); };   // per-lane sums in T, reduced in FP64
     __device__ bool begin() const { return true; }
     __device__ const T* xin() const { return cur ? ys0 : ys1; }   // y' of the task's LP
     __device__ bool live(int t) const { return !ctrl[task_lp[t]].skip; }
@@ -287,18 +287,18 @@ struct EpiBPrimalT {
     __device__ void row(int j, T ktyn, const Pre& p, Acc& a) const {
         (cur ? kty0 : kty1)[j] = ktyn;
         if (adapt) {
-            const double dx = (double)p.xn - (double)p.x;
+            const T dx = p.xn - p.x;
             a.dx2 += dx * dx;
-            a.inter += dx * ((double)ktyn - (double)p.kt);
+            a.inter += dx * (ktyn - p.kt);
         }
     }
     __device__ void task_done(int t, Acc& a) const {
-        const double s0 = warp_sum(a.dx2), s1 = warp_sum(a.inter);
+        const double s0 = warp_sum((double)a.dx2), s1 = warp_sum((double)a.inter);
         if (adapt && (threadIdx.x & 31) == 0) {
             part[t] = s0;
             part[(size_t)ntasks + t] = s1;
         }
-        a.dx2 = a.inter = 0.0;
+        a.dx2 = a.inter = T(0);
     }
     __device__ void finish(Acc&) const {}
 };
@@ -376,7 +376,7 @@ kb_check_prep(const Ctrl* __restrict__ ctrl, const int32_t* lp_row, const int32_
             const T pw = (T)C.pend_w;
             T s = xs[t];
             if (pw != T(0)) { s += pw * (C.cur ? x1 : x0)[t]; xs[t] = s; }
-            T a = C.W > 0.0 ? (T)((double)s / C.W) : T(0);
+            T a = s * (T)C.Winv;
             if (a < l[t]) a = l[t];
             if (a > u[t]) a = u[t];
             xa[t] = a;
@@ -387,19 +387,19 @@ kb_check_prep(const Ctrl* __restrict__ ctrl, const int32_t* lp_row, const int32_
             const T pw = (T)C.pend_w;
             T s = ys[i];
             if (pw != T(0)) { s += pw * (C.cur ? y1 : y0)[i]; ys[i] = s; }
-            T a = C.W > 0.0 ? (T)((double)s / C.W) : T(0);
+            T a = s * (T)C.Winv;
             if (sense[i] && a < T(0)) a = T(0);
             ya[i] = a;
         }
     }
 }
 
-// one warp per K task: the 8 row-side sums of k_check_rows over the task's rows
+// one warp per K task: the row-side terms of RowCheck over the task's rows
 template <typename T>
 __global__ void kb_check_rows(const Ctrl* ctrl, const int32_t* taskK, const int32_t* lpK, int ntK,
                               const T* y0, const T* y1, const T* kx0, const T* kx1, const T* ya,
                               const T* kxa, const T* yanc, const T* q, const uint8_t* sense,
-                              const double* R, double* part)
+                              const T* R, const T* Rinv, double* part)
 {
     const int t = blockIdx.x * (kEW / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -411,46 +411,27 @@ __global__ void kb_check_rows(const Ctrl* ctrl, const int32_t* taskK, const int3
     const T* kx = C.cur ? kx1 : kx0;
     const T* yp = C.cur ? y0 : y1;
     const T* kxp = C.cur ? kx0 : kx1;
-    double v[kRowQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    InfeasRow ir;
+    RowCheck<T> rc;
     for (int i = taskK[t] + lane; i < taskK[t + 1]; i += 32) {
-        const double qi = (double)q[i], Ri = R[i];
+        const T qi = q[i], ri = Rinv[i], kxi = kx[i], yi = y[i];
         const bool ge = sense[i] != 0;
-        const double yan = (double)yanc[i];
-        double r = qi - (double)kx[i];
-        if (ge && r < 0.0) r = 0.0;
-        v[0] += r * r;
-        v[1] += (r / Ri) * (r / Ri);
-        const double yc = (double)y[i];
-        v[2] += qi * yc;
-        v[3] += (yc - yan) * (yc - yan);
-        double ra = qi - (double)kxa[i];
-        if (ge && ra < 0.0) ra = 0.0;
-        v[4] += ra * ra;
-        v[5] += (ra / Ri) * (ra / Ri);
-        const double yv = (double)ya[i];
-        v[6] += qi * yv;
-        v[7] += (yv - yan) * (yv - yan);
-        if (inf) ir.add((double)kx[i], (double)kxp[i], yc, (double)yp[i], qi, Ri, ge);
+        rc.add(qi, kxi, yi, kxa[i], ya[i], yanc[i], ri, ge);
+        if (inf) rc.add_infeas(qi, kxi, kxp[i], yi, yp[i], R[i], ri, ge);
     }
-    v[8] = ir.adx2;
-    v[9] = ir.dy2;
-    v[10] = ir.psi;
-    v[11] = ir.gneg;
-    v[12] = ir.yneg;
 #pragma unroll
     for (int qq = 0; qq < kRowQ; ++qq) {
-        const double s = qq < kRowSums ? warp_sum(v[qq]) : warp_max(v[qq]);
+        const double s = qq < kRowSums ? warp_sum((double)rc.v[qq])
+                                       : warp_max((double)rc.mx[qq - kRowSums]);
         if (lane == 0) part[(size_t)qq * ntK + t] = s;
     }
 }
 
-// one warp per K^T task: the 10 column-side sums of k_check_cols
+// one warp per K^T task: the column-side terms of ColCheck
 template <typename T>
 __global__ void kb_check_cols(const Ctrl* ctrl, const int32_t* taskT, const int32_t* lpT, int ntT,
                               const T* x0, const T* x1, const T* kty0, const T* kty1, const T* xa,
                               const T* ktya, const T* xanc, const T* c, const T* l, const T* u,
-                              const double* Cs, double* part)
+                              const T* Cs, const T* Cinv, double* part)
 {
     const int t = blockIdx.x * (kEW / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -462,40 +443,19 @@ __global__ void kb_check_cols(const Ctrl* ctrl, const int32_t* taskT, const int3
     const T* kty = CC.cur ? kty1 : kty0;
     const T* xp = CC.cur ? x0 : x1;
     const T* ktyp = CC.cur ? kty0 : kty1;
-    double v[kColQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    InfeasCol ic;
+    ColCheck<T> cc;
     for (int j = taskT[t] + lane; j < taskT[t + 1]; j += 32) {
-        const double cj = (double)c[j], lj = (double)l[j], uj = (double)u[j], Cj = Cs[j];
+        const T cj = c[j], lj = l[j], uj = u[j], ci = Cinv[j], xj = x[j], kj = kty[j];
+        const T xan = xanc[j];
         const bool lf = isfinite(lj), uf = isfinite(uj);
-        const double xan = (double)xanc[j];
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const double vj = cj - (double)(side ? ktya[j] : kty[j]);
-            const double lam = proj_lambda(vj, lf, uf);
-            const double d = vj - lam;
-            const double xv = (double)(side ? xa[j] : x[j]);
-            double lt = 0.0;
-            if (lam > 0.0) lt += lj * lam;
-            if (lam < 0.0) lt += uj * lam;
-            v[5 * side + 0] += d * d;
-            v[5 * side + 1] += (d / Cj) * (d / Cj);
-            v[5 * side + 2] += cj * xv;
-            v[5 * side + 3] += lt;
-            v[5 * side + 4] += (xv - xan) * (xv - xan);
-        }
-        if (inf)
-            ic.add((double)x[j], (double)xp[j], (double)kty[j], (double)ktyp[j], cj, lj, uj, Cj,
-                   lf, uf);
+        cc.side(0, cj, kj, xj, xan, lj, uj, ci, lf, uf);
+        cc.side(1, cj, ktya[j], xa[j], xan, lj, uj, ci, lf, uf);
+        if (inf) cc.add_infeas(cj, xj, xp[j], kj, ktyp[j], lj, uj, Cs[j], ci, lf, uf);
     }
-    v[10] = ic.dx2;
-    v[11] = ic.cdx;
-    v[12] = ic.r2;
-    v[13] = ic.dl2;
-    v[14] = ic.psi;
-    v[15] = ic.vviol;
 #pragma unroll
     for (int qq = 0; qq < kColQ; ++qq) {
-        const double s = qq < kColSums ? warp_sum(v[qq]) : warp_max(v[qq]);
+        const double s = qq < kColSums ? warp_sum((double)cc.v[qq])
+                                       : warp_max((double)cc.mx[qq - kColSums]);
         if (lane == 0) part[(size_t)qq * ntT + t] = s;
     }
 }
@@ -878,10 +838,10 @@ void b_launch_check(BatchHandle* bh, cudaStream_t st, cudaGraphConditionalHandle
     launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, h->trp, h->tci, E.tval, h->dev_err, m, e2);
     kb_check_rows<T><<<(S.ntK + 7) / 8, kEW, 0, st>>>(bh->ctrl, S.taskK, S.lpK, S.ntK, E.Y[0],
                                                        E.Y[1], E.KX[0], E.KX[1], E.YA, E.KXA,
-                                                       E.YANC, E.q, h->sense, h->R, S.partR);
+                                                       E.YANC, E.q, h->sense, E.Rt, E.Rinv, S.partR);
     kb_check_cols<T><<<(S.ntT + 7) / 8, kEW, 0, st>>>(bh->ctrl, S.taskT, S.lpT, S.ntT, E.X[0],
                                                        E.X[1], E.KTY[0], E.KTY[1], E.XA, E.KTYA,
-                                                       E.XANC, E.c, E.l, E.u, h->C, S.partC);
+                                                       E.XANC, E.c, E.l, E.u, E.Ct, E.Cinv, S.partC);
     kb_check_ctrl<<<(B + kBW - 1) / kBW, kBW * 32, 0, st>>>(bh->ctrl, B, S.t0K, S.t0T, S.partR,
                                                             S.ntK, S.partC, S.ntT);
     kb_restart_apply<T><<<grid_n(n + m), kEW, 0, st>>>(
@@ -1006,6 +966,7 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
     kb_init_ctrl<<<grid_n(B, 256, 4096), 256, 0, st>>>(bh->ctrl, B, normK, cs2, qs2, bh->meta.qn,
                                                        bh->meta.cn, tmpl, o->eta_scale, o->eta0,
                                                        o->omega0, o->eps_zero, t0);
+    LP_TRY(engine_factors<T>(h));
     // start point and its products
     kb_init_state<T><<<grid_n(n + m, 256, 8192), 256, 0, st>>>(E.X[0], E.Y[0], E.XANC, E.YANC,
                                                                E.XS, E.YS, E.l, E.u, n, m);

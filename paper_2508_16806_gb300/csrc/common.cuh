@@ -33,6 +33,7 @@ struct Ctrl {
     double eta, omega;
     double pend_w;       // eta of the last accepted iterate not yet added to the averages
     double W;            // sum of eta over the iterates in the averages
+    double Winv;         // 1 / W (0 while W = 0)
     // restart state (Section 2.4.2)
     double kkt_anchor, kkt_prev;
     // last check
@@ -89,6 +90,8 @@ struct Engine {
     int32_t* bcol = nullptr;   int ntblk = 0;   // K^T rows
     int64_t* bnzK = nullptr;   int64_t* bnzT = nullptr;   // first nonzero of each task
     int gK = 0, gT = 0;                         // blocks of the K and K^T SpMV launches
+    // Ruiz factors R, C and their reciprocals in this precision (KKT checks)
+    T* Rt = nullptr; T* Ct = nullptr; T* Rinv = nullptr; T* Cinv = nullptr;
     // reduction partials
     double* partD = nullptr;   // [gK]
     double* partT = nullptr;   // [2][gT]
@@ -321,6 +324,8 @@ __global__ void k_scale_vectors(int64_t m, int64_t n, const double* R, const dou
 lp_status setup_create(Handle* h, const lp_desc* d);
 lp_status setup_scale(Handle* h, const lp_opts* o, double* normK);
 template <typename T> lp_status setup_engine(Handle* h, const lp_opts* o);
+// Engine<T>::Rt, Ct, Rinv, Cinv from the current FP64 Ruiz factors (allocated once).
+template <typename T> lp_status engine_factors(Handle* h);
 // solver.cu
 template <typename T>
 lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,

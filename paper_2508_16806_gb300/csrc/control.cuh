@@ -10,69 +10,108 @@ namespace pdhg {
 
 // lambda = proj_Lambda(v) (Section 2.3.1): Lambda_j = {0}, R^-, R^+ or R by
 // which of l_j, u_j is finite.
-__device__ __forceinline__ double proj_lambda(double v, bool lf, bool uf)
+template <typename T>
+__device__ __forceinline__ T proj_lambda(T v, bool lf, bool uf)
 {
-    if (!lf && !uf) return 0.0;
-    if (!lf) return v < 0.0 ? v : 0.0;
-    if (!uf) return v > 0.0 ? v : 0.0;
+    if (!lf && !uf) return T(0);
+    if (!lf) return v < T(0) ? v : T(0);
+    if (!uf) return v > T(0) ? v : T(0);
     return v;
 }
 
-// Algorithm 6 terms of one row from the current and the previous iterate.
-// With K~ = R K C, y = R y~ and x = C x~: (K dx)_i = (K~ dx~)_i / R_i,
-// dy_i = R_i dy~_i and q_i dy_i = q~_i dy~_i, so the unscaled directions come
-// from the stored scaled iterates and products.
-struct InfeasRow {
-    double adx2 = 0.0;   // ||A dx||^2 (equality rows)
-    double dy2 = 0.0;    // ||dy||^2
-    double psi = 0.0;    // q^T dy
-    double gneg = 0.0;   // max(0, max -(G dx)_i)  (>= rows)
-    double yneg = 0.0;   // max(0, max -dy_i)      (>= rows)
-    __device__ void add(double kx, double kxp, double y, double yp, double q, double R, bool ge)
+// Row-side terms of a KKT check, accumulated per thread in the iterate
+// precision T (GB300's FP64 pipe is narrow; FP32 sums of a few rows per thread
+// keep 1e-7 relative accuracy, and every partial is reduced in FP64):
+// [0] sum r_s^2  [1] sum (r_s / R)^2  [2] q~^T y  [3] ||y - y_anchor||^2  (current)
+// [4..7] the same for the average; r = q~ - K~ x, clamped at 0 on >= rows.
+// Algorithm 6 on the last step: [8] ||A dx||^2, [9] ||dy||^2, [10] q^T dy and
+// the maxima mx[0] of -(G dx), mx[1] of -dy_ineq (both >= 0).  With K~ = R K C,
+// y = R y~, x = C x~: (K dx)_i = (K~ dx~)_i / R_i, dy_i = R_i dy~_i and
+// q_i dy_i = q~_i dy~_i.
+template <typename T>
+struct RowCheck {
+    T v[kRowSums] = {};
+    T mx[kRowMax] = {};
+    __device__ __forceinline__ void add(T q, T kx, T y, T kxa, T ya, T yanc, T rinv, bool ge)
     {
-        const double adx = (kx - kxp) / R;
-        const double dys = y - yp;
-        const double dy = R * dys;
+        T r = q - kx;
+        if (ge && r < T(0)) r = T(0);
+        const T ru = r * rinv;
+        v[0] += r * r;
+        v[1] += ru * ru;
+        v[2] += q * y;
+        v[3] += (y - yanc) * (y - yanc);
+        T ra = q - kxa;
+        if (ge && ra < T(0)) ra = T(0);
+        const T rau = ra * rinv;
+        v[4] += ra * ra;
+        v[5] += rau * rau;
+        v[6] += q * ya;
+        v[7] += (ya - yanc) * (ya - yanc);
+    }
+    __device__ __forceinline__ void add_infeas(T q, T kx, T kxp, T y, T yp, T R, T rinv, bool ge)
+    {
+        const T adx = (kx - kxp) * rinv;
+        const T dys = y - yp;
+        const T dy = R * dys;
         if (ge) {
-            gneg = fmax(gneg, -adx);
-            yneg = fmax(yneg, -dy);
+            mx[0] = fmax(mx[0], -adx);
+            mx[1] = fmax(mx[1], -dy);
         } else {
-            adx2 += adx * adx;
+            v[8] += adx * adx;
         }
-        dy2 += dy * dy;
-        psi += q * dys;
+        v[9] += dy * dy;
+        v[10] += q * dys;
     }
 };
 
-// Algorithm 6 terms of one column: dx_j = C_j dx~_j, c_j dx_j = c~_j dx~_j,
+// Column-side terms, same conventions: [0] sum d_s^2  [1] sum (d_s / C)^2
+// [2] c~^T x  [3] l~^T lambda^+ + u~^T lambda^-  [4] ||x - x_anchor||^2
+// (current), [5..9] average; d = v - lambda, v = c~ - K~^T y, lambda = proj_Lambda(v).
+// Algorithm 6: [10] ||dx||^2, [11] c^T dx, [12] ||K^T dy + dlambda||^2,
+// [13] ||dlambda||^2, [14] l^T dlambda^+ + u^T dlambda^- and mx[0] the largest
+// distance of dx_j to V_j; dx_j = C_j dx~_j, c_j dx_j = c~_j dx~_j,
 // (K^T dy)_j = (K~^T dy~)_j / C_j, dlambda_j = dlambda~_j / C_j and
-// l_j dlambda_j = l~_j dlambda~_j (lambda~ = proj_Lambda(c~ - K~^T y~)).
-struct InfeasCol {
-    double dx2 = 0.0;    // ||dx||^2
-    double cdx = 0.0;    // c^T dx
-    double r2 = 0.0;     // ||K^T dy + dlambda||^2
-    double dl2 = 0.0;    // ||dlambda||^2
-    double psi = 0.0;    // l^T dlambda^+ + u^T dlambda^-
-    double vviol = 0.0;  // max distance of dx_j to V_j
-    __device__ void add(double x, double xp, double kty, double ktyp, double c, double l,
-                        double u, double C, bool lf, bool uf)
+// l_j dlambda_j = l~_j dlambda~_j.
+template <typename T>
+struct ColCheck {
+    T v[kColSums] = {};
+    T mx[kColMax] = {};
+    __device__ __forceinline__ void side(int s, T c, T kty, T x, T xanc, T l, T u, T cinv, bool lf,
+                                         bool uf)
     {
-        const double dxs = x - xp;
-        const double dx = C * dxs;
-        dx2 += dx * dx;
-        cdx += c * dxs;
-        double v = 0.0;
-        if (lf && uf) v = fabs(dx);
-        else if (lf) v = dx < 0.0 ? -dx : 0.0;
-        else if (uf) v = dx > 0.0 ? dx : 0.0;
-        vviol = fmax(vviol, v);
-        const double dls = proj_lambda(c - kty, lf, uf) - proj_lambda(c - ktyp, lf, uf);
-        const double dl = dls / C;
-        const double r = (kty - ktyp) / C + dl;
-        r2 += r * r;
-        dl2 += dl * dl;
-        if (dls > 0.0) psi += l * dls;
-        if (dls < 0.0) psi += u * dls;
+        const T vj = c - kty;
+        const T lam = proj_lambda(vj, lf, uf);
+        const T d = vj - lam;
+        const T du = d * cinv;
+        T lt = T(0);
+        if (lam > T(0)) lt = l * lam;
+        if (lam < T(0)) lt = u * lam;
+        v[5 * s + 0] += d * d;
+        v[5 * s + 1] += du * du;
+        v[5 * s + 2] += c * x;
+        v[5 * s + 3] += lt;
+        v[5 * s + 4] += (x - xanc) * (x - xanc);
+    }
+    __device__ __forceinline__ void add_infeas(T c, T x, T xp, T kty, T ktyp, T l, T u, T C,
+                                               T cinv, bool lf, bool uf)
+    {
+        const T dxs = x - xp;
+        const T dx = C * dxs;
+        v[10] += dx * dx;
+        v[11] += c * dxs;
+        T dist = T(0);
+        if (lf && uf) dist = fabs(dx);
+        else if (lf) dist = dx < T(0) ? -dx : T(0);
+        else if (uf) dist = dx > T(0) ? dx : T(0);
+        mx[0] = fmax(mx[0], dist);
+        const T dls = proj_lambda(c - kty, lf, uf) - proj_lambda(c - ktyp, lf, uf);
+        const T dl = dls * cinv;
+        const T r = (kty - ktyp) * cinv + dl;
+        v[12] += r * r;
+        v[13] += dl * dl;
+        if (dls > T(0)) v[14] += l * dls;
+        if (dls < T(0)) v[14] += u * dls;
     }
 };
 
@@ -111,6 +150,7 @@ __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, d
         ctrl->epoch_k += 1;
         ctrl->pend_w = eta;
         ctrl->W += eta;
+        ctrl->Winv = 1.0 / ctrl->W;
         ctrl->rejects = 0;
     } else {
         ctrl->pend_w = 0.0;
@@ -202,6 +242,7 @@ __device__ __forceinline__ void check_decide(Ctrl* ctrl, const double* r, const 
         ctrl->kkt_prev = INFINITY;
         ctrl->epoch_k = 0;
         ctrl->W = 0.0;
+        ctrl->Winv = 0.0;
         ctrl->restarts += 1;
     } else if (!first) {
         ctrl->kkt_prev = kkt_cand;

@@ -663,4 +663,42 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
 template lp_status setup_engine<double>(Handle*, const lp_opts*);
 template lp_status setup_engine<float>(Handle*, const lp_opts*);
 
+template <typename T>
+__global__ void k_factors(int64_t m, int64_t n, const double* R, const double* C, T* Rt, T* Ct,
+                          T* Rinv, T* Cinv)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m + n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n) {
+            Ct[t] = (T)C[t];
+            Cinv[t] = (T)(1.0 / C[t]);
+        } else {
+            const int64_t i = t - n;
+            Rt[i] = (T)R[i];
+            Rinv[i] = (T)(1.0 / R[i]);
+        }
+    }
+}
+
+template <typename T>
+lp_status engine_factors(Handle* h)
+{
+    Engine<T>& E = engine_of<T>(h);
+    const int64_t m = h->m, n = h->n;
+    if (!E.Rt) {
+        LP_TRY(dev_alloc_n(h, &E.Rt, (size_t)m));
+        LP_TRY(dev_alloc_n(h, &E.Rinv, (size_t)m));
+        LP_TRY(dev_alloc_n(h, &E.Ct, (size_t)n));
+        LP_TRY(dev_alloc_n(h, &E.Cinv, (size_t)n));
+    }
+    k_factors<T><<<grid_for(m + n), 256, 0, h->stream>>>(m, n, h->R, h->C, E.Rt, E.Ct, E.Rinv,
+                                                         E.Cinv);
+    ++h->launches;
+    LP_CUDA_TRY(cudaGetLastError());
+    return LP_OK;
+}
+
+template lp_status engine_factors<double>(Handle*);
+template lp_status engine_factors<float>(Handle*);
+
 }  // namespace pdhg

@@ -91,7 +91,7 @@ struct EpiDual {
     double* part;
     int cur; T sigma; T pw; int adapt;
     struct Pre { T y = 0, kx = 0, q = 0, ys = 0; uint8_t ge = 0; };
-    struct Acc { double dy2 = 0.0; };
+    struct Acc { T dy2 = T(0); };   // per-lane sums in T, reduced in FP64
     __device__ bool begin() {
         if (ctrl->skip) return false;
         cur = ctrl->cur;
@@ -116,12 +116,12 @@ struct EpiDual {
         if (p.ge && v < T(0)) v = T(0);
         (cur ? y0 : y1)[i] = v;
         (cur ? kx0 : kx1)[i] = kxn;
-        const double d = (double)v - (double)p.y;
+        const T d = v - p.y;
         a.dy2 += d * d;
     }
     __device__ void finish(Acc& a) const {
         if (adapt) {
-            const double t[1] = {a.dy2};
+            const double t[1] = {(double)a.dy2};
             block_partials<1, kSpmvNT>(t, part, gridDim.x);
         }
     }
@@ -143,7 +143,7 @@ struct EpiPrimalT {
     int nD;
     int cur; int adapt;
     struct Pre { T x = 0, xn = 0, kt = 0; };
-    struct Acc { double dx2 = 0.0, inter = 0.0; };
+    struct Acc { T dx2 = T(0), inter = T(0); };   // per-lane sums in T, reduced in FP64
     __device__ bool begin() {
         if (ctrl->skip) return false;
         cur = ctrl->cur;
@@ -163,15 +163,15 @@ struct EpiPrimalT {
     __device__ void row(int j, T ktyn, const Pre& p, Acc& a) const {
         (cur ? kty0 : kty1)[j] = ktyn;
         if (adapt) {
-            const double dx = (double)p.xn - (double)p.x;
+            const T dx = p.xn - p.x;
             a.dx2 += dx * dx;
-            a.inter += dx * ((double)ktyn - (double)p.kt);
+            a.inter += dx * (ktyn - p.kt);
         }
     }
     __device__ void finish(Acc& a) const {
         __shared__ int last;
         if (adapt) {
-            const double t[2] = {a.dx2, a.inter};
+            const double t[2] = {(double)a.dx2, (double)a.inter};
             block_partials<2, kSpmvNT>(t, part, gridDim.x);
         }
         __threadfence();
@@ -207,7 +207,7 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
     if (!ctrl->want_check) return;
     const int cur = ctrl->cur;
     const T pw = (T)ctrl->pend_w;
-    const double W = ctrl->W;
+    const T winv = (T)ctrl->Winv;
     const T* x = cur ? x1 : x0;
     const T* y = cur ? y1 : y0;
     for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < n + m;
@@ -215,7 +215,7 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
         if (t < n) {
             T s = xs[t];
             if (pw != T(0)) { s += pw * x[t]; xs[t] = s; }
-            T a = W > 0.0 ? (T)((double)s / W) : T(0);
+            T a = s * winv;
             if (a < l[t]) a = l[t];
             if (a > u[t]) a = u[t];
             xa[t] = a;
@@ -223,23 +223,20 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
             const int64_t i = t - n;
             T s = ys[i];
             if (pw != T(0)) { s += pw * y[i]; ys[i] = s; }
-            T a = W > 0.0 ? (T)((double)s / W) : T(0);
+            T a = s * winv;
             if (sense[i] && a < T(0)) a = T(0);
             ya[i] = a;
         }
     }
 }
 
-// Row side of the KKT terms for the current point and the average:
-// [0] sum r_s^2  [1] sum (r_s / R)^2  [2] q~^T y  [3] ||y - y_anchor||^2   (current)
-// [4..7] the same for the average.  r = q~ - K~ x, clamped at 0 on >= rows.
-// [8..10] ||A dx||^2, ||dy||^2, q^T dy and the maxima [11] -(G dx), [12] -dy_ineq
-// of Algorithm 6 on the last step (zero unless the check runs it).
+// Row side of a KKT check (terms of RowCheck), block partials in FP64:
+// part[q * gridDim.x + block], sums q < kRowSums, then the maxima.
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_check_rows(const Ctrl* __restrict__ ctrl, const T* y0, const T* y1, const T* kx0,
              const T* kx1, const T* ya, const T* kxa, const T* yanc, const T* q,
-             const uint8_t* sense, const double* R, int64_t m, double* part)
+             const uint8_t* sense, const T* R, const T* Rinv, int64_t m, double* part)
 {
     if (!ctrl->want_check) return;
     const int cur = ctrl->cur;
@@ -248,47 +245,28 @@ k_check_rows(const Ctrl* __restrict__ ctrl, const T* y0, const T* y1, const T* k
     const T* kx = cur ? kx1 : kx0;
     const T* yp = cur ? y0 : y1;
     const T* kxp = cur ? kx0 : kx1;
-    double v[kRowSums] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    InfeasRow ir;
+    RowCheck<T> rc;
     for (int64_t i = (int64_t)blockIdx.x * kEW + threadIdx.x; i < m; i += (int64_t)gridDim.x * kEW) {
-        const double qi = (double)q[i], Ri = R[i];
+        const T qi = q[i], ri = Rinv[i], kxi = kx[i], yi = y[i];
         const bool ge = sense[i] != 0;
-        const double ya_ = (double)yanc[i];
-        double r = qi - (double)kx[i];
-        if (ge && r < 0.0) r = 0.0;
-        v[0] += r * r;
-        v[1] += (r / Ri) * (r / Ri);
-        const double yc = (double)y[i];
-        v[2] += qi * yc;
-        v[3] += (yc - ya_) * (yc - ya_);
-        double ra = qi - (double)kxa[i];
-        if (ge && ra < 0.0) ra = 0.0;
-        v[4] += ra * ra;
-        v[5] += (ra / Ri) * (ra / Ri);
-        const double yv = (double)ya[i];
-        v[6] += qi * yv;
-        v[7] += (yv - ya_) * (yv - ya_);
-        if (inf) ir.add((double)kx[i], (double)kxp[i], yc, (double)yp[i], qi, Ri, ge);
+        rc.add(qi, kxi, yi, kxa[i], ya[i], yanc[i], ri, ge);
+        if (inf) rc.add_infeas(qi, kxi, kxp[i], yi, yp[i], R[i], ri, ge);
     }
-    v[8] = ir.adx2;
-    v[9] = ir.dy2;
-    v[10] = ir.psi;
-    const double mx[kRowMax] = {ir.gneg, ir.yneg};
+    double v[kRowSums], mx[kRowMax];
+#pragma unroll
+    for (int k = 0; k < kRowSums; ++k) v[k] = (double)rc.v[k];
+#pragma unroll
+    for (int k = 0; k < kRowMax; ++k) mx[k] = (double)rc.mx[k];
     block_partials<kRowSums, kEW>(v, part, gridDim.x);
     block_partials_max<kRowMax, kEW>(mx, part + (size_t)kRowSums * gridDim.x, gridDim.x);
 }
 
-// Column side: [0] sum d_s^2  [1] sum (d_s / C)^2  [2] c~^T x
-// [3] l~^T lambda^+ + u~^T lambda^-  [4] ||x - x_anchor||^2  (current), [5..9] average;
-// d = v - lambda, v = c~ - K~^T y, lambda = proj_Lambda(v).
-// [10..14] ||dx||^2, c^T dx, ||K^T dy + dlambda||^2, ||dlambda||^2,
-// l^T dlambda^+ + u^T dlambda^- and the maximum [15] distance of dx to V
-// (Algorithm 6 on the last step; zero unless the check runs it).
+// Column side (terms of ColCheck), same layout with kColSums / kColMax.
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_check_cols(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* kty0,
              const T* kty1, const T* xa, const T* ktya, const T* xanc, const T* c,
-             const T* l, const T* u, const double* C, int64_t n, double* part)
+             const T* l, const T* u, const T* C, const T* Cinv, int64_t n, double* part)
 {
     if (!ctrl->want_check) return;
     const int cur = ctrl->cur;
@@ -297,37 +275,20 @@ k_check_cols(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* k
     const T* kty = cur ? kty1 : kty0;
     const T* xp = cur ? x0 : x1;
     const T* ktyp = cur ? kty0 : kty1;
-    double v[kColSums] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    InfeasCol ic;
+    ColCheck<T> cc;
     for (int64_t j = (int64_t)blockIdx.x * kEW + threadIdx.x; j < n; j += (int64_t)gridDim.x * kEW) {
-        const double cj = (double)c[j], lj = (double)l[j], uj = (double)u[j], Cj = C[j];
+        const T cj = c[j], lj = l[j], uj = u[j], ci = Cinv[j], xj = x[j], kj = kty[j];
+        const T xan = xanc[j];
         const bool lf = isfinite(lj), uf = isfinite(uj);
-        const double xan = (double)xanc[j];
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const double vj = cj - (double)(side ? ktya[j] : kty[j]);
-            const double lam = proj_lambda(vj, lf, uf);
-            const double d = vj - lam;
-            const double xv = (double)(side ? xa[j] : x[j]);
-            double lt = 0.0;
-            if (lam > 0.0) lt += lj * lam;
-            if (lam < 0.0) lt += uj * lam;
-            v[5 * side + 0] += d * d;
-            v[5 * side + 1] += (d / Cj) * (d / Cj);
-            v[5 * side + 2] += cj * xv;
-            v[5 * side + 3] += lt;
-            v[5 * side + 4] += (xv - xan) * (xv - xan);
-        }
-        if (inf)
-            ic.add((double)x[j], (double)xp[j], (double)kty[j], (double)ktyp[j], cj, lj, uj, Cj,
-                   lf, uf);
+        cc.side(0, cj, kj, xj, xan, lj, uj, ci, lf, uf);
+        cc.side(1, cj, ktya[j], xa[j], xan, lj, uj, ci, lf, uf);
+        if (inf) cc.add_infeas(cj, xj, xp[j], kj, ktyp[j], lj, uj, C[j], ci, lf, uf);
     }
-    v[10] = ic.dx2;
-    v[11] = ic.cdx;
-    v[12] = ic.r2;
-    v[13] = ic.dl2;
-    v[14] = ic.psi;
-    const double mx[kColMax] = {ic.vviol};
+    double v[kColSums], mx[kColMax];
+#pragma unroll
+    for (int k = 0; k < kColSums; ++k) v[k] = (double)cc.v[k];
+#pragma unroll
+    for (int k = 0; k < kColMax; ++k) mx[k] = (double)cc.mx[k];
     block_partials<kColSums, kEW>(v, part, gridDim.x);
     block_partials_max<kColMax, kEW>(mx, part + (size_t)kColSums * gridDim.x, gridDim.x);
 }
@@ -523,9 +484,11 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
     EpiStore<T> e2{E.YA, E.KTYA, nullptr, nullptr, gate};
     launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
     k_check_rows<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YA,
-                                             E.KXA, E.YANC, E.q, h->sense, h->R, m, E.partR);
+                                             E.KXA, E.YANC, E.q, h->sense, E.Rt, E.Rinv, m,
+                                             E.partR);
     k_check_cols<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.XA,
-                                             E.KTYA, E.XANC, E.c, E.l, E.u, h->C, n, E.partC);
+                                             E.KTYA, E.XANC, E.c, E.l, E.u, E.Ct, E.Cinv, n,
+                                             E.partC);
     k_check_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partR, E.partC, kEWGrid, E.trace);
     k_restart_apply<T><<<ew_grid(n + m), kEW, 0, st>>>(
         E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.KTY[0], E.KTY[1], E.XA, E.YA,
@@ -609,6 +572,7 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     LP_CUDA_TRY((spmv_prepare<T, EpiStore<T>>()));
     LP_CUDA_TRY((spmv_prepare<T, EpiDual<T>>()));
     LP_CUDA_TRY((spmv_prepare<T, EpiPrimalT<T>>()));
+    LP_TRY(engine_factors<T>(h));
     // warm start from the caller (unscaled) must be on the device
     const double* dwx = nullptr;
     const double* dwy = nullptr;

@@ -89,8 +89,19 @@ constexpr int kSpmvCarveout = PDHG_SPMV_CARVEOUT;
 template <typename T> struct Unroll { static constexpr int value = PDHG_SPMV_UNROLL; };
 // nonzeros per warp task: one pass of U vector loads per lane covers the task's
 // aligned range, whose start may sit up to VEC - 1 elements before the first nonzero
+// (PDHG_SPMV_CAP > 0 lowers it, trading nonzeros per stage for a smaller
+// shared-memory footprint and so a larger L1 for the gathers)
+#ifndef PDHG_SPMV_CAP
+#define PDHG_SPMV_CAP 0
+#endif
 template <typename T>
-__host__ __device__ constexpr int cap_w() { return 32 * VecTraits<T>::N * Unroll<T>::value - VecTraits<T>::N; }
+__host__ __device__ constexpr int cap_w()
+{
+    return (PDHG_SPMV_CAP > 0 &&
+            PDHG_SPMV_CAP < 32 * VecTraits<T>::N * Unroll<T>::value - VecTraits<T>::N)
+               ? PDHG_SPMV_CAP
+               : 32 * VecTraits<T>::N * Unroll<T>::value - VecTraits<T>::N;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum_T(T v)
@@ -205,7 +216,7 @@ struct alignas(16) WarpStage {
     T v[2][VPAD];
     int i[2][IPAD];
     uint64_t bar[2];
-    int64_t rps[kTaskRows + 1];
+    int rps[kTaskRows + 1];   // row starts of a short task, relative to its first nonzero
 };
 
 template <typename T>
@@ -318,7 +329,7 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
             if (lane < nrows) pre0 = epi.load(r0 + lane);
             if (kTaskRows > 32 && lane + 32 < nrows) pre1 = epi.load(r0 + 32 + lane);
             if (!is_long)
-                for (int t = lane; t <= nrows; t += 32) W.rps[t] = rp[r0 + t];
+                for (int t = lane; t <= nrows; t += 32) W.rps[t] = (int)(rp[r0 + t] - s);
             along = 0;
         }
         if (ce > cs) {
@@ -389,14 +400,14 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
             }
             T* vs = vbuf + vo;
             __syncwarp();
-            const int64_t* rps = W.rps;
+            const int* rps = W.rps;
             if (nrows <= 32) {
                 int G = 32;
                 while (G > 1 && G * nrows > 32) G >>= 1;
                 const int j = lane / G, g = lane % G;
                 T a = 0;
                 if (j < nrows) {
-                    const int pb = (int)(rps[j] - s), pe = (int)(rps[j + 1] - s);
+                    const int pb = rps[j], pe = rps[j + 1];
                     for (int p = pb + g; p < pe; p += G) a += vs[p];
                 }
                 for (int o = G >> 1; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o, G);
@@ -407,7 +418,7 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
                 for (int half = 0; half < 2; ++half) {
                     const int j = lane + 32 * half;
                     if (j < nrows) {
-                        const int pb = (int)(rps[j] - s), pe = (int)(rps[j + 1] - s);
+                        const int pb = rps[j], pe = rps[j + 1];
                         T a = 0;
                         for (int p = pb; p < pe; ++p) a += vs[p];
                         epi.row(r0 + j, a, half ? pre1 : pre0, acc);
@@ -439,23 +450,24 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
     epi.finish(acc);
 }
 
-// Sets the dynamic shared-memory limit of one SpMV instantiation (call before
-// any launch or capture) and launches it.
+// Dynamic shared-memory limit (and the optional carveout preference) of one
+// SpMV instantiation; spmv_prepare sets both gather variants of an epilogue.
+// Call before any launch or graph capture of that epilogue.
+template <typename T>
+inline cudaError_t spmv_set_attrs(const void* f)
+{
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)spmv_smem_bytes<T>());
+    if (e != cudaSuccess || kSpmvCarveout < 0) return e;
+    return cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, kSpmvCarveout);
+}
+
 template <typename T, class Epi>
 inline cudaError_t spmv_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_spmv<T, Epi, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)spmv_smem_bytes<T>());
+    cudaError_t e = spmv_set_attrs<T>((const void*)k_spmv<T, Epi, true>);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_spmv<T, Epi, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)spmv_smem_bytes<T>());
-    if (e != cudaSuccess || kSpmvCarveout < 0) return e;
-    e = cudaFuncSetAttribute(k_spmv<T, Epi, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             kSpmvCarveout);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_spmv<T, Epi, false>,
-                                cudaFuncAttributePreferredSharedMemoryCarveout, kSpmvCarveout);
+    return spmv_set_attrs<T>((const void*)k_spmv<T, Epi, false>);
 }
 
 // Gathers from a vector of at most this many bytes go through L1 (it stays
@@ -467,13 +479,13 @@ inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
                         const int64_t* task_nz, int ntasks, const int64_t* rp, const int32_t* ci,
                         const T* val, int* err, int64_t x_len, const Epi& epi)
 {
+    const size_t sm = spmv_smem_bytes<T>();
     if (x_len * (int64_t)sizeof(T) <= kL1GatherBytes)
-        k_spmv<T, Epi, true><<<grid, kSpmvNT, spmv_smem_bytes<T>(), st>>>(task_row, task_nz, ntasks,
-                                                                         rp, ci, val, err, epi);
+        k_spmv<T, Epi, true><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, rp, ci, val,
+                                                        err, epi);
     else
-        k_spmv<T, Epi, false><<<grid, kSpmvNT, spmv_smem_bytes<T>(), st>>>(task_row, task_nz,
-                                                                          ntasks, rp, ci, val, err,
-                                                                          epi);
+        k_spmv<T, Epi, false><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, rp, ci, val,
+                                                         err, epi);
 }
 
 // The task hooks of an epilogue that serves a single LP: every task is live,
