@@ -96,6 +96,10 @@ def _load():
         _lib.orc_infeasibility.argtypes = [P(_Lp), C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                            C.c_void_p]
         _lib.orc_infeasibility.restype = C.c_int
+        _lib.orc_fishnet.argtypes = [P(_Lp), P(_Opts), C.c_int32, C.c_int32, C.c_void_p,
+                                     C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     P(C.c_int32)]
+        _lib.orc_fishnet.restype = C.c_int
         _lib.orc_unrolled_forward.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_unrolled_adjoint.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
@@ -193,6 +197,16 @@ def pdhg_step(lp, x, y, tau, sigma, vals=None, c=None, q=None, l=None, u=None):
     return xn, yn
 
 
+def _opts(o, x0a=None, y0a=None):
+    return _Opts(o["tol"], int(o["max_iters"]), int(o["check_every"]), int(o["ruiz_iters"]),
+                 o["ruiz_tol"], int(o["pock_chambolle"]), int(o["power_iters"]),
+                 int(o["adaptive_step"]), int(o["primal_weight_update"]), int(o["restarts"]),
+                 o["eta_scale"], o["beta_sufficient"], o["beta_necessary"],
+                 o["beta_artificial"], o["eps_zero"],
+                 None if x0a is None else _ptr(x0a), None if y0a is None else _ptr(y0a),
+                 o["omega0"], o["eta0"], int(o["infeas_detect"]), 0, o["infeas_tol"])
+
+
 def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
     """Restarted PDHG.  Returns (x, y, info dict, trace list of dicts)."""
     o = dict(DEFAULTS)
@@ -200,13 +214,7 @@ def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
     b = _Bound(lp)
     x0a = None if x0 is None else _f64(x0)
     y0a = None if y0 is None else _f64(y0)
-    opts = _Opts(o["tol"], int(o["max_iters"]), int(o["check_every"]), int(o["ruiz_iters"]),
-                 o["ruiz_tol"], int(o["pock_chambolle"]), int(o["power_iters"]),
-                 int(o["adaptive_step"]), int(o["primal_weight_update"]), int(o["restarts"]),
-                 o["eta_scale"], o["beta_sufficient"], o["beta_necessary"],
-                 o["beta_artificial"], o["eps_zero"],
-                 None if x0a is None else _ptr(x0a), None if y0a is None else _ptr(y0a),
-                 o["omega0"], o["eta0"], int(o["infeas_detect"]), 0, o["infeas_tol"])
+    opts = _opts(o, x0a, y0a)
     x = np.empty(lp.n)
     y = np.empty(lp.m)
     info = _Info()
@@ -217,6 +225,41 @@ def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
     d = {f: getattr(info, f) for f, _ in _Info._fields_ if f != "pad"}
     trace = [dict(zip(TRACE_FIELDS, r.tolist())) for r in tr[: min(tl.value, trace_cap)]]
     return x, y, d, trace
+
+
+def fishnet(lp, P, k_steps, G, Z, **kw):
+    """Algorithm 7 (fishnet casting).  G: (n, P) standard-normal casting draws,
+    Z: 1-D normal draws of the repopulations.  Returns (x0, y0, gaps, rounds):
+    the unscaled warm start and, per round, the |duality gap| of each column
+    before the cull (NaN where a round had fewer columns)."""
+    o = dict(DEFAULTS)
+    o.update(kw)
+    b = _Bound(lp)
+    G = _f64(G).reshape(lp.n, P)
+    Z = _f64(np.asarray(Z, dtype=np.float64).ravel())
+    x = np.empty(lp.n)
+    y = np.empty(lp.m)
+    gaps = np.full((2 * 8 + 2, P), np.nan)
+    rounds = C.c_int32(0)
+    st = _load().orc_fishnet(C.byref(b.st), C.byref(_opts(o)), P, k_steps, _ptr(G), _ptr(Z),
+                             Z.shape[0], _ptr(x), _ptr(y), _ptr(gaps), C.byref(rounds))
+    if st != 0:
+        raise ValueError("orc_fishnet: invalid P or too few repopulation draws")
+    return x, y, gaps[: rounds.value], rounds.value
+
+
+def fishnet_draws(P):
+    """Normal draws one fishnet run with P columns consumes in its repopulations."""
+    total, cols, i = 0, P, 0
+    while cols > 1:
+        keep = cols // 2
+        if i % 2 == 1 and cols > 2:
+            total += keep * keep
+            cols = 2 * keep
+        else:
+            cols = keep
+        i += 1
+    return total
 
 
 def infeasibility(lp, dx, dy, dlam, tol):

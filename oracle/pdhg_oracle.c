@@ -25,6 +25,8 @@
  *   orc_solve                 Algorithm 1 + restarts (Section 2.4.2), primal weight
  *                             (Section 2.4.3, Algorithm 4), adaptive step
  *                             (Algorithm 5), termination (Section 2.3.2)
+ *   orc_infeasibility         Algorithm 6 (infeasibility detection, Section 2.4.5)
+ *   orc_fishnet               Algorithm 7 (fishnet casting, Section 2.5)
  *   orc_unrolled_forward /
  *   orc_unrolled_adjoint      K fixed-step iterations and their exact reverse-mode
  *                             derivative (the paper names autodiff only; the reverse
@@ -733,4 +735,186 @@ void orc_unrolled_adjoint(const orc_lp* lp, double tau, double sigma, int32_t K_
     }
     free(xs); free(ys); free(gx); free(gy); free(KTy); free(vx); free(xbar);
     free(Kxb); free(gvy); free(gxbar); free(gvx); free(Kgvx);
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 7: fishnet casting                                        */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Multi-start warm start of Section 2.5, on the scaled problem of the solver
+ * (Ruiz per o->ruiz_iters, eta = eta_scale / ||K~||_2 or o->eta0,
+ * omega = ||c~|| / ||q~|| or o->omega0, exactly as orc_solve sets them up).
+ *
+ * P columns (a power of two, 1..64); G holds n x P standard-normal draws,
+ * G[j * P + p] for coordinate j of point p; Z holds the normal draws of the
+ * repopulations, consumed in order (nZ of them available).
+ *
+ * Readings:
+ *  - spectral casting: r = ||K~||_2 (the Algorithm 2 estimate); point p is
+ *    x~_p = (r / sqrt(n)) g_p, so that E||x~_p||^2 = r^2 ("a normal
+ *    distribution around B_r");
+ *  - Y^0 = K~ X^0 as printed; PDHG(.) is k_steps fixed-step iterations of
+ *    Algorithm 1 (theta = 1, tau = eta / omega, sigma = eta * omega) per column;
+ *  - j is the column count at the top of a round; cull_points keeps the j / 2
+ *    columns of smallest |duality gap| |c~^T x - (q~^T y + l~^T lambda^+ +
+ *    u~^T lambda^-)|, lambda = proj_Lambda(c~ - K~^T y) (ties: lower index
+ *    first), in their old order;
+ *  - repopulate (round index i odd and j > 2) appends one new column per kept
+ *    column: new column t = sum_s w_ts * kept_s with w_ts = |z_ts| / sum_s |z_ts|
+ *    (the text normalises normal draws to sum one and calls the result a convex
+ *    combination; absolute values make it one; all-zero draws give equal
+ *    weights); the same weights combine the dual columns;
+ *  - the loop ends when one column is left; its unscaled (C x~, R y~) is the
+ *    output.
+ * gaps (may be NULL): per round, the |gap| of each of the j columns before the
+ * cull, at gaps[round * P + column] (unused entries untouched).
+ * rounds_out (may be NULL): number of rounds.  Returns 0, or -1 for an invalid P
+ * or too few draws in Z.
+ */
+int orc_fishnet(const orc_lp* lp, const orc_opts* o, int32_t P, int32_t k_steps,
+                const double* G, const double* Z, int64_t nZ, double* x_out, double* y_out,
+                double* gaps, int32_t* rounds_out)
+{
+    if (P < 1 || P > 64 || (P & (P - 1)) != 0 || k_steps < 0) return -1;
+    const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
+    double* vs = (double*)xalloc(nnz);
+    double* R = (double*)xalloc(m);
+    double* C = (double*)xalloc(n);
+    double *cs = (double*)xalloc(n), *qs = (double*)xalloc(m);
+    double *ls = (double*)xalloc(n), *us = (double*)xalloc(n);
+    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, vs, R, C);
+    for (int64_t j = 0; j < n; ++j) {
+        cs[j] = C[j] * lp->c[j];
+        ls[j] = lp->l[j] / C[j];
+        us[j] = lp->u[j] / C[j];
+    }
+    for (int64_t i = 0; i < m; ++i) qs[i] = R[i] * lp->q[i];
+    const double normK = orc_power_norm(lp, vs, o->power_iters);
+    double eta = normK > 0.0 ? o->eta_scale / normK : 1.0;
+    if (o->eta0 > 0.0) eta = o->eta0;
+    const double nc = nrm2(n, cs), nq = nrm2(m, qs);
+    double omega = (nc > o->eps_zero && nq > o->eps_zero) ? nc / nq : 1.0;
+    if (o->omega0 > 0.0) omega = o->omega0;
+    const double tau = eta / omega, sigma = eta * omega;
+
+    /* columns: X[p] (n), Y[p] (m) */
+    double** X = (double**)calloc((size_t)P, sizeof(double*));
+    double** Y = (double**)calloc((size_t)P, sizeof(double*));
+    double** X2 = (double**)calloc((size_t)P, sizeof(double*));
+    double** Y2 = (double**)calloc((size_t)P, sizeof(double*));
+    for (int p = 0; p < P; ++p) {
+        X[p] = (double*)xalloc(n);
+        Y[p] = (double*)xalloc(m);
+        X2[p] = (double*)xalloc(n);
+        Y2[p] = (double*)xalloc(m);
+    }
+    double* xn = (double*)xalloc(n);
+    double* yn = (double*)xalloc(m);
+    double* gap = (double*)calloc((size_t)P, sizeof(double));
+    int* order = (int*)calloc((size_t)P, sizeof(int));
+    double* w = (double*)calloc((size_t)P, sizeof(double));
+    double kk[8];
+
+    /* spectral casting and Y^0 = K~ X^0 */
+    const double rad = normK / sqrt((double)n);
+    for (int p = 0; p < P; ++p) {
+        for (int64_t j = 0; j < n; ++j) X[p][j] = rad * G[j * P + p];
+        orc_spmv(lp, vs, X[p], Y[p]);
+    }
+
+    int status = 0, cols = P, round = 0;
+    int64_t zpos = 0;
+    while (cols > 1) {
+        const int j_top = cols;
+        for (int p = 0; p < cols; ++p) {
+            for (int t = 0; t < k_steps; ++t) {
+                orc_pdhg_step(lp, vs, cs, qs, ls, us, X[p], Y[p], tau, sigma, xn, yn);
+                memcpy(X[p], xn, sizeof(double) * (size_t)n);
+                memcpy(Y[p], yn, sizeof(double) * (size_t)m);
+            }
+            orc_kkt(lp, vs, cs, qs, ls, us, X[p], Y[p], omega, kk);
+            gap[p] = fabs(kk[0] - kk[1]);
+            if (gaps) gaps[(int64_t)round * P + p] = gap[p];
+        }
+        /* cull_points: rank by gap (insertion sort, stable), keep the best half */
+        for (int p = 0; p < cols; ++p) order[p] = p;
+        for (int a = 1; a < cols; ++a) {
+            const int v = order[a];
+            int b = a - 1;
+            while (b >= 0 && gap[order[b]] > gap[v]) {
+                order[b + 1] = order[b];
+                --b;
+            }
+            order[b + 1] = v;
+        }
+        const int keep = cols / 2;
+        /* survivors in their old order */
+        int* kept = (int*)calloc((size_t)keep, sizeof(int));
+        for (int a = 0; a < keep; ++a) kept[a] = order[a];
+        for (int a = 1; a < keep; ++a) {
+            const int v = kept[a];
+            int b = a - 1;
+            while (b >= 0 && kept[b] > v) {
+                kept[b + 1] = kept[b];
+                --b;
+            }
+            kept[b + 1] = v;
+        }
+        for (int a = 0; a < keep; ++a) {
+            memcpy(X2[a], X[kept[a]], sizeof(double) * (size_t)n);
+            memcpy(Y2[a], Y[kept[a]], sizeof(double) * (size_t)m);
+        }
+        free(kept);
+        for (int a = 0; a < keep; ++a) {
+            memcpy(X[a], X2[a], sizeof(double) * (size_t)n);
+            memcpy(Y[a], Y2[a], sizeof(double) * (size_t)m);
+        }
+        cols = keep;
+        /* repopulate */
+        if ((round & 1) == 1 && j_top > 2) {
+            if (zpos + (int64_t)keep * keep > nZ) {
+                status = -1;
+                break;
+            }
+            for (int t = 0; t < keep; ++t) {
+                double sw = 0.0;
+                for (int a = 0; a < keep; ++a) {
+                    w[a] = fabs(Z[zpos + (int64_t)t * keep + a]);
+                    sw += w[a];
+                }
+                for (int a = 0; a < keep; ++a) w[a] = sw > 0.0 ? w[a] / sw : 1.0 / keep;
+                double* xt = X[keep + t];
+                double* yt = Y[keep + t];
+                for (int64_t j = 0; j < n; ++j) {
+                    double v = 0.0;
+                    for (int a = 0; a < keep; ++a) v += w[a] * X[a][j];
+                    xt[j] = v;
+                }
+                for (int64_t i = 0; i < m; ++i) {
+                    double v = 0.0;
+                    for (int a = 0; a < keep; ++a) v += w[a] * Y[a][i];
+                    yt[i] = v;
+                }
+            }
+            zpos += (int64_t)keep * keep;
+            cols = 2 * keep;
+        }
+        ++round;
+    }
+    if (status == 0) {
+        for (int64_t j = 0; j < n; ++j) x_out[j] = C[j] * X[0][j];
+        for (int64_t i = 0; i < m; ++i) y_out[i] = R[i] * Y[0][i];
+    }
+    if (rounds_out) *rounds_out = round;
+    for (int p = 0; p < P; ++p) {
+        free(X[p]);
+        free(Y[p]);
+        free(X2[p]);
+        free(Y2[p]);
+    }
+    free(X); free(Y); free(X2); free(Y2);
+    free(xn); free(yn); free(gap); free(order); free(w);
+    free(vs); free(R); free(C); free(cs); free(qs); free(ls); free(us);
+    return status;
 }
