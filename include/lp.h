@@ -223,6 +223,34 @@ lp_status lp_grad(lp_handle h, const lp_opts* opts, int32_t K_iters, int32_t ckp
 lp_status lp_unroll(lp_handle h, const lp_opts* opts, int32_t K_iters, double* x_K, double* y_K,
                     int32_t memory_space, double* tau_sigma_out);
 
+/* Algorithm 7 (fishnet casting, Section 2.5): a multi-start warm start.  On
+ * the scaled problem that lp_solve would build with the same opts (Ruiz per
+ * ruiz_iters, eta = eta_scale / ||K~||_2 or eta0, omega = ||c~|| / ||q~|| or
+ * omega0): P points x~_p = (||K~||_2 / sqrt(n)) g_p and Y = K~ X; then rounds of
+ * k_steps fixed-step PDHG iterations (Algorithm 1) on all points, each round
+ * keeping the half with the smallest |duality gap| and, at odd rounds while
+ * more than two points entered the round, adding one convex combination of the
+ * survivors per survivor (weights |z| / sum |z|), until one point is left.
+ *   P        number of points, a power of two in 1..64
+ *   G        n*P standard-normal draws, G[j*P + p] for coordinate j of point p
+ *   Z        nZ normal draws for the repopulations; lp_fishnet_draws(P) of them
+ *            are used, in order (fewer: LP_INVALID_ARGUMENT)
+ *   x0, y0   receive the surviving point, unscaled (x0[n], y0[m]); pass them to
+ *            lp_solve as opts.x0 / opts.y0 for the warm start
+ *   gaps     host array of rounds*P doubles or NULL: the |gap| of each point of a
+ *            round before its cull, gaps[round*P + point]
+ *   rounds   host int32 or NULL: number of rounds
+ * G, Z, x0 and y0 live in memory_space.  The points are FP64 n x P and m x P
+ * blocks allocated for the call (about 8 (3n + 4m) P bytes) and freed before it
+ * returns.  The random draws are inputs, so the result is deterministic. */
+lp_status lp_fishnet(lp_handle h, const lp_opts* opts, int32_t P, int32_t k_steps,
+                     const double* G, const double* Z, int64_t nZ, double* x0, double* y0,
+                     double* gaps, int32_t* rounds, int32_t memory_space);
+
+/* Number of repopulation draws lp_fishnet consumes for P points (-1 for an
+ * invalid P).  Host only. */
+int64_t lp_fishnet_draws(int32_t P);
+
 /* Replaces values of the LP on its existing sparsity pattern: vals[nnz] (in
  * lp_desc's nonzero order), c[n], q[m], l[n], u[n]; a NULL pointer keeps the old
  * array.  The same validation as lp_create (LP_INVALID_ARGUMENT on NaN, l > u).

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -170,6 +171,25 @@ void lp_destroy(lp_handle p)
     delete p;
 }
 
+// FP64 engine, scaling (Algorithm 3), ||K~||_2 (Algorithm 2), the initial step
+// size eta_scale / ||K~||_2 (Section 3.2) and primal weight ||c~|| / ||q~||
+// (Section 2.4.3), or the caller's eta0 / omega0.
+static lp_status prepare_fp64(Handle* h, const lp_opts* o, double* normK, double* eta0,
+                              double* omega0)
+{
+    LP_TRY(setup_engine<double>(h, o));
+    LP_TRY(setup_scale(h, o, normK));
+    double cs2 = 0.0, qs2 = 0.0;
+    LP_TRY(sum_of_squares(h, h->e64.c, h->n, &cs2));
+    LP_TRY(sum_of_squares(h, h->e64.q, h->m, &qs2));
+    const double cn = std::sqrt(cs2), qn = std::sqrt(qs2);
+    *omega0 = (cn > o->eps_zero && qn > o->eps_zero) ? cn / qn : 1.0;
+    if (o->omega0 > 0.0) *omega0 = o->omega0;
+    *eta0 = *normK > 0.0 ? o->eta_scale / *normK : 1.0;
+    if (o->eta0 > 0.0) *eta0 = o->eta0;
+    return LP_OK;
+}
+
 static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
 {
     LP_TRY(check_opts(o));
@@ -181,18 +201,8 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
         return LP_INVALID_ARGUMENT;
     const double t0 = now_s();
     const long long launches0 = h->launches;
-    // setup: scaling (Algorithm 3), norm (Algorithm 2), step size and weight
-    LP_TRY(setup_engine<double>(h, o));
-    double normK = 0.0;
-    LP_TRY(setup_scale(h, o, &normK));
-    double cs2 = 0.0, qs2 = 0.0;
-    LP_TRY(sum_of_squares(h, h->e64.c, h->n, &cs2));
-    LP_TRY(sum_of_squares(h, h->e64.q, h->m, &qs2));
-    const double cn = std::sqrt(cs2), qn = std::sqrt(qs2);
-    double omega0 = (cn > o->eps_zero && qn > o->eps_zero) ? cn / qn : 1.0;
-    if (o->omega0 > 0.0) omega0 = o->omega0;
-    double eta0 = normK > 0.0 ? o->eta_scale / normK : 1.0;
-    if (o->eta0 > 0.0) eta0 = o->eta0;
+    double normK = 0.0, eta0 = 0.0, omega0 = 0.0;
+    LP_TRY(prepare_fp64(h, o, &normK, &eta0, &omega0));
     if (o->precision == LP_PREC_MIXED) LP_TRY(setup_engine<float>(h, o));
     LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
     const double t1 = now_s();
@@ -266,6 +276,49 @@ lp_status lp_solve_batch(const lp_handle* hs, int32_t count, const lp_opts* o, l
     s = lp_batch_solve(b, o, rs);
     lp_batch_destroy(b);
     return s < 0 ? s : LP_OK;
+}
+
+int64_t lp_fishnet_draws(int32_t P)
+{
+    if (P < 1 || P > 64 || (P & (P - 1)) != 0) return -1;
+    return fishnet_draws(P);
+}
+
+lp_status lp_fishnet(lp_handle p, const lp_opts* o, int32_t P, int32_t k_steps, const double* G,
+                     const double* Z, int64_t nZ, double* x0, double* y0, double* gaps,
+                     int32_t* rounds, int32_t memory_space)
+{
+    if (!p || !o || P < 1 || P > 64 || (P & (P - 1)) != 0 || k_steps < 0 || !G || nZ < 0 ||
+        (nZ > 0 && !Z) || !x0 || !y0)
+        return LP_INVALID_ARGUMENT;
+    if (memory_space != LP_MEM_HOST && memory_space != LP_MEM_DEVICE) return LP_INVALID_ARGUMENT;
+    if (check_opts(o) != LP_OK) return LP_INVALID_ARGUMENT;
+    if (fishnet_draws(P) > nZ) return LP_INVALID_ARGUMENT;
+    Handle* h = &p->h;
+    lp_status s = LP_OK;
+    try {
+        double normK = 0.0, eta0 = 0.0, omega0 = 0.0;
+        s = prepare_fp64(h, o, &normK, &eta0, &omega0);
+        std::vector<double> zh((size_t)nZ);
+        if (s == LP_OK && nZ > 0) {
+            if (memory_space == LP_MEM_HOST) {
+                std::memcpy(zh.data(), Z, sizeof(double) * (size_t)nZ);
+            } else if (cudaMemcpy(zh.data(), Z, sizeof(double) * (size_t)nZ,
+                                  cudaMemcpyDeviceToHost) != cudaSuccess) {
+                s = LP_CUDA_ERROR;
+            }
+        }
+        if (s == LP_OK)
+            s = run_fishnet(h, eta0, omega0, normK, P, k_steps, G, zh.data(), nZ, x0, y0, gaps,
+                            rounds, memory_space);
+    } catch (const std::bad_alloc&) {
+        s = LP_OUT_OF_MEMORY;
+    }
+    if (s < 0) {
+        cudaStreamSynchronize(h->stream);
+        (void)cudaGetLastError();
+    }
+    return s;
 }
 
 lp_status lp_grad(lp_handle p, const lp_opts* o, int32_t K_iters, int32_t ckpt_every,

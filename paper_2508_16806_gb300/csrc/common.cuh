@@ -346,6 +346,12 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes);
 lp_status run_grad(Handle* h, const lp_opts* o, int K_iters, int ckpt, const double* gxK,
                    double* dc, double* dq, double* dvals, double* xK, int space,
                    double* tau_sigma);
+// Algorithm 7 (fishnet.cu): repopulation draws of P columns, and the run on
+// the prepared FP64 engine.
+int64_t fishnet_draws(int P);
+lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, int k_steps,
+                      const double* G, const double* Z_host, int64_t nZ, double* x0, double* y0,
+                      double* gaps_host, int32_t* rounds_out, int space);
 lp_status run_unroll(Handle* h, const lp_opts* o, int K_iters, double* xK, double* yK, int space,
                      double* tau_sigma);
 // setup.cu

@@ -1,0 +1,402 @@
+// Algorithm 7 (fishnet casting, Section 2.5) on the GPU: P candidate points
+// advanced together by fixed-step PDHG, so each product with K or K^T is a
+// sparse-times-dense product over a row-major n x P (m x P) point block instead
+// of P separate SpMVs; cull by duality gap and convex repopulation between
+// rounds.  FP64 throughout (the cull compares gaps, so the decision is taken in
+// the same precision as the FP64 oracle).
+//
+// Readings shared with the oracle: points x~_p = (||K~||_2 / sqrt(n)) g_p on the
+// scaled problem, Y^0 = K~ X^0, k fixed steps of Algorithm 1 per round with the
+// solver's initial eta and omega, cull to the half with the smallest |gap|
+// (stable by index, survivors in their old order), repopulation at odd rounds
+// while more than two columns entered the round, with weights |z| / sum |z|.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "control.cuh"
+
+namespace pdhg {
+namespace {
+
+constexpr int kFW = 8;             // warps per block of the block-SpMM kernels
+constexpr int kFGrid = 152 * 16;   // grid cap of the block-SpMM kernels (persistent rows loop)
+
+// out[r, p] = sum_k val_k X[col_k, p] for the rows r of a CSR matrix; X is row
+// major with P columns (a power of two, 1..64).  One warp per row: lane l serves
+// column l % P (and l + 32 when P = 64); for P < 32 the 32 / P lane groups take
+// every (32 / P)-th nonzero of each batch of 32 and are added by a fixed
+// butterfly.  Each gathered row of X is P contiguous doubles (coalesced).
+template <class Epi>
+__global__ void __launch_bounds__(kFW * 32)
+k_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+       const double* __restrict__ val, int64_t rows, int P, const double* __restrict__ X, Epi epi)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int Pl = P < 32 ? P : 32;
+    const int G = 32 / Pl;
+    const int g = lane / Pl, p = lane % Pl;
+    const bool two = P == 64;
+    for (int64_t r = (int64_t)blockIdx.x * kFW + (threadIdx.x >> 5); r < rows;
+         r += (int64_t)gridDim.x * kFW) {
+        const int64_t s = rp[r], e = rp[r + 1];
+        double a0 = 0.0, a1 = 0.0;
+        for (int64_t b = s; b < e; b += 32) {
+            const int64_t k = b + lane;
+            const int c = k < e ? ci[k] : 0;
+            const double v = k < e ? val[k] : 0.0;
+            const int cnt = e - b < 32 ? (int)(e - b) : 32;
+#pragma unroll 4
+            for (int t0 = 0; t0 < cnt; t0 += G) {
+                const int t = t0 + g;   // <= 31; lanes past the row's end hold v = 0
+                const int ct = __shfl_sync(full, c, t);
+                const double vt = __shfl_sync(full, v, t);
+                const double* xr = X + (int64_t)ct * P;
+                a0 += vt * xr[p];
+                if (two) a1 += vt * xr[p + 32];
+            }
+        }
+        for (int o = Pl; o < 32; o <<= 1) a0 += __shfl_xor_sync(full, a0, o);
+        if (g == 0) {
+            epi.row(r, p, a0);
+            if (two) epi.row(r, p + 32, a1);
+        }
+    }
+}
+
+struct FStore {
+    double* out;
+    int P;
+    __device__ void row(int64_t r, int p, double v) const { out[r * P + p] = v; }
+};
+
+// x' = proj_X(x - tau (c - K^T y)) per column (Algorithm 1, theta = 1)
+struct FPrimal {
+    const double* X;
+    double* Xn;
+    const double *c, *l, *u;
+    double tau;
+    int P;
+    __device__ void row(int64_t j, int p, double kty) const
+    {
+        const int64_t t = j * P + p;
+        double v = X[t] - tau * (c[j] - kty);
+        if (v < l[j]) v = l[j];
+        if (v > u[j]) v = u[j];
+        Xn[t] = v;
+    }
+};
+
+// y' = proj_Y(y + sigma (q - (2 K x' - K x))); K x' replaces K x
+struct FDual {
+    const double* Y;
+    double* Yn;
+    double* KX;
+    const double* q;
+    const uint8_t* sense;
+    double sigma;
+    int P;
+    __device__ void row(int64_t i, int p, double kxn) const
+    {
+        const int64_t t = i * P + p;
+        double v = Y[t] + sigma * (q[i] - (2.0 * kxn - KX[t]));
+        if (sense[i] && v < 0.0) v = 0.0;
+        Yn[t] = v;
+        KX[t] = kxn;
+    }
+};
+
+__global__ void k_cast(int64_t n, int P, double rad, const double* G, double* X)
+{
+    const int64_t total = n * P;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        X[t] = rad * G[t];
+}
+
+// Per-column sums over the rows of a point block, fixed order: thread t of a
+// block serves column t % P and rows blockIdx.x * (256 / P) + t / P, ... .
+// part[q * P * gridDim.x + p * gridDim.x + block] for the NQ sums.
+constexpr int kGapNT = 256;
+
+template <int NQ>
+__device__ void column_partials(const double (&v)[NQ], int P, double* part)
+{
+    __shared__ double sh[NQ][kGapNT];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] = v[q];
+    __syncthreads();
+    if ((int)threadIdx.x < P) {
+        const int per = kGapNT / P;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int k = 0; k < per; ++k) s += sh[q][k * P + threadIdx.x];
+            part[((size_t)q * P + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+        }
+    }
+}
+
+// c~^T x_p and l~^T lambda_p^+ + u~^T lambda_p^-, lambda_p = proj_Lambda(c~ - K~^T y_p)
+__global__ void __launch_bounds__(kGapNT)
+k_gap_cols(int64_t n, int P, const double* X, const double* KTY, const double* c,
+           const double* l, const double* u, double* part)
+{
+    const int p = threadIdx.x % P, per = kGapNT / P;
+    double v[2] = {0.0, 0.0};
+    for (int64_t j = (int64_t)blockIdx.x * per + threadIdx.x / P; j < n;
+         j += (int64_t)gridDim.x * per) {
+        const int64_t t = j * P + p;
+        const double cj = c[j], lj = l[j], uj = u[j];
+        v[0] += cj * X[t];
+        const double lam = proj_lambda(cj - KTY[t], isfinite(lj), isfinite(uj));
+        if (lam > 0.0) v[1] += lj * lam;
+        if (lam < 0.0) v[1] += uj * lam;
+    }
+    column_partials<2>(v, P, part);
+}
+
+// q~^T y_p
+__global__ void __launch_bounds__(kGapNT)
+k_gap_rows(int64_t m, int P, const double* Y, const double* q, double* part)
+{
+    const int p = threadIdx.x % P, per = kGapNT / P;
+    double v[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * per + threadIdx.x / P; i < m;
+         i += (int64_t)gridDim.x * per)
+        v[0] += q[i] * Y[i * P + p];
+    column_partials<1>(v, P, part);
+}
+
+// |pobj_p - dobj_p| per column
+__global__ void k_gap_final(int P, const double* partC, int nbC, const double* partR, int nbR,
+                            double* gap)
+{
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        double pobj = 0.0, lt = 0.0, qy = 0.0;
+        for (int b = 0; b < nbC; ++b) pobj += partC[(size_t)p * nbC + b];
+        for (int b = 0; b < nbC; ++b) lt += partC[((size_t)P + p) * nbC + b];
+        for (int b = 0; b < nbR; ++b) qy += partR[(size_t)p * nbR + b];
+        gap[p] = fabs(pobj - (qy + lt));
+    }
+}
+
+// dst (rows x Pn) from src (rows x Po): columns t < keep copy src column
+// kept[t]; column t >= keep is sum_a W[(t - keep) * keep + a] * src column kept[a].
+__global__ void k_combine(int64_t rows, int Po, int Pn, int keep, const int* kept,
+                          const double* W, const double* src, double* dst)
+{
+    const int64_t total = rows * Pn;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / Pn;
+        const int t = (int)(e - r * Pn);
+        const double* s = src + r * Po;
+        if (t < keep) {
+            dst[e] = s[kept[t]];
+        } else {
+            const double* w = W + (size_t)(t - keep) * keep;
+            double v = 0.0;
+            for (int a = 0; a < keep; ++a) v += w[a] * s[kept[a]];
+            dst[e] = v;
+        }
+    }
+}
+
+__global__ void k_unscale(int64_t count, const double* v, const double* f, double* out)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = f[t] * v[t];
+}
+
+int ew_blocks(int64_t count)
+{
+    int64_t g = (count + 255) / 256;
+    if (g < 1) g = 1;
+    if (g > kEWGrid * 4) g = kEWGrid * 4;
+    return (int)g;
+}
+
+int spmm_blocks(int64_t rows)
+{
+    int64_t g = (rows + kFW - 1) / kFW;
+    if (g < 1) g = 1;
+    if (g > kFGrid) g = kFGrid;
+    return (int)g;
+}
+
+// device buffers owned by one fishnet call
+struct Scratch {
+    std::vector<void*> ptrs;
+    ~Scratch()
+    {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    lp_status get(T** p, size_t count)
+    {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            *p = nullptr;
+            return e == cudaErrorMemoryAllocation ? LP_OUT_OF_MEMORY : LP_CUDA_ERROR;
+        }
+        ptrs.push_back(*p);
+        return LP_OK;
+    }
+};
+
+}  // namespace
+
+int64_t fishnet_draws(int P)
+{
+    int64_t total = 0;
+    int cols = P, i = 0;
+    while (cols > 1) {
+        const int keep = cols / 2;
+        if ((i & 1) == 1 && cols > 2) {
+            total += (int64_t)keep * keep;
+            cols = 2 * keep;
+        } else {
+            cols = keep;
+        }
+        ++i;
+    }
+    return total;
+}
+
+lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, int k_steps,
+                      const double* G, const double* Z_host, int64_t nZ, double* x0, double* y0,
+                      double* gaps_host, int32_t* rounds_out, int space)
+{
+    const int64_t m = h->m, n = h->n;
+    const Engine<double>& E = h->e64;
+    cudaStream_t st = h->stream;
+    if (fishnet_draws(P) > nZ) return LP_INVALID_ARGUMENT;
+    Scratch S;
+    double *X, *Xn, *KTY, *Y, *Yn, *KX, *KX2, *Gd = nullptr, *gap, *W, *partC, *partR;
+    int* kept_d;
+    LP_TRY(S.get(&X, (size_t)n * P));
+    LP_TRY(S.get(&Xn, (size_t)n * P));
+    LP_TRY(S.get(&KTY, (size_t)n * P));
+    LP_TRY(S.get(&Y, (size_t)m * P));
+    LP_TRY(S.get(&Yn, (size_t)m * P));
+    LP_TRY(S.get(&KX, (size_t)m * P));
+    LP_TRY(S.get(&KX2, (size_t)m * P));
+    LP_TRY(S.get(&gap, (size_t)P));
+    LP_TRY(S.get(&W, (size_t)P * P));
+    LP_TRY(S.get(&kept_d, (size_t)P));
+    const int nbC = ew_blocks(n), nbR = ew_blocks(m);
+    LP_TRY(S.get(&partC, (size_t)2 * P * nbC));
+    LP_TRY(S.get(&partR, (size_t)P * nbR));
+    if (space == LP_MEM_HOST) {
+        LP_TRY(S.get(&Gd, (size_t)n * P));
+        LP_CUDA_TRY(cudaMemcpyAsync(Gd, G, sizeof(double) * (size_t)n * P,
+                                    cudaMemcpyHostToDevice, st));
+        G = Gd;
+    }
+    const double tau = eta / omega, sigma = eta * omega;
+    // spectral casting, Y^0 = K~ X^0 (also the first K x)
+    k_cast<<<ew_blocks(n * P), 256, 0, st>>>(n, P, normK / std::sqrt((double)n), G, X);
+    k_spmm<FStore><<<spmm_blocks(m), kFW * 32, 0, st>>>(h->rp, h->ci, E.val, m, P, X,
+                                                          FStore{Y, P});
+    LP_CUDA_TRY(cudaMemcpyAsync(KX, Y, sizeof(double) * (size_t)m * P, cudaMemcpyDeviceToDevice,
+                                st));
+    h->launches += 2;
+    LP_CUDA_TRY(cudaGetLastError());
+
+    std::vector<double> gh(P), wh((size_t)P * P);
+    std::vector<int> order(P), kept(P);
+    int cols = P, round = 0;
+    int64_t zpos = 0;
+    while (cols > 1) {
+        const int j_top = cols;
+        for (int t = 0; t < k_steps; ++t) {
+            k_spmm<FPrimal><<<spmm_blocks(n), kFW * 32, 0, st>>>(
+                h->trp, h->tci, E.tval, n, cols, Y, FPrimal{X, Xn, E.c, E.l, E.u, tau, cols});
+            k_spmm<FDual><<<spmm_blocks(m), kFW * 32, 0, st>>>(
+                h->rp, h->ci, E.val, m, cols, Xn, FDual{Y, Yn, KX, E.q, h->sense, sigma, cols});
+            std::swap(X, Xn);
+            std::swap(Y, Yn);
+            h->launches += 2;
+        }
+        // |duality gap| of every column
+        k_spmm<FStore><<<spmm_blocks(n), kFW * 32, 0, st>>>(h->trp, h->tci, E.tval, n, cols, Y,
+                                                              FStore{KTY, cols});
+        k_gap_cols<<<nbC, kGapNT, 0, st>>>(n, cols, X, KTY, E.c, E.l, E.u, partC);
+        k_gap_rows<<<nbR, kGapNT, 0, st>>>(m, cols, Y, E.q, partR);
+        k_gap_final<<<1, 64, 0, st>>>(cols, partC, nbC, partR, nbR, gap);
+        h->launches += 4;
+        LP_CUDA_TRY(cudaGetLastError());
+        LP_CUDA_TRY(cudaMemcpyAsync(gh.data(), gap, sizeof(double) * cols,
+                                    cudaMemcpyDeviceToHost, st));
+        LP_CUDA_TRY(cudaStreamSynchronize(st));
+        if (gaps_host)
+            for (int p = 0; p < cols; ++p) gaps_host[(int64_t)round * P + p] = gh[p];
+        // cull_points: the half with the smallest gaps, in their old order
+        std::iota(order.begin(), order.begin() + cols, 0);
+        std::stable_sort(order.begin(), order.begin() + cols,
+                         [&](int a, int b) { return gh[a] < gh[b]; });
+        const int keep = cols / 2;
+        std::copy(order.begin(), order.begin() + keep, kept.begin());
+        std::sort(kept.begin(), kept.begin() + keep);
+        int ncols = keep;
+        // repopulate: one convex combination of the survivors per survivor
+        if ((round & 1) == 1 && j_top > 2) {
+            for (int t = 0; t < keep; ++t) {
+                double sw = 0.0;
+                for (int a = 0; a < keep; ++a) {
+                    wh[(size_t)t * keep + a] = std::fabs(Z_host[zpos + (int64_t)t * keep + a]);
+                    sw += wh[(size_t)t * keep + a];
+                }
+                for (int a = 0; a < keep; ++a)
+                    wh[(size_t)t * keep + a] =
+                        sw > 0.0 ? wh[(size_t)t * keep + a] / sw : 1.0 / keep;
+            }
+            zpos += (int64_t)keep * keep;
+            ncols = 2 * keep;
+            LP_CUDA_TRY(cudaMemcpyAsync(W, wh.data(), sizeof(double) * (size_t)keep * keep,
+                                        cudaMemcpyHostToDevice, st));
+        }
+        LP_CUDA_TRY(cudaMemcpyAsync(kept_d, kept.data(), sizeof(int) * keep,
+                                    cudaMemcpyHostToDevice, st));
+        k_combine<<<ew_blocks(n * ncols), 256, 0, st>>>(n, cols, ncols, keep, kept_d, W, X, Xn);
+        k_combine<<<ew_blocks(m * ncols), 256, 0, st>>>(m, cols, ncols, keep, kept_d, W, Y, Yn);
+        k_combine<<<ew_blocks(m * ncols), 256, 0, st>>>(m, cols, ncols, keep, kept_d, W, KX, KX2);
+        h->launches += 3;
+        LP_CUDA_TRY(cudaGetLastError());
+        std::swap(X, Xn);
+        std::swap(Y, Yn);
+        std::swap(KX, KX2);
+        // the host vectors above are reused next round: wait for the copies
+        LP_CUDA_TRY(cudaStreamSynchronize(st));
+        cols = ncols;
+        ++round;
+    }
+    // the survivor, unscaled (x = C x~, y = R y~)
+    double *xo = x0, *yo = y0, *xd = nullptr, *yd = nullptr;
+    if (space == LP_MEM_HOST) {
+        LP_TRY(S.get(&xd, (size_t)n));
+        LP_TRY(S.get(&yd, (size_t)m));
+        xo = xd;
+        yo = yd;
+    }
+    k_unscale<<<ew_blocks(n), 256, 0, st>>>(n, X, h->C, xo);
+    k_unscale<<<ew_blocks(m), 256, 0, st>>>(m, Y, h->R, yo);
+    h->launches += 2;
+    LP_CUDA_TRY(cudaGetLastError());
+    if (space == LP_MEM_HOST) {
+        LP_CUDA_TRY(cudaMemcpyAsync(x0, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        LP_CUDA_TRY(cudaMemcpyAsync(y0, yd, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    }
+    LP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rounds_out) *rounds_out = round;
+    return LP_OK;
+}
+
+}  // namespace pdhg

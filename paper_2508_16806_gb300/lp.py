@@ -80,7 +80,7 @@ class LpResult(C.Structure):
 EXPORTS = ("lp_opts_default", "lp_create", "lp_solve", "lp_solve_batch", "lp_grad",
            "lp_unroll", "lp_update_values", "lp_profile_step", "lp_destroy", "lp_status_string",
            "lp_abi_version", "lp_kkt_noalloc", "lp_batch_create", "lp_batch_solve",
-           "lp_batch_destroy")
+           "lp_batch_destroy", "lp_fishnet", "lp_fishnet_draws")
 
 _lib = None
 
@@ -134,6 +134,12 @@ def load(build_if_missing: bool = True):
     lib.lp_kkt_noalloc.argtypes = [P(LpDesc), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                    C.c_void_p]
     lib.lp_kkt_noalloc.restype = C.c_int
+    lib.lp_fishnet.argtypes = [C.c_void_p, P(LpOpts), C.c_int32, C.c_int32, C.c_void_p,
+                               C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                               P(C.c_int32), C.c_int32]
+    lib.lp_fishnet.restype = C.c_int
+    lib.lp_fishnet_draws.argtypes = [C.c_int32]
+    lib.lp_fishnet_draws.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -178,6 +184,16 @@ def lp_unroll(h, opts: LpOpts, K_iters: int, x_K: int | None, y_K: int | None,
               memory_space: int, tau_sigma_out=None) -> int:
     return load().lp_unroll(h, C.byref(opts), K_iters, x_K or None, y_K or None, memory_space,
                             tau_sigma_out)
+
+
+def lp_fishnet(h, opts: LpOpts, P: int, k_steps: int, G: int, Z: int | None, nZ: int, x0: int,
+               y0: int, gaps=None, rounds=None, memory_space: int = LP_MEM_HOST) -> int:
+    return load().lp_fishnet(h, C.byref(opts), P, k_steps, G, Z or None, nZ, x0, y0, gaps,
+                             rounds, memory_space)
+
+
+def lp_fishnet_draws(P: int) -> int:
+    return int(load().lp_fishnet_draws(P))
 
 
 def lp_update_values(h, vals=None, c=None, q=None, l=None, u=None,
@@ -330,6 +346,23 @@ class Problem:
             for r in tr[: min(res.trace_len, trace_cap)]:
                 trace.append({f: getattr(r, f) for f in TRACE_FIELDS})
         return x, y, info, trace
+
+    def fishnet(self, P: int, k_steps: int, G, Z, **opts):
+        """Algorithm 7 on this LP: G (n, P) and Z (1-D) are numpy normal draws.
+        Returns (x0, y0, gaps (rounds, P) with NaN for absent points, rounds)."""
+        o = lp_opts_default(**opts)
+        Gh = np.ascontiguousarray(np.asarray(G, np.float64).reshape(self.n, P))
+        Zh = np.ascontiguousarray(np.asarray(Z, np.float64).ravel())
+        x0 = np.empty(self.n)
+        y0 = np.empty(self.m)
+        gaps = np.full((2 * 8 + 2, P), np.nan)
+        rounds = C.c_int32(0)
+        s = lp_fishnet(self.handle, o, P, k_steps, Gh.ctypes.data,
+                       Zh.ctypes.data if Zh.size else None, Zh.size, x0.ctypes.data,
+                       y0.ctypes.data, gaps.ctypes.data, C.byref(rounds), LP_MEM_HOST)
+        if s < 0:
+            raise LpError(s, "lp_fishnet")
+        return x0, y0, gaps[: rounds.value], rounds.value
 
     def profile_step(self, precision: int = LP_PREC_FP64, reps: int = 20):
         return lp_profile_step(self.handle, precision, reps)
