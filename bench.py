@@ -49,6 +49,11 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-4)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fishnet", action="store_true",
+                   help="skip the Algorithm 7 warm-start measurement (extra key)")
+    p.add_argument("--fishnet-profile", action="store_true",
+                   help="one lp_fishnet call on the workload (32 points, 2 steps per round), "
+                        "for kernel profilers; prints its time")
     p.add_argument("--host-loop", action="store_true",
                    help="host-driven loop graph (lp_opts.loop_mode = 1), for ncu launch lists")
     p.add_argument("--kernel-profile", action="store_true",
@@ -313,8 +318,90 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def fishnet_schedule(P):
+    """Point counts of the rounds of Algorithm 7 (cull to half; repopulate back
+    at odd rounds while more than two points entered the round)."""
+    out, cols, i = [], P, 0
+    while cols > 1:
+        out.append(cols)
+        keep = cols // 2
+        cols = 2 * keep if (i % 2 == 1 and cols > 2) else keep
+        i += 1
+    return out
+
+
+def spmm_bytes(lp, P, s=4):
+    """Algorithmic bytes of one fixed PDHG step on P points with s-byte values:
+    K^T-side block product with the primal update, then K-side with the dual
+    update.  Matrix (s-byte value + 4-byte index per nonzero, row pointers), one
+    gathered row of P values per nonzero, point blocks read / written by the
+    epilogues, c, l, u, q and sense."""
+    t_side = lp.nnz * (s + 4) + (lp.n + 1) * 8 + lp.nnz * P * s + lp.n * P * s * 2 + lp.n * 3 * s
+    k_side = lp.nnz * (s + 4) + (lp.m + 1) * 8 + lp.nnz * P * s + lp.m * P * s * 4 + lp.m * (s + 1)
+    return t_side + k_side
+
+
+def fishnet_leg(L, lp, prob, stream, opts, cold_iters, cold_s, rank, P=32, k_steps=20):
+    """Algorithm 7 on the bench LP (device-resident draws, CUDA events on the
+    solver's stream), then the mixed solve from its point."""
+    import torch
+    rng = np.random.default_rng(20250821 + rank)
+    G = torch.from_numpy(rng.standard_normal((lp.n, P))).to("cuda")
+    nz = L.lp_fishnet_draws(P)
+    Z = torch.from_numpy(rng.standard_normal(nz)).to("cuda")
+    x0 = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+    y0 = torch.empty(lp.m, dtype=torch.float64, device="cuda")
+    o = L.lp_opts_default(**{k: v for k, v in opts.items() if k != "loop_mode"})
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s = L.lp_fishnet(prob.handle, o, P, k_steps, G.data_ptr(), Z.data_ptr(), nz, x0.data_ptr(),
+                     y0.data_ptr(), None, None, L.LP_MEM_DEVICE)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if s != 0:
+        return {"error": L.lp_status_string(s)}
+    fish_s = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    _, _, info, _ = prob.solve(x0=x0.cpu().numpy(), y0=y0.cpu().numpy(), **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    warm_s = e0.elapsed_time(e1) / 1e3
+    sched = fishnet_schedule(P)
+    s = 4 if o.precision == L.LP_PREC_MIXED else 8
+    steps_bytes = sum(k_steps * spmm_bytes(lp, c, s) for c in sched)
+    return {"points": P, "k_steps": k_steps, "rounds": len(sched), "points_per_round": sched,
+            "fishnet_s": fish_s,
+            "precision": "f32 point blocks, f64 gap reductions" if s == 4 else "f64",
+            "block_spmm_bytes": steps_bytes,
+            "block_spmm_gbs_lower_bound": steps_bytes / fish_s / 1e9,
+            "warm_solve_s": warm_s, "warm_iters": int(info["iters"]),
+            "warm_status": L.STATUS[info["status"]],
+            "cold_solve_s": cold_s, "cold_iters": cold_iters,
+            "note": "fishnet_s includes Ruiz, the power iteration, gap reductions, culls and "
+                    "host round trips; the bandwidth is therefore a lower bound for the block "
+                    "products"}
+
+
+def fishnet_profile(args):
+    import torch
+    from paper_2508_16806_gb300 import lp as L
+    L.load()
+    lp, desc = workload(args.workload)
+    stream = torch.cuda.Stream()
+    prob = L.Problem(lp, device_copy=True, stream=stream)
+    out = fishnet_leg(L, lp, prob, stream, dict(tol=args.tol, precision=L.LP_PREC_MIXED,
+                                                max_iters=1), 0, 0.0, 0, P=32, k_steps=2)
+    print(json.dumps({"fishnet_profile": desc, "fishnet_s": out.get("fishnet_s")}), flush=True)
+    prob.close()
+
+
 def main():
     args = parse()
+    if args.fishnet_profile:
+        fishnet_profile(args)
+        return
     if args.kernel_profile:
         kernel_profile(args)
         return
@@ -409,6 +496,10 @@ def main():
         e2e = {"value": min(times), "unit": "s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    fish = None
+    if not args.no_fishnet:
+        fish = fishnet_leg(L, lp, prob, stream, opts, iters, ms / 1e3, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_iters, src = reference_iterations(args.tol)
@@ -445,6 +536,7 @@ def main():
             "gpu_launches": launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "fishnet": fish,
         }
         print(json.dumps(line), flush=True)
     prob.close()

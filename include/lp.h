@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define LP_ABI_VERSION 2
+#define LP_ABI_VERSION 3
 
 typedef struct lp_problem_s* lp_handle;
 
@@ -117,6 +117,11 @@ typedef struct {
     int32_t reserved_opts;       /* must be 0 */
     double infeas_tol;           /* tolerance of Algorithm 6, applied to the differences
                                     normalised to unit length (default 1e-6) */
+    int32_t autotune;            /* 1 (default): at the first solve of each precision, time the
+                                    candidate warp-task schedules of K and K^T (nonzeros and
+                                    rows per task) on the device and keep the fastest of each;
+                                    0: the largest tasks (the compiled defaults) */
+    int32_t reserved_opts2;      /* must be 0 */
 } lp_opts;
 
 /* One record per KKT check (the start, every check_every accepted
@@ -240,9 +245,12 @@ lp_status lp_unroll(lp_handle h, const lp_opts* opts, int32_t K_iters, double* x
  *   gaps     host array of rounds*P doubles or NULL: the |gap| of each point of a
  *            round before its cull, gaps[round*P + point]
  *   rounds   host int32 or NULL: number of rounds
- * G, Z, x0 and y0 live in memory_space.  The points are FP64 n x P and m x P
- * blocks allocated for the call (about 8 (3n + 4m) P bytes) and freed before it
- * returns.  The random draws are inputs, so the result is deterministic. */
+ * G, Z, x0 and y0 live in memory_space.  opts.precision selects the point
+ * blocks and products: LP_PREC_FP64 (the cull decisions then match an FP64
+ * evaluation) or LP_PREC_MIXED (FP32 blocks and products, FP64 gap reductions).
+ * The blocks (n x P and m x P, about s (3n + 4m) P bytes for s-byte values) are
+ * allocated for the call and freed before it returns.  The random draws are
+ * inputs, so the result is deterministic. */
 lp_status lp_fishnet(lp_handle h, const lp_opts* opts, int32_t P, int32_t k_steps,
                      const double* G, const double* Z, int64_t nZ, double* x0, double* y0,
                      double* gaps, int32_t* rounds, int32_t memory_space);

@@ -49,6 +49,8 @@ struct BatchMeta {
 template <typename T>
 struct BatchSched {
     bool ready = false;
+    bool tuned = false;
+    SchedParams pK, pT;                              // task shapes of the two schedules
     int ntK = 0, ntT = 0;
     int32_t *taskK = nullptr, *taskT = nullptr;      // task -> first row (K) / column (K^T)
     int64_t *nzK = nullptr, *nzT = nullptr;          // task -> first nonzero
@@ -633,14 +635,39 @@ __global__ void kb_read_clock(unsigned long long* t) { *t = global_ns(); }
 
 // ---------------------------------------------------------------- host
 
+// LP-aligned task boundaries over all rows (K: rows = true, K^T: columns)
+std::vector<int32_t> batch_blocks(BatchHandle* bh, bool rows, SchedParams p)
+{
+    Handle* h = &bh->h;
+    std::vector<int32_t> out;
+    for (int k = 0; k < bh->meta.B; ++k) {
+        const int64_t a = rows ? bh->meta.row0[k] : bh->meta.col0[k];
+        const int64_t b = rows ? bh->meta.row0[k + 1] : bh->meta.col0[k + 1];
+        const int64_t* rp = (rows ? h->h_rp.data() : h->h_trp.data()) + a;
+        std::vector<int32_t> t = make_row_blocks(rp, b - a, p.cap, p.max_rows);
+        for (size_t i = 0; i + 1 < t.size(); ++i) out.push_back((int32_t)(t[i] + a));
+    }
+    out.push_back((int32_t)(rows ? h->m : h->n));
+    return out;
+}
+
+// Builds (or rebuilds with other task shapes) the LP-aligned schedules and the
+// per-task partials of precision T.
 template <typename T>
-lp_status build_sched(BatchHandle* bh)
+lp_status build_sched(BatchHandle* bh, SchedParams pK, SchedParams pT)
 {
     BatchSched<T>& S = sched_of<T>(bh);
-    if (S.ready) return LP_OK;
+    if (S.ready && S.pK.cap == pK.cap && S.pK.max_rows == pK.max_rows && S.pT.cap == pT.cap &&
+        S.pT.max_rows == pT.max_rows)
+        return LP_OK;
     Handle* h = &bh->h;
     const int B = bh->meta.B;
-    const int cap = cap_w<T>();
+    if (S.ready) {
+        for (void* p : {(void*)S.taskK, (void*)S.taskT, (void*)S.lpK, (void*)S.lpT,
+                        (void*)S.t0K, (void*)S.t0T, (void*)S.nzK, (void*)S.nzT, (void*)S.partK,
+                        (void*)S.partT, (void*)S.partR, (void*)S.partC})
+            dev_free(h, p);
+    }
     std::vector<int32_t> tK, tT, lK, lT, k0(B + 1), c0(B + 1);
     std::vector<int64_t> nK, nT;
     for (int k = 0; k < B; ++k) {
@@ -648,8 +675,10 @@ lp_status build_sched(BatchHandle* bh)
         c0[k] = (int32_t)tT.size();
         const int64_t r0 = bh->meta.row0[k], r1 = bh->meta.row0[k + 1];
         const int64_t q0 = bh->meta.col0[k], q1 = bh->meta.col0[k + 1];
-        std::vector<int32_t> a = make_row_blocks(h->h_rp.data() + r0, r1 - r0, cap, kTaskRows);
-        std::vector<int32_t> c = make_row_blocks(h->h_trp.data() + q0, q1 - q0, cap, kTaskRows);
+        std::vector<int32_t> a =
+            make_row_blocks(h->h_rp.data() + r0, r1 - r0, pK.cap, pK.max_rows);
+        std::vector<int32_t> c =
+            make_row_blocks(h->h_trp.data() + q0, q1 - q0, pT.cap, pT.max_rows);
         for (size_t i = 0; i + 1 < a.size(); ++i) {
             tK.push_back((int32_t)(a[i] + r0));
             lK.push_back(k);
@@ -694,6 +723,8 @@ lp_status build_sched(BatchHandle* bh)
     LP_TRY(dev_alloc_n(h, &S.partR, kRowQ * (size_t)S.ntK + 8));
     LP_TRY(dev_alloc_n(h, &S.partC, kColQ * (size_t)S.ntT + 8));
     LP_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    S.pK = pK;
+    S.pT = pT;
     // vectors and scaled data of this precision
     Engine<T>& E = engine_of<T>(h);
     if (!E.ready) {
@@ -714,6 +745,49 @@ lp_status build_sched(BatchHandle* bh)
 }
 
 template <typename T>
+lp_status ensure_sched(BatchHandle* bh)
+{
+    if (sched_of<T>(bh).ready) return LP_OK;
+    const SchedParams d{cap_w<T>(), kTaskRows};
+    return build_sched<T>(bh, d, d);
+}
+
+// Autotuner of the batch schedules (once per precision): candidate task shapes
+// are timed on the stacked matrix with this precision's values; a change
+// rebuilds the schedules and drops the captured loop graph.
+template <typename T>
+lp_status tune_batch(BatchHandle* bh)
+{
+    BatchSched<T>& S = sched_of<T>(bh);
+    if (S.tuned) return LP_OK;
+    Handle* h = &bh->h;
+    Engine<T>& E = engine_of<T>(h);
+    int sms = 0;
+    LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    LP_CUDA_TRY(cudaMemsetAsync(E.XA, 0, sizeof(T) * (size_t)h->n, h->stream));
+    LP_CUDA_TRY(cudaMemsetAsync(E.YA, 0, sizeof(T) * (size_t)h->m, h->stream));
+    SchedParams pK, pT;
+    float msK = 0.0f, msT = 0.0f;
+    LP_TRY(tune_schedule<T>(
+        sms, h->stream, [&](int cap, int rows) { return batch_blocks(bh, true, {cap, rows}); },
+        h->h_rp.data(), h->rp, h->ci, E.val, E.XA, E.KXA, h->n, h->dev_err, &pK, &msK));
+    LP_TRY(tune_schedule<T>(
+        sms, h->stream, [&](int cap, int rows) { return batch_blocks(bh, false, {cap, rows}); },
+        h->h_trp.data(), h->trp, h->tci, E.tval, E.YA, E.KTYA, h->m, h->dev_err, &pT, &msT));
+    h->launches += 2 * 6 * 4;
+    if (pK.cap != S.pK.cap || pK.max_rows != S.pK.max_rows || pT.cap != S.pT.cap ||
+        pT.max_rows != S.pT.max_rows) {
+        LP_TRY(build_sched<T>(bh, pK, pT));
+        if (bh->exec) {
+            cudaGraphExecDestroy(bh->exec);
+            bh->exec = nullptr;
+        }
+    }
+    S.tuned = true;
+    return LP_OK;
+}
+
+template <typename T>
 __global__ void kb_cast(const double* src, const int32_t* perm, T* dst, int64_t count)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
@@ -728,7 +802,7 @@ lp_status batch_scale(BatchHandle* bh, const lp_opts* o, double* normK_dev)
     const int B = bh->meta.B;
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     cudaStream_t st = h->stream;
-    LP_TRY(build_sched<double>(bh));
+    LP_TRY(ensure_sched<double>(bh));
     Engine<double>& E = h->e64;
     BatchSched<double>& S = bh->s64;
     LP_CUDA_TRY(cudaMemcpyAsync(E.val, h->val0, pad8(nnz) * sizeof(double),
@@ -909,7 +983,7 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
     // setup: per-LP Ruiz and norms in FP64, then this precision's copies
     double* normK = bh->lpd + 3 * B;
     LP_TRY(batch_scale(bh, o, normK));
-    LP_TRY(build_sched<T>(bh));
+    LP_TRY(ensure_sched<T>(bh));
     Engine<T>& E = engine_of<T>(h);
     if (sizeof(T) == 4) {
         const Engine<double>& D = h->e64;
@@ -967,6 +1041,7 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
                                                        bh->meta.cn, tmpl, o->eta_scale, o->eta0,
                                                        o->omega0, o->eps_zero, t0);
     LP_TRY(engine_factors<T>(h));
+    if (o->autotune) LP_TRY(tune_batch<T>(bh));
     // start point and its products
     kb_init_state<T><<<grid_n(n + m, 256, 8192), 256, 0, st>>>(E.X[0], E.Y[0], E.XANC, E.YANC,
                                                                E.XS, E.YS, E.l, E.u, n, m);

@@ -42,6 +42,7 @@ lp_status check_opts(const lp_opts* o)
     if (o->loop_mode != 0 && o->loop_mode != 1) return LP_INVALID_ARGUMENT;
     if (o->infeas_detect != 0 && o->infeas_detect != 1) return LP_INVALID_ARGUMENT;
     if (o->infeas_detect && !(o->infeas_tol > 0.0)) return LP_INVALID_ARGUMENT;
+    if (o->autotune != 0 && o->autotune != 1) return LP_INVALID_ARGUMENT;
     return LP_OK;
 }
 
@@ -94,6 +95,7 @@ void lp_opts_default(lp_opts* o)
     o->loop_mode = 0;
     o->infeas_detect = 1;
     o->infeas_tol = 1e-6;
+    o->autotune = 1;
 }
 
 const char* lp_status_string(lp_status s)
@@ -299,6 +301,7 @@ lp_status lp_fishnet(lp_handle p, const lp_opts* o, int32_t P, int32_t k_steps, 
     try {
         double normK = 0.0, eta0 = 0.0, omega0 = 0.0;
         s = prepare_fp64(h, o, &normK, &eta0, &omega0);
+        if (s == LP_OK && o->precision == LP_PREC_MIXED) s = setup_engine<float>(h, o);
         std::vector<double> zh((size_t)nZ);
         if (s == LP_OK && nZ > 0) {
             if (memory_space == LP_MEM_HOST) {
@@ -309,8 +312,8 @@ lp_status lp_fishnet(lp_handle p, const lp_opts* o, int32_t P, int32_t k_steps, 
             }
         }
         if (s == LP_OK)
-            s = run_fishnet(h, eta0, omega0, normK, P, k_steps, G, zh.data(), nZ, x0, y0, gaps,
-                            rounds, memory_space);
+            s = run_fishnet(h, o->precision, eta0, omega0, normK, P, k_steps, G, zh.data(), nZ,
+                            x0, y0, gaps, rounds, memory_space);
     } catch (const std::bad_alloc&) {
         s = LP_OUT_OF_MEMORY;
     }

@@ -68,6 +68,12 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Warp-task schedule parameters: nonzeros (cap) and rows (max_rows) per task.
+struct SchedParams {
+    int cap = 0;
+    int max_rows = 0;
+};
+
 // State and scaled data of one precision T (double or float).
 template <typename T>
 struct Engine {
@@ -90,11 +96,13 @@ struct Engine {
     int32_t* bcol = nullptr;   int ntblk = 0;   // K^T rows
     int64_t* bnzK = nullptr;   int64_t* bnzT = nullptr;   // first nonzero of each task
     int gK = 0, gT = 0;                         // blocks of the K and K^T SpMV launches
+    SchedParams schedK, schedT;                 // parameters of the two schedules
+    bool tuned = false;                         // schedules chosen by the autotuner
     // Ruiz factors R, C and their reciprocals in this precision (KKT checks)
     T* Rt = nullptr; T* Ct = nullptr; T* Rinv = nullptr; T* Cinv = nullptr;
     // reduction partials
-    double* partD = nullptr;   // [gK]
-    double* partT = nullptr;   // [2][gT]
+    double* partD = nullptr;   // [gK] (sized for the largest grid)
+    double* partT = nullptr;   // [2][gT] (sized for the largest grid)
     double* partR = nullptr;   // [kRowQ][kEWGrid]
     double* partC = nullptr;   // [kColQ][kEWGrid]
     Ctrl* ctrl = nullptr;
@@ -326,6 +334,15 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK);
 template <typename T> lp_status setup_engine(Handle* h, const lp_opts* o);
 // Engine<T>::Rt, Ct, Rinv, Cinv from the current FP64 Ruiz factors (allocated once).
 template <typename T> lp_status engine_factors(Handle* h);
+// (Re)builds the engine's warp-task schedules of K and K^T with the given
+// parameters (frees the previous ones).
+template <typename T> lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT);
+// Times the candidate warp-task schedules of K and K^T on the engine's scaled
+// values and keeps the fastest of each (once per engine; drops a captured loop
+// graph when a schedule changes).
+template <typename T> lp_status tune_engine(Handle* h);
+// Frees one allocation made by dev_alloc / dev_alloc_n.
+void dev_free(Handle* h, void* p);
 // solver.cu
 template <typename T>
 lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
@@ -349,9 +366,9 @@ lp_status run_grad(Handle* h, const lp_opts* o, int K_iters, int ckpt, const dou
 // Algorithm 7 (fishnet.cu): repopulation draws of P columns, and the run on
 // the prepared FP64 engine.
 int64_t fishnet_draws(int P);
-lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, int k_steps,
-                      const double* G, const double* Z_host, int64_t nZ, double* x0, double* y0,
-                      double* gaps_host, int32_t* rounds_out, int space);
+lp_status run_fishnet(Handle* h, int precision, double eta, double omega, double normK, int P,
+                      int k_steps, const double* G, const double* Z_host, int64_t nZ, double* x0,
+                      double* y0, double* gaps_host, int32_t* rounds_out, int space);
 lp_status run_unroll(Handle* h, const lp_opts* o, int K_iters, double* xK, double* yK, int space,
                      double* tau_sigma);
 // setup.cu

@@ -2,8 +2,11 @@
 // advanced together by fixed-step PDHG, so each product with K or K^T is a
 // sparse-times-dense product over a row-major n x P (m x P) point block instead
 // of P separate SpMVs; cull by duality gap and convex repopulation between
-// rounds.  FP64 throughout (the cull compares gaps, so the decision is taken in
-// the same precision as the FP64 oracle).
+// rounds.  T = double keeps the point blocks and products in FP64 (the cull
+// compares gaps, so its decisions are then taken as in the FP64 oracle);
+// T = float keeps them in FP32 (GB300's FP64 pipe makes the FP64 block products
+// arithmetic-bound: P fused multiply-adds per nonzero), with FP64 gap
+// reductions.
 //
 // Readings shared with the oracle: points x~_p = (||K~||_2 / sqrt(n)) g_p on the
 // scaled problem, Y^0 = K~ X^0, k fixed steps of Algorithm 1 per round with the
@@ -28,11 +31,11 @@ constexpr int kFGrid = 152 * 16;   // grid cap of the block-SpMM kernels (persis
 // major with P columns (a power of two, 1..64).  One warp per row: lane l serves
 // column l % P (and l + 32 when P = 64); for P < 32 the 32 / P lane groups take
 // every (32 / P)-th nonzero of each batch of 32 and are added by a fixed
-// butterfly.  Each gathered row of X is P contiguous doubles (coalesced).
-template <class Epi>
+// butterfly.  Each gathered row of X is P contiguous values (coalesced).
+template <typename T, class Epi>
 __global__ void __launch_bounds__(kFW * 32)
 k_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-       const double* __restrict__ val, int64_t rows, int P, const double* __restrict__ X, Epi epi)
+       const T* __restrict__ val, int64_t rows, int P, const T* __restrict__ X, Epi epi)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -43,18 +46,18 @@ k_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
     for (int64_t r = (int64_t)blockIdx.x * kFW + (threadIdx.x >> 5); r < rows;
          r += (int64_t)gridDim.x * kFW) {
         const int64_t s = rp[r], e = rp[r + 1];
-        double a0 = 0.0, a1 = 0.0;
+        T a0 = 0, a1 = 0;
         for (int64_t b = s; b < e; b += 32) {
             const int64_t k = b + lane;
             const int c = k < e ? ci[k] : 0;
-            const double v = k < e ? val[k] : 0.0;
+            const T v = k < e ? val[k] : T(0);
             const int cnt = e - b < 32 ? (int)(e - b) : 32;
 #pragma unroll 4
             for (int t0 = 0; t0 < cnt; t0 += G) {
                 const int t = t0 + g;   // <= 31; lanes past the row's end hold v = 0
                 const int ct = __shfl_sync(full, c, t);
-                const double vt = __shfl_sync(full, v, t);
-                const double* xr = X + (int64_t)ct * P;
+                const T vt = __shfl_sync(full, v, t);
+                const T* xr = X + (int64_t)ct * P;
                 a0 += vt * xr[p];
                 if (two) a1 += vt * xr[p + 32];
             }
@@ -67,23 +70,25 @@ k_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
     }
 }
 
+template <typename T>
 struct FStore {
-    double* out;
+    T* out;
     int P;
-    __device__ void row(int64_t r, int p, double v) const { out[r * P + p] = v; }
+    __device__ void row(int64_t r, int p, T v) const { out[r * P + p] = v; }
 };
 
 // x' = proj_X(x - tau (c - K^T y)) per column (Algorithm 1, theta = 1)
+template <typename T>
 struct FPrimal {
-    const double* X;
-    double* Xn;
-    const double *c, *l, *u;
-    double tau;
+    const T* X;
+    T* Xn;
+    const T *c, *l, *u;
+    T tau;
     int P;
-    __device__ void row(int64_t j, int p, double kty) const
+    __device__ void row(int64_t j, int p, T kty) const
     {
         const int64_t t = j * P + p;
-        double v = X[t] - tau * (c[j] - kty);
+        T v = X[t] - tau * (c[j] - kty);
         if (v < l[j]) v = l[j];
         if (v > u[j]) v = u[j];
         Xn[t] = v;
@@ -91,30 +96,32 @@ struct FPrimal {
 };
 
 // y' = proj_Y(y + sigma (q - (2 K x' - K x))); K x' replaces K x
+template <typename T>
 struct FDual {
-    const double* Y;
-    double* Yn;
-    double* KX;
-    const double* q;
+    const T* Y;
+    T* Yn;
+    T* KX;
+    const T* q;
     const uint8_t* sense;
-    double sigma;
+    T sigma;
     int P;
-    __device__ void row(int64_t i, int p, double kxn) const
+    __device__ void row(int64_t i, int p, T kxn) const
     {
         const int64_t t = i * P + p;
-        double v = Y[t] + sigma * (q[i] - (2.0 * kxn - KX[t]));
-        if (sense[i] && v < 0.0) v = 0.0;
+        T v = Y[t] + sigma * (q[i] - (T(2) * kxn - KX[t]));
+        if (sense[i] && v < T(0)) v = T(0);
         Yn[t] = v;
         KX[t] = kxn;
     }
 };
 
-__global__ void k_cast(int64_t n, int P, double rad, const double* G, double* X)
+template <typename T>
+__global__ void k_cast(int64_t n, int P, double rad, const double* G, T* X)
 {
     const int64_t total = n * P;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x)
-        X[t] = rad * G[t];
+        X[t] = (T)(rad * G[t]);
 }
 
 // Per-column sums over the rows of a point block, fixed order: thread t of a
@@ -141,33 +148,37 @@ __device__ void column_partials(const double (&v)[NQ], int P, double* part)
 }
 
 // c~^T x_p and l~^T lambda_p^+ + u~^T lambda_p^-, lambda_p = proj_Lambda(c~ - K~^T y_p)
+template <typename T>
 __global__ void __launch_bounds__(kGapNT)
-k_gap_cols(int64_t n, int P, const double* X, const double* KTY, const double* c,
-           const double* l, const double* u, double* part)
+k_gap_cols(int64_t n, int P, const T* X, const T* KTY, const T* c, const T* l, const T* u,
+           double* part)
 {
     const int p = threadIdx.x % P, per = kGapNT / P;
-    double v[2] = {0.0, 0.0};
+    T a[2] = {T(0), T(0)};
     for (int64_t j = (int64_t)blockIdx.x * per + threadIdx.x / P; j < n;
          j += (int64_t)gridDim.x * per) {
         const int64_t t = j * P + p;
-        const double cj = c[j], lj = l[j], uj = u[j];
-        v[0] += cj * X[t];
-        const double lam = proj_lambda(cj - KTY[t], isfinite(lj), isfinite(uj));
-        if (lam > 0.0) v[1] += lj * lam;
-        if (lam < 0.0) v[1] += uj * lam;
+        const T cj = c[j], lj = l[j], uj = u[j];
+        a[0] += cj * X[t];
+        const T lam = proj_lambda(cj - KTY[t], isfinite(lj), isfinite(uj));
+        if (lam > T(0)) a[1] += lj * lam;
+        if (lam < T(0)) a[1] += uj * lam;
     }
+    const double v[2] = {(double)a[0], (double)a[1]};
     column_partials<2>(v, P, part);
 }
 
 // q~^T y_p
+template <typename T>
 __global__ void __launch_bounds__(kGapNT)
-k_gap_rows(int64_t m, int P, const double* Y, const double* q, double* part)
+k_gap_rows(int64_t m, int P, const T* Y, const T* q, double* part)
 {
     const int p = threadIdx.x % P, per = kGapNT / P;
-    double v[1] = {0.0};
+    T a = T(0);
     for (int64_t i = (int64_t)blockIdx.x * per + threadIdx.x / P; i < m;
          i += (int64_t)gridDim.x * per)
-        v[0] += q[i] * Y[i * P + p];
+        a += q[i] * Y[i * P + p];
+    const double v[1] = {(double)a};
     column_partials<1>(v, P, part);
 }
 
@@ -186,31 +197,33 @@ __global__ void k_gap_final(int P, const double* partC, int nbC, const double* p
 
 // dst (rows x Pn) from src (rows x Po): columns t < keep copy src column
 // kept[t]; column t >= keep is sum_a W[(t - keep) * keep + a] * src column kept[a].
+template <typename T>
 __global__ void k_combine(int64_t rows, int Po, int Pn, int keep, const int* kept,
-                          const double* W, const double* src, double* dst)
+                          const double* W, const T* src, T* dst)
 {
     const int64_t total = rows * Pn;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / Pn;
         const int t = (int)(e - r * Pn);
-        const double* s = src + r * Po;
+        const T* s = src + r * Po;
         if (t < keep) {
             dst[e] = s[kept[t]];
         } else {
             const double* w = W + (size_t)(t - keep) * keep;
-            double v = 0.0;
-            for (int a = 0; a < keep; ++a) v += w[a] * s[kept[a]];
+            T v = T(0);
+            for (int a = 0; a < keep; ++a) v += (T)w[a] * s[kept[a]];
             dst[e] = v;
         }
     }
 }
 
-__global__ void k_unscale(int64_t count, const double* v, const double* f, double* out)
+template <typename T>
+__global__ void k_unscale(int64_t count, const T* v, const double* f, double* out)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
          t += (int64_t)gridDim.x * blockDim.x)
-        out[t] = f[t] * v[t];
+        out[t] = f[t] * (double)v[t];
 }
 
 int ew_blocks(int64_t count)
@@ -270,16 +283,20 @@ int64_t fishnet_draws(int P)
     return total;
 }
 
-lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, int k_steps,
-                      const double* G, const double* Z_host, int64_t nZ, double* x0, double* y0,
-                      double* gaps_host, int32_t* rounds_out, int space)
+namespace {
+
+template <typename T>
+lp_status fishnet_t(Handle* h, double eta, double omega, double normK, int P, int k_steps,
+                    const double* G, const double* Z_host, int64_t nZ, double* x0, double* y0,
+                    double* gaps_host, int32_t* rounds_out, int space)
 {
     const int64_t m = h->m, n = h->n;
-    const Engine<double>& E = h->e64;
+    const Engine<T>& E = engine_of<T>(h);
     cudaStream_t st = h->stream;
     if (fishnet_draws(P) > nZ) return LP_INVALID_ARGUMENT;
     Scratch S;
-    double *X, *Xn, *KTY, *Y, *Yn, *KX, *KX2, *Gd = nullptr, *gap, *W, *partC, *partR;
+    T *X, *Xn, *KTY, *Y, *Yn, *KX, *KX2;
+    double *Gd = nullptr, *gap, *W, *partC, *partR;
     int* kept_d;
     LP_TRY(S.get(&X, (size_t)n * P));
     LP_TRY(S.get(&Xn, (size_t)n * P));
@@ -300,13 +317,12 @@ lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, 
                                     cudaMemcpyHostToDevice, st));
         G = Gd;
     }
-    const double tau = eta / omega, sigma = eta * omega;
+    const T tau = (T)(eta / omega), sigma = (T)(eta * omega);
     // spectral casting, Y^0 = K~ X^0 (also the first K x)
-    k_cast<<<ew_blocks(n * P), 256, 0, st>>>(n, P, normK / std::sqrt((double)n), G, X);
-    k_spmm<FStore><<<spmm_blocks(m), kFW * 32, 0, st>>>(h->rp, h->ci, E.val, m, P, X,
-                                                          FStore{Y, P});
-    LP_CUDA_TRY(cudaMemcpyAsync(KX, Y, sizeof(double) * (size_t)m * P, cudaMemcpyDeviceToDevice,
-                                st));
+    k_cast<T><<<ew_blocks(n * P), 256, 0, st>>>(n, P, normK / std::sqrt((double)n), G, X);
+    k_spmm<T, FStore<T>><<<spmm_blocks(m), kFW * 32, 0, st>>>(h->rp, h->ci, E.val, m, P, X,
+                                                                FStore<T>{Y, P});
+    LP_CUDA_TRY(cudaMemcpyAsync(KX, Y, sizeof(T) * (size_t)m * P, cudaMemcpyDeviceToDevice, st));
     h->launches += 2;
     LP_CUDA_TRY(cudaGetLastError());
 
@@ -317,19 +333,20 @@ lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, 
     while (cols > 1) {
         const int j_top = cols;
         for (int t = 0; t < k_steps; ++t) {
-            k_spmm<FPrimal><<<spmm_blocks(n), kFW * 32, 0, st>>>(
-                h->trp, h->tci, E.tval, n, cols, Y, FPrimal{X, Xn, E.c, E.l, E.u, tau, cols});
-            k_spmm<FDual><<<spmm_blocks(m), kFW * 32, 0, st>>>(
-                h->rp, h->ci, E.val, m, cols, Xn, FDual{Y, Yn, KX, E.q, h->sense, sigma, cols});
+            k_spmm<T, FPrimal<T>><<<spmm_blocks(n), kFW * 32, 0, st>>>(
+                h->trp, h->tci, E.tval, n, cols, Y, FPrimal<T>{X, Xn, E.c, E.l, E.u, tau, cols});
+            k_spmm<T, FDual<T>><<<spmm_blocks(m), kFW * 32, 0, st>>>(
+                h->rp, h->ci, E.val, m, cols, Xn,
+                FDual<T>{Y, Yn, KX, E.q, h->sense, sigma, cols});
             std::swap(X, Xn);
             std::swap(Y, Yn);
             h->launches += 2;
         }
         // |duality gap| of every column
-        k_spmm<FStore><<<spmm_blocks(n), kFW * 32, 0, st>>>(h->trp, h->tci, E.tval, n, cols, Y,
-                                                              FStore{KTY, cols});
-        k_gap_cols<<<nbC, kGapNT, 0, st>>>(n, cols, X, KTY, E.c, E.l, E.u, partC);
-        k_gap_rows<<<nbR, kGapNT, 0, st>>>(m, cols, Y, E.q, partR);
+        k_spmm<T, FStore<T>><<<spmm_blocks(n), kFW * 32, 0, st>>>(h->trp, h->tci, E.tval, n,
+                                                                    cols, Y, FStore<T>{KTY, cols});
+        k_gap_cols<T><<<nbC, kGapNT, 0, st>>>(n, cols, X, KTY, E.c, E.l, E.u, partC);
+        k_gap_rows<T><<<nbR, kGapNT, 0, st>>>(m, cols, Y, E.q, partR);
         k_gap_final<<<1, 64, 0, st>>>(cols, partC, nbC, partR, nbR, gap);
         h->launches += 4;
         LP_CUDA_TRY(cudaGetLastError());
@@ -365,9 +382,10 @@ lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, 
         }
         LP_CUDA_TRY(cudaMemcpyAsync(kept_d, kept.data(), sizeof(int) * keep,
                                     cudaMemcpyHostToDevice, st));
-        k_combine<<<ew_blocks(n * ncols), 256, 0, st>>>(n, cols, ncols, keep, kept_d, W, X, Xn);
-        k_combine<<<ew_blocks(m * ncols), 256, 0, st>>>(m, cols, ncols, keep, kept_d, W, Y, Yn);
-        k_combine<<<ew_blocks(m * ncols), 256, 0, st>>>(m, cols, ncols, keep, kept_d, W, KX, KX2);
+        k_combine<T><<<ew_blocks(n * ncols), 256, 0, st>>>(n, cols, ncols, keep, kept_d, W, X, Xn);
+        k_combine<T><<<ew_blocks(m * ncols), 256, 0, st>>>(m, cols, ncols, keep, kept_d, W, Y, Yn);
+        k_combine<T><<<ew_blocks(m * ncols), 256, 0, st>>>(m, cols, ncols, keep, kept_d, W, KX,
+                                                           KX2);
         h->launches += 3;
         LP_CUDA_TRY(cudaGetLastError());
         std::swap(X, Xn);
@@ -386,8 +404,8 @@ lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, 
         xo = xd;
         yo = yd;
     }
-    k_unscale<<<ew_blocks(n), 256, 0, st>>>(n, X, h->C, xo);
-    k_unscale<<<ew_blocks(m), 256, 0, st>>>(m, Y, h->R, yo);
+    k_unscale<T><<<ew_blocks(n), 256, 0, st>>>(n, X, h->C, xo);
+    k_unscale<T><<<ew_blocks(m), 256, 0, st>>>(m, Y, h->R, yo);
     h->launches += 2;
     LP_CUDA_TRY(cudaGetLastError());
     if (space == LP_MEM_HOST) {
@@ -397,6 +415,19 @@ lp_status run_fishnet(Handle* h, double eta, double omega, double normK, int P, 
     LP_CUDA_TRY(cudaStreamSynchronize(st));
     if (rounds_out) *rounds_out = round;
     return LP_OK;
+}
+
+}  // namespace
+
+lp_status run_fishnet(Handle* h, int precision, double eta, double omega, double normK, int P,
+                      int k_steps, const double* G, const double* Z_host, int64_t nZ, double* x0,
+                      double* y0, double* gaps_host, int32_t* rounds_out, int space)
+{
+    if (precision == LP_PREC_MIXED)
+        return fishnet_t<float>(h, eta, omega, normK, P, k_steps, G, Z_host, nZ, x0, y0,
+                                gaps_host, rounds_out, space);
+    return fishnet_t<double>(h, eta, omega, normK, P, k_steps, G, Z_host, nZ, x0, y0, gaps_host,
+                             rounds_out, space);
 }
 
 }  // namespace pdhg

@@ -25,6 +25,17 @@ lp_status dev_alloc(Handle* h, void** p, size_t bytes)
     return LP_OK;
 }
 
+void dev_free(Handle* h, void* p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < h->allocs.size(); ++i)
+        if (h->allocs[i].p == p) {
+            cudaFree(p);
+            h->allocs.erase(h->allocs.begin() + (std::ptrdiff_t)i);
+            return;
+        }
+}
+
 std::vector<int32_t> make_row_blocks(const int64_t* rp, int64_t rows, int cap, int max_rows)
 {
     std::vector<int32_t> b;
@@ -593,37 +604,56 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
 
 // Allocation, schedules and (for T = float) the FP32 casts of the scaled data.
 template <typename T>
+lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
+{
+    Engine<T>& E = engine_of<T>(h);
+    std::vector<int32_t> bk = make_row_blocks(h->h_rp.data(), h->m, sK.cap, sK.max_rows);
+    std::vector<int32_t> bt = make_row_blocks(h->h_trp.data(), h->n, sT.cap, sT.max_rows);
+    std::vector<int64_t> nk(bk.size()), nt(bt.size());
+    for (size_t t = 0; t < bk.size(); ++t) nk[t] = h->h_rp[(size_t)bk[t]];
+    for (size_t t = 0; t < bt.size(); ++t) nt[t] = h->h_trp[(size_t)bt[t]];
+    int sms = 0;
+    LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    dev_free(h, E.brow);
+    dev_free(h, E.bcol);
+    dev_free(h, E.bnzK);
+    dev_free(h, E.bnzT);
+    E.brow = E.bcol = nullptr;
+    E.bnzK = E.bnzT = nullptr;
+    LP_TRY(dev_alloc_n(h, &E.brow, bk.size()));
+    LP_TRY(dev_alloc_n(h, &E.bcol, bt.size()));
+    LP_TRY(dev_alloc_n(h, &E.bnzK, nk.size()));
+    LP_TRY(dev_alloc_n(h, &E.bnzT, nt.size()));
+    LP_CUDA_TRY(cudaMemcpyAsync(E.brow, bk.data(), bk.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    LP_CUDA_TRY(cudaMemcpyAsync(E.bcol, bt.data(), bt.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    LP_CUDA_TRY(cudaMemcpyAsync(E.bnzK, nk.data(), nk.size() * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    LP_CUDA_TRY(cudaMemcpyAsync(E.bnzT, nt.data(), nt.size() * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    LP_CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
+    E.nblk = (int)bk.size() - 1;
+    E.ntblk = (int)bt.size() - 1;
+    E.gK = spmv_grid(E.nblk, sms);
+    E.gT = spmv_grid(E.ntblk, sms);
+    E.schedK = sK;
+    E.schedT = sT;
+    return LP_OK;
+}
+
+template lp_status engine_schedule<double>(Handle*, SchedParams, SchedParams);
+template lp_status engine_schedule<float>(Handle*, SchedParams, SchedParams);
+
+template <typename T>
 lp_status setup_engine(Handle* h, const lp_opts* o)
 {
     (void)o;
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     Engine<T>& E = engine_of<T>(h);
     if (!E.ready) {
-        const int cap = cap_w<T>();
-        std::vector<int32_t> bk = make_row_blocks(h->h_rp.data(), m, cap, kTaskRows);
-        std::vector<int32_t> bt = make_row_blocks(h->h_trp.data(), n, cap, kTaskRows);
-        E.nblk = (int)bk.size() - 1;
-        E.ntblk = (int)bt.size() - 1;
-        int sms = 0;
-        LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-        E.gK = spmv_grid(E.nblk, sms);
-        E.gT = spmv_grid(E.ntblk, sms);
-        LP_TRY(dev_alloc_n(h, &E.brow, bk.size()));
-        LP_TRY(dev_alloc_n(h, &E.bcol, bt.size()));
-        LP_CUDA_TRY(cudaMemcpyAsync(E.brow, bk.data(), bk.size() * sizeof(int32_t),
-                                    cudaMemcpyHostToDevice, h->stream));
-        LP_CUDA_TRY(cudaMemcpyAsync(E.bcol, bt.data(), bt.size() * sizeof(int32_t),
-                                    cudaMemcpyHostToDevice, h->stream));
-        std::vector<int64_t> nk(bk.size()), nt(bt.size());
-        for (size_t t = 0; t < bk.size(); ++t) nk[t] = h->h_rp[(size_t)bk[t]];
-        for (size_t t = 0; t < bt.size(); ++t) nt[t] = h->h_trp[(size_t)bt[t]];
-        LP_TRY(dev_alloc_n(h, &E.bnzK, nk.size()));
-        LP_TRY(dev_alloc_n(h, &E.bnzT, nt.size()));
-        LP_CUDA_TRY(cudaMemcpyAsync(E.bnzK, nk.data(), nk.size() * sizeof(int64_t),
-                                    cudaMemcpyHostToDevice, h->stream));
-        LP_CUDA_TRY(cudaMemcpyAsync(E.bnzT, nt.data(), nt.size() * sizeof(int64_t),
-                                    cudaMemcpyHostToDevice, h->stream));
-        LP_CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
+        LP_TRY(engine_schedule<T>(h, SchedParams{cap_w<T>(), kTaskRows},
+                                  SchedParams{cap_w<T>(), kTaskRows}));
         LP_TRY(dev_alloc_n(h, &E.val, pad8(nnz)));
         LP_TRY(dev_alloc_n(h, &E.tval, pad8(nnz)));
         LP_CUDA_TRY(cudaMemsetAsync(E.val, 0, pad8(nnz) * sizeof(T), h->stream));
@@ -633,8 +663,11 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         for (T** p : vn) LP_TRY(dev_alloc_n(h, p, (size_t)n));
         T** vm[] = {&E.q, &E.Y[0], &E.Y[1], &E.KX[0], &E.KX[1], &E.YS, &E.YA, &E.KXA, &E.YANC};
         for (T** p : vm) LP_TRY(dev_alloc_n(h, p, (size_t)m));
-        LP_TRY(dev_alloc_n(h, &E.partD, (size_t)E.gK + 8));
-        LP_TRY(dev_alloc_n(h, &E.partT, 2 * (size_t)E.gT + 8));
+        int sms = 0;
+        LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        const size_t gmax = (size_t)spmv_grid(1 << 30, sms);
+        LP_TRY(dev_alloc_n(h, &E.partD, gmax + 8));
+        LP_TRY(dev_alloc_n(h, &E.partT, 2 * gmax + 8));
         LP_TRY(dev_alloc_n(h, &E.partR, kRowQ * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.partC, kColQ * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.ctrl, 1));

@@ -300,18 +300,28 @@ k_check_ctrl(Ctrl* ctrl, const double* partR, const double* partC, int nparts,
              lp_trace_rec* trace)
 {
     if (!ctrl->want_check) return;
-    double r[kRowQ], cc[kColQ];
-    const int nr = infeas_active(*ctrl) ? kRowSums : 8, nc = infeas_active(*ctrl) ? kColSums : 10;
-    for (int q = 0; q < kRowQ; ++q) r[q] = 0.0;
-    for (int q = 0; q < kColQ; ++q) cc[q] = 0.0;
-    for (int q = 0; q < nr; ++q) r[q] = block_sum_array<kCtlNT>(partR + (size_t)q * nparts, nparts);
-    for (int q = 0; q < nc; ++q) cc[q] = block_sum_array<kCtlNT>(partC + (size_t)q * nparts, nparts);
-    if (nr > 8) {
-        for (int q = kRowSums; q < kRowQ; ++q)
-            r[q] = block_max_array<kCtlNT>(partR + (size_t)q * nparts, nparts);
-        for (int q = kColSums; q < kColQ; ++q)
-            cc[q] = block_max_array<kCtlNT>(partC + (size_t)q * nparts, nparts);
+    // one warp per reduced quantity (fixed order: lane-strided sums, then the
+    // warp's tree); the Algorithm 6 terms only when the check runs it
+    __shared__ double red[kRowQ + kColQ];
+    const bool inf = infeas_active(*ctrl);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < kRowQ + kColQ; q += kCtlNT / 32) {
+        const bool row_side = q < kRowQ;
+        const int k = row_side ? q : q - kRowQ;
+        const bool is_max = row_side ? k >= kRowSums : k >= kColSums;
+        const bool used = inf || (row_side ? k < 8 : k < 10);
+        const double* part = (row_side ? partR : partC) + (size_t)k * nparts;
+        double v = 0.0;
+        if (used)
+            for (int i = lane; i < nparts; i += 32)
+                v = is_max ? fmax(v, __ldcg(part + i)) : v + __ldcg(part + i);
+        v = is_max ? warp_max(v) : warp_sum(v);
+        if (lane == 0) red[q] = v;
     }
+    __syncthreads();
+    double r[kRowQ], cc[kColQ];
+    for (int q = 0; q < kRowQ; ++q) r[q] = red[q];
+    for (int q = 0; q < kColQ; ++q) cc[q] = red[kRowQ + q];
     if (threadIdx.x != 0) return;
     check_decide(ctrl, r, cc, trace);
 }
@@ -573,6 +583,7 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     LP_CUDA_TRY((spmv_prepare<T, EpiDual<T>>()));
     LP_CUDA_TRY((spmv_prepare<T, EpiPrimalT<T>>()));
     LP_TRY(engine_factors<T>(h));
+    if (o->autotune) LP_TRY(tune_engine<T>(h));
     // warm start from the caller (unscaled) must be on the device
     const double* dwx = nullptr;
     const double* dwy = nullptr;

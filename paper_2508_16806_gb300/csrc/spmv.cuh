@@ -32,6 +32,8 @@
 // PDHG_SINGLE_LP_TASK_HOOKS supplies the no-op task hooks of a single LP.
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace pdhg {
@@ -514,7 +516,7 @@ struct EpiStore {
     __device__ void row(int r, T v, const Pre&, Acc& a) const {
         if (scale) v = (T)((double)v * *scale);
         out[r] = v;
-        a.s2 += (double)v * (double)v;
+        if (part) a.s2 += (double)v * (double)v;
     }
     __device__ void finish(Acc& a) const {
         if (part) {
@@ -541,5 +543,18 @@ inline int spmv_grid(int ntasks, int num_sms)
 // holds <= cap nonzeros and <= max_rows rows; a row longer than cap gets a task
 // of its own.  Returns the task boundaries (ntasks + 1 entries).
 std::vector<int32_t> make_row_blocks(const int64_t* rp, int64_t rows, int cap, int max_rows);
+
+// Schedule autotuner (tune.cu).  Candidates: cap in {CAPW, CAPW / 2} nonzeros
+// and max_rows in {kTaskRows, 32, 16} rows per task.  build(cap, max_rows)
+// returns the task boundaries over all rows of one orientation (h_rp: its host
+// row pointers).  Each candidate's SpMV (store epilogue, x -> out) is launched
+// once to warm up and timed over three launches with CUDA events on `st`; the
+// fastest is returned in *best (and its mean milliseconds in *best_ms).
+using RowBlockBuilder = std::function<std::vector<int32_t>(int cap, int max_rows)>;
+template <typename T>
+lp_status tune_schedule(int sms, cudaStream_t st, const RowBlockBuilder& build,
+                        const int64_t* h_rp, const int64_t* rp, const int32_t* ci, const T* val,
+                        const T* x, T* out, int64_t x_len, int* err, SchedParams* best,
+                        float* best_ms);
 
 }  // namespace pdhg

@@ -52,7 +52,8 @@ class LpOpts(C.Structure):
                 ("omega0", C.c_double), ("eta0", C.c_double),
                 ("warm_memory_space", C.c_int32), ("loop_mode", C.c_int32),
                 ("infeas_detect", C.c_int32), ("reserved_opts", C.c_int32),
-                ("infeas_tol", C.c_double)]
+                ("infeas_tol", C.c_double), ("autotune", C.c_int32),
+                ("reserved_opts2", C.c_int32)]
 
 
 TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",

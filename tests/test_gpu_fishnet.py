@@ -53,6 +53,23 @@ def test_fishnet_matches_oracle(L, oracle_mod, name):
     assert rel(gx, ox) <= 1e-9 and rel(gy, oy) <= 1e-9
 
 
+@pytest.mark.parametrize("name", ["lp200x400_P32_k20", "ragged_P8_k10", "powerlaw_P64_k5"])
+def test_fishnet_fp32_blocks_track_oracle(L, oracle_mod, name):
+    """FP32 point blocks and products (FP64 gap reductions): the same rounds and
+    survivors as the FP64 oracle on these draws, gaps and the surviving point
+    within FP32 rounding of a fixed-step trajectory."""
+    lp, P, k = CASES[name]
+    rng = np.random.default_rng(sum(map(ord, name)))
+    G = rng.standard_normal((lp.n, P))
+    Z = rng.standard_normal(max(oracle_mod.fishnet_draws(P), 1))
+    ox, oy, og, orounds = oracle_mod.fishnet(lp, P, k, G, Z)
+    gx, gy, gg, grounds = L.Problem(lp).fishnet(P, k, G, Z, precision=L.LP_PREC_MIXED)
+    assert grounds == orounds
+    fin = np.isfinite(og)
+    np.testing.assert_allclose(gg[fin], og[fin], rtol=1e-3, atol=1e-6)
+    assert rel(gx, ox) <= 1e-3 and rel(gy, oy) <= 1e-3
+
+
 def test_fishnet_device_inputs(L):
     torch = pytest.importorskip("torch")
     lp, P, k = CASES["ragged_P8_k10"]

@@ -67,3 +67,68 @@ def test_batch_512_mixed_to_1e4(L, oracle_mod):
         x, y, info = out[k]
         kk = oracle_mod.kkt(lps[k], x, y)
         assert max(kk["rel_gap"], kk["rel_pres"], kk["rel_dres"]) <= 1.5e-4
+
+
+def test_powerlaw_1Mx2M_mixed_to_1e6(L, oracle_mod):
+    """C1 to the tighter tolerance: the FP32 phase hands over at 1e-5 and the
+    FP64 polish finishes; the oracle's FP64 evaluation confirms 1e-6."""
+    lp = synth.power_law_lp()
+    x, y, info, k = _check(L, oracle_mod, lp, 1e-6, 900)
+    assert info["fp64_iters"] > 0 and info["precision_used"] == L.LP_PREC_FP64
+    f = float(lp.c @ x)
+    assert abs(f - lp.f_star) / (1 + abs(lp.f_star)) < 1e-5
+
+
+def test_powerlaw_1Mx2M_fp64_to_1e4(L, oracle_mod):
+    """The plain FP64 path on C1 (the comparison line of the benchmark)."""
+    lp = synth.power_law_lp()
+    prob = L.Problem(lp)
+    x, y, info, _ = prob.solve(tol=1e-4, precision=L.LP_PREC_FP64, time_limit_s=600)
+    prob.close()
+    assert info["status"] == L.LP_OPTIMAL, info
+    k = oracle_mod.kkt(lp, x, y)
+    assert max(k["rel_gap"], k["rel_pres"], k["rel_dres"]) <= 1e-4 * (1 + 1e-6)
+    assert abs(float(lp.c @ x) - lp.f_star) / (1 + abs(lp.f_star)) < 1e-3
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) /
+                 max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def test_adjoint_100kx200k_K500(L, oracle_mod):
+    """C4 at full size: 500 unrolled fixed-step iterations, checkpoints every
+    50.  The FP64 adjoint equals the oracle's FP64 unrolled adjoint; the FP32
+    adjoint's distance to it is bounded (and printed)."""
+    from paper_2508_16806_gb300 import autograd as AG
+    lp, xt = synth.adjoint_lp()
+    prob = L.Problem(lp)
+    x64, _, (tau, sigma) = AG.unroll(prob, 500)
+    g = 2.0 * (x64 - xt)
+    d64 = AG.grad(prob, 500, 50, g)
+    oc, oq, ov = oracle_mod.unrolled_adjoint(lp, tau, sigma, 500, g)
+    for a, b in zip(d64[:3], (oc, oq, ov)):
+        assert _rel(a, b) < 1e-9, _rel(a, b)
+    d32 = AG.grad(prob, 500, 50, g, precision=L.LP_PREC_MIXED)
+    errs = [_rel(a, b) for a, b in zip(d32[:3], d64[:3])]
+    print("FP32 adjoint relative error (dc, dq, dvals):", errs)
+    assert all(np.all(np.isfinite(a)) for a in d32[:3])
+    assert max(errs) < 1e-2, errs
+
+
+def test_adjoint_batch_of_64_at_m5000(L, oracle_mod):
+    """C4's batch form: 64 instances at m = 5,000 (K = 500, checkpoints every
+    50, FP32); two of them are compared with the FP64 adjoint."""
+    from paper_2508_16806_gb300 import autograd as AG
+    t = time.time()
+    for k in range(64):
+        lp, xt = synth.adjoint_lp(5000, 10000, 20, seed=20250820 + k)
+        prob = L.Problem(lp)
+        x32, _, _ = AG.unroll(prob, 500, precision=L.LP_PREC_MIXED)
+        d32 = AG.grad(prob, 500, 50, 2.0 * (x32 - xt), precision=L.LP_PREC_MIXED)
+        assert all(np.all(np.isfinite(a)) for a in d32[:3])
+        if k < 2:
+            d64 = AG.grad(prob, 500, 50, 2.0 * (x32 - xt))
+            assert max(_rel(a, b) for a, b in zip(d32[:3], d64[:3])) < 1e-2
+        prob.close()
+    print("64 adjoints at m=5000:", time.time() - t, "s")
