@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fishnet", action="store_true",
                    help="skip the Algorithm 7 warm-start measurement (extra key)")
+    p.add_argument("--fp64-profile", action="store_true",
+                   help="with --kernel-profile: also time the FP64 step kernels")
     p.add_argument("--fishnet-profile", action="store_true",
                    help="one lp_fishnet call on the workload (32 points, 2 steps per round), "
                         "for kernel profilers; prints its time")
@@ -71,7 +73,11 @@ def kernel_profile(args):
     prob = L.Problem(lp, device_copy=True, stream=stream)
     prob.solve(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=64)
     ms, by = prob.profile_step(L.LP_PREC_MIXED, reps=3)
-    print(json.dumps({"kernel_profile": desc, "ms": ms, "bytes": by}), flush=True)
+    line = {"kernel_profile": desc, "ms": ms, "bytes": by}
+    if args.fp64_profile:
+        prob.solve(tol=args.tol, precision=L.LP_PREC_FP64, max_iters=64)
+        line["ms_fp64"], line["bytes_fp64"] = prob.profile_step(L.LP_PREC_FP64, reps=3)
+    print(json.dumps(line), flush=True)
     prob.close()
 
 
@@ -108,7 +114,7 @@ def run_batch(args):
     # the same 512 shifted by rank so that every rank has a full batch)
     lps = all_lps if world == 1 else synth.batch_lps(seed=20250819 + 512 * rank)
     batch = L.Batch(lps)
-    opts = dict(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=2_000_000)
+    opts = dict(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=2_000_000, autotune=1)
     for _ in range(args.warmup):
         batch.solve(**opts)
     torch.cuda.synchronize()

@@ -117,10 +117,12 @@ typedef struct {
     int32_t reserved_opts;       /* must be 0 */
     double infeas_tol;           /* tolerance of Algorithm 6, applied to the differences
                                     normalised to unit length (default 1e-6) */
-    int32_t autotune;            /* 1 (default): at the first solve of each precision, time the
-                                    candidate warp-task schedules of K and K^T (nonzeros and
-                                    rows per task) on the device and keep the fastest of each;
-                                    0: the largest tasks (the compiled defaults) */
+    int32_t autotune;            /* 1: at the first solve of each precision, time the candidate
+                                    warp-task schedules of K and K^T (nonzeros and rows per task)
+                                    on the device and keep the fastest of each (a candidate must
+                                    beat the default by 3 %); the summation order, and so the
+                                    last bits of the result, then depends on that timing.
+                                    0 (default): the largest tasks (the compiled defaults) */
     int32_t reserved_opts2;      /* must be 0 */
 } lp_opts;
 

@@ -55,6 +55,8 @@ struct BatchSched {
     int32_t *taskK = nullptr, *taskT = nullptr;      // task -> first row (K) / column (K^T)
     int64_t *nzK = nullptr, *nzT = nullptr;          // task -> first nonzero
     int32_t *lpK = nullptr, *lpT = nullptr;          // task -> LP
+    int32_t *wbegK = nullptr, *permK = nullptr;      // per-warp task lists (K)
+    int32_t *wbegT = nullptr, *permT = nullptr;      // per-warp task lists (K^T)
     int32_t *t0K = nullptr, *t0T = nullptr;          // LP -> first task [B + 1]
     double *partK = nullptr, *partT = nullptr;       // per-task step partials [1 | 2][nt]
     double *partR = nullptr, *partC = nullptr;       // per-task check partials [kRowQ | kColQ][nt]
@@ -665,7 +667,8 @@ lp_status build_sched(BatchHandle* bh, SchedParams pK, SchedParams pT)
     if (S.ready) {
         for (void* p : {(void*)S.taskK, (void*)S.taskT, (void*)S.lpK, (void*)S.lpT,
                         (void*)S.t0K, (void*)S.t0T, (void*)S.nzK, (void*)S.nzT, (void*)S.partK,
-                        (void*)S.partT, (void*)S.partR, (void*)S.partC})
+                        (void*)S.partT, (void*)S.partR, (void*)S.partC, (void*)S.wbegK,
+                        (void*)S.permK, (void*)S.wbegT, (void*)S.permT})
             dev_free(h, p);
     }
     std::vector<int32_t> tK, tT, lK, lT, k0(B + 1), c0(B + 1);
@@ -700,6 +703,9 @@ lp_status build_sched(BatchHandle* bh, SchedParams pK, SchedParams pT)
     LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     S.gK = spmv_grid(S.ntK, sms);
     S.gT = spmv_grid(S.ntT, sms);
+    std::vector<int32_t> wk, pk, wt, pt;
+    assign_tasks(nK, pK.cap, S.gK * kTaskWarps, wk, pk);
+    assign_tasks(nT, pT.cap, S.gT * kTaskWarps, wt, pt);
     auto up32 = [&](int32_t** d, const std::vector<int32_t>& v) -> lp_status {
         LP_TRY(dev_alloc_n(h, d, v.size()));
         LP_CUDA_TRY(cudaMemcpyAsync(*d, v.data(), v.size() * 4, cudaMemcpyHostToDevice, h->stream));
@@ -718,6 +724,10 @@ lp_status build_sched(BatchHandle* bh, SchedParams pK, SchedParams pT)
     LP_TRY(up32(&S.t0T, c0));
     LP_TRY(up64(&S.nzK, nK));
     LP_TRY(up64(&S.nzT, nT));
+    LP_TRY(up32(&S.wbegK, wk));
+    LP_TRY(up32(&S.permK, pk));
+    LP_TRY(up32(&S.wbegT, wt));
+    LP_TRY(up32(&S.permT, pt));
     LP_TRY(dev_alloc_n(h, &S.partK, (size_t)S.ntK + 8));
     LP_TRY(dev_alloc_n(h, &S.partT, 2 * (size_t)S.ntT + 8));
     LP_TRY(dev_alloc_n(h, &S.partR, kRowQ * (size_t)S.ntK + 8));
@@ -858,9 +868,9 @@ lp_status batch_scale(BatchHandle* bh, const lp_opts* o, double* normK_dev)
     k_fill_i32<<<grid_n(B, 256, 4096), 256, 0, st>>>(reinterpret_cast<int32_t*>(bh->go), B, 1);
     for (int it = 0; it < o->power_iters; ++it) {
         EpiBStore<double> e1{b, t, nullptr, S.lpK, bh->go, nullptr};
-        launch_spmv<double>(S.gK, st, S.taskK, S.nzK, S.ntK, h->rp, h->ci, E.val, h->dev_err, n, e1);
+        launch_spmv<double>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permK, h->rp, h->ci, E.val, h->dev_err, n, e1);
         EpiBStore<double> e2{t, b, S.partT, S.lpT, bh->go, nullptr};
-        launch_spmv<double>(S.gT, st, S.taskT, S.nzT, S.ntT, h->trp, h->tci, E.tval, h->dev_err, m,
+        launch_spmv<double>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permT, h->trp, h->tci, E.tval, h->dev_err, m,
                             e2);
         kb_pow_norm<<<(B + kBW - 1) / kBW, kBW * 32, 0, st>>>(B, S.t0T, S.partT, nb, bh->go,
                                                               nullptr);
@@ -868,7 +878,7 @@ lp_status batch_scale(BatchHandle* bh, const lp_opts* o, double* normK_dev)
         h->launches += 4;
     }
     EpiBStore<double> e3{b, t, S.partK, S.lpK, nullptr, nullptr};
-    launch_spmv<double>(S.gK, st, S.taskK, S.nzK, S.ntK, h->rp, h->ci, E.val, h->dev_err, n, e3);
+    launch_spmv<double>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permK, h->rp, h->ci, E.val, h->dev_err, n, e3);
     kb_pow_norm<<<(B + kBW - 1) / kBW, kBW * 32, 0, st>>>(B, S.t0K, S.partK, nullptr, bh->go,
                                                           normK_dev);
     h->launches += 2;
@@ -886,10 +896,10 @@ void b_launch_attempt(BatchHandle* bh, cudaStream_t st)
                                                 E.KTY[1], E.c, E.l, E.u, E.XS, h->n);
     EpiBDual<T> ed{bh->ctrl, S.lpK, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS,
                    E.q, h->sense, S.partK};
-    launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, h->rp, h->ci, E.val, h->dev_err, h->n, ed);
+    launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed);
     EpiBPrimalT<T> et{bh->ctrl, S.lpT, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1],
                       S.partT, S.ntT};
-    launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
+    launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
     kb_step_ctrl<<<(bh->meta.B + kBW - 1) / kBW, kBW * 32, 0, st>>>(
         bh->ctrl, bh->meta.B, S.t0K, S.t0T, S.partK, S.partT, S.ntT);
 }
@@ -907,9 +917,9 @@ void b_launch_check(BatchHandle* bh, cudaStream_t st, cudaGraphConditionalHandle
                                                      E.X[0], E.X[1], E.Y[0], E.Y[1], E.XS, E.YS,
                                                      E.XA, E.YA, E.l, E.u, h->sense, n, m);
     EpiBStore<T> e1{E.XA, E.KXA, nullptr, S.lpK, nullptr, bh->ctrl};
-    launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, h->rp, h->ci, E.val, h->dev_err, n, e1);
+    launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permK, h->rp, h->ci, E.val, h->dev_err, n, e1);
     EpiBStore<T> e2{E.YA, E.KTYA, nullptr, S.lpT, nullptr, bh->ctrl};
-    launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, h->trp, h->tci, E.tval, h->dev_err, m, e2);
+    launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permT, h->trp, h->tci, E.tval, h->dev_err, m, e2);
     kb_check_rows<T><<<(S.ntK + 7) / 8, kEW, 0, st>>>(bh->ctrl, S.taskK, S.lpK, S.ntK, E.Y[0],
                                                        E.Y[1], E.KX[0], E.KX[1], E.YA, E.KXA,
                                                        E.YANC, E.q, h->sense, E.Rt, E.Rinv, S.partR);
@@ -1048,9 +1058,9 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
     BatchSched<T>& S = sched_of<T>(bh);
     {
         EpiBStore<T> e1{E.X[0], E.KX[0], nullptr, S.lpK, nullptr, nullptr};
-        launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, h->rp, h->ci, E.val, h->dev_err, n, e1);
+        launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permK, h->rp, h->ci, E.val, h->dev_err, n, e1);
         EpiBStore<T> e2{E.Y[0], E.KTY[0], nullptr, S.lpT, nullptr, nullptr};
-        launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, h->trp, h->tci, E.tval, h->dev_err, m, e2);
+        launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permT, h->trp, h->tci, E.tval, h->dev_err, m, e2);
     }
     b_launch_check<T>(bh, st, cudaGraphConditionalHandle{}, 0, 0);
     h->launches += 9 + 3 + 4;

@@ -95,7 +95,7 @@ void lp_opts_default(lp_opts* o)
     o->loop_mode = 0;
     o->infeas_detect = 1;
     o->infeas_tol = 1e-6;
-    o->autotune = 1;
+    o->autotune = 0;
 }
 
 const char* lp_status_string(lp_status s)

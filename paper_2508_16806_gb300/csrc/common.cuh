@@ -95,6 +95,8 @@ struct Engine {
     int32_t* brow = nullptr;   int nblk = 0;    // K rows: task boundaries, task count
     int32_t* bcol = nullptr;   int ntblk = 0;   // K^T rows
     int64_t* bnzK = nullptr;   int64_t* bnzT = nullptr;   // first nonzero of each task
+    int32_t* wbegK = nullptr;  int32_t* permK = nullptr;  // per-warp task lists (K)
+    int32_t* wbegT = nullptr;  int32_t* permT = nullptr;  // per-warp task lists (K^T)
     int gK = 0, gT = 0;                         // blocks of the K and K^T SpMV launches
     SchedParams schedK, schedT;                 // parameters of the two schedules
     bool tuned = false;                         // schedules chosen by the autotuner

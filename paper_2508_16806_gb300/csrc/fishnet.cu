@@ -32,6 +32,37 @@ constexpr int kFGrid = 152 * 16;   // grid cap of the block-SpMM kernels (persis
 // column l % P (and l + 32 when P = 64); for P < 32 the 32 / P lane groups take
 // every (32 / P)-th nonzero of each batch of 32 and are added by a fixed
 // butterfly.  Each gathered row of X is P contiguous values (coalesced).
+// Rows with more nonzeros than this go to k_spmm_long (a block per row), so that
+// no single warp walks a power-law row of thousands of nonzeros alone.
+constexpr int64_t kLongRow = 32 * kFW;
+
+// Accumulates the batches b0, b0 + stride, ... (32 nonzeros each) of row [s, e)
+// into a0 (and a1 for P = 64); every lane of the warp calls it.
+template <typename T>
+__device__ __forceinline__ void spmm_row_part(const int32_t* __restrict__ ci,
+                                              const T* __restrict__ val, int64_t b0, int64_t e,
+                                              int64_t stride, int P, const T* __restrict__ X,
+                                              int lane, int G, int g, int p, bool two, T& a0,
+                                              T& a1)
+{
+    const unsigned full = 0xffffffffu;
+    for (int64_t b = b0; b < e; b += stride) {
+        const int64_t k = b + lane;
+        const int c = k < e ? ci[k] : 0;
+        const T v = k < e ? val[k] : T(0);
+        const int cnt = e - b < 32 ? (int)(e - b) : 32;
+#pragma unroll 8
+        for (int t0 = 0; t0 < cnt; t0 += G) {
+            const int t = t0 + g;   // <= 31; lanes past the row's end hold v = 0
+            const int ct = __shfl_sync(full, c, t);
+            const T vt = __shfl_sync(full, v, t);
+            const T* xr = X + (int64_t)ct * P;
+            a0 += vt * xr[p];
+            if (two) a1 += vt * xr[p + 32];
+        }
+    }
+}
+
 template <typename T, class Epi>
 __global__ void __launch_bounds__(kFW * 32)
 k_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -46,27 +77,55 @@ k_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
     for (int64_t r = (int64_t)blockIdx.x * kFW + (threadIdx.x >> 5); r < rows;
          r += (int64_t)gridDim.x * kFW) {
         const int64_t s = rp[r], e = rp[r + 1];
+        if (e - s > kLongRow) continue;
         T a0 = 0, a1 = 0;
-        for (int64_t b = s; b < e; b += 32) {
-            const int64_t k = b + lane;
-            const int c = k < e ? ci[k] : 0;
-            const T v = k < e ? val[k] : T(0);
-            const int cnt = e - b < 32 ? (int)(e - b) : 32;
-#pragma unroll 4
-            for (int t0 = 0; t0 < cnt; t0 += G) {
-                const int t = t0 + g;   // <= 31; lanes past the row's end hold v = 0
-                const int ct = __shfl_sync(full, c, t);
-                const T vt = __shfl_sync(full, v, t);
-                const T* xr = X + (int64_t)ct * P;
-                a0 += vt * xr[p];
-                if (two) a1 += vt * xr[p + 32];
-            }
-        }
+        spmm_row_part(ci, val, s, e, 32, P, X, lane, G, g, p, two, a0, a1);
         for (int o = Pl; o < 32; o <<= 1) a0 += __shfl_xor_sync(full, a0, o);
         if (g == 0) {
             epi.row(r, p, a0);
             if (two) epi.row(r, p + 32, a1);
         }
+    }
+}
+
+// The rows longer than kLongRow (listed in `rows`): one block per row, warp w
+// takes the row's batches w, w + kFW, ...; the warps' sums are added in warp
+// order (fixed) before the epilogue.
+template <typename T, class Epi>
+__global__ void __launch_bounds__(kFW * 32)
+k_spmm_long(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+            const T* __restrict__ val, const int32_t* __restrict__ rows, int count, int P,
+            const T* __restrict__ X, Epi epi)
+{
+    __shared__ T sh[kFW][64];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Pl = P < 32 ? P : 32;
+    const int G = 32 / Pl;
+    const int g = lane / Pl, p = lane % Pl;
+    const bool two = P == 64;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int64_t r = rows[i];
+        const int64_t s = rp[r], e = rp[r + 1];
+        T a0 = 0, a1 = 0;
+        spmm_row_part(ci, val, s + 32 * (int64_t)warp, e, 32 * (int64_t)kFW, P, X, lane, G, g,
+                      p, two, a0, a1);
+        for (int o = Pl; o < 32; o <<= 1) a0 += __shfl_xor_sync(full, a0, o);
+        if (g == 0) {
+            sh[warp][p] = a0;
+            if (two) sh[warp][p + 32] = a1;
+        }
+        __syncthreads();
+        if (warp == 0 && g == 0) {
+            T t0 = 0, t1 = 0;
+            for (int w = 0; w < kFW; ++w) {
+                t0 += sh[w][p];
+                if (two) t1 += sh[w][p + 32];
+            }
+            epi.row(r, p, t0);
+            if (two) epi.row(r, p + 32, t1);
+        }
+        __syncthreads();
     }
 }
 
@@ -242,6 +301,29 @@ int spmm_blocks(int64_t rows)
     return (int)g;
 }
 
+// Rows of a CSR orientation with more than kLongRow nonzeros (host).
+std::vector<int32_t> long_rows(const std::vector<int64_t>& rp)
+{
+    std::vector<int32_t> out;
+    for (size_t r = 0; r + 1 < rp.size(); ++r)
+        if (rp[r + 1] - rp[r] > kLongRow) out.push_back((int32_t)r);
+    return out;
+}
+
+// One block product: the short rows (a warp each), then the long ones (a block each).
+template <typename T, class Epi>
+void spmm(Handle* h, const int64_t* rp, const int32_t* ci, const T* val, int64_t rows, int P,
+          const T* X, const int32_t* lrows, int nlong, const Epi& epi)
+{
+    k_spmm<T, Epi><<<spmm_blocks(rows), kFW * 32, 0, h->stream>>>(rp, ci, val, rows, P, X, epi);
+    ++h->launches;
+    if (nlong > 0) {
+        k_spmm_long<T, Epi><<<std::min(nlong, kFGrid), kFW * 32, 0, h->stream>>>(
+            rp, ci, val, lrows, nlong, P, X, epi);
+        ++h->launches;
+    }
+}
+
 // device buffers owned by one fishnet call
 struct Scratch {
     std::vector<void*> ptrs;
@@ -317,13 +399,23 @@ lp_status fishnet_t(Handle* h, double eta, double omega, double normK, int P, in
                                     cudaMemcpyHostToDevice, st));
         G = Gd;
     }
+    const std::vector<int32_t> lk = long_rows(h->h_rp), lt = long_rows(h->h_trp);
+    int32_t *lk_d = nullptr, *lt_d = nullptr;
+    LP_TRY(S.get(&lk_d, lk.size()));
+    LP_TRY(S.get(&lt_d, lt.size()));
+    if (!lk.empty())
+        LP_CUDA_TRY(cudaMemcpyAsync(lk_d, lk.data(), lk.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, st));
+    if (!lt.empty())
+        LP_CUDA_TRY(cudaMemcpyAsync(lt_d, lt.data(), lt.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, st));
+    const int nlk = (int)lk.size(), nlt = (int)lt.size();
     const T tau = (T)(eta / omega), sigma = (T)(eta * omega);
     // spectral casting, Y^0 = K~ X^0 (also the first K x)
     k_cast<T><<<ew_blocks(n * P), 256, 0, st>>>(n, P, normK / std::sqrt((double)n), G, X);
-    k_spmm<T, FStore<T>><<<spmm_blocks(m), kFW * 32, 0, st>>>(h->rp, h->ci, E.val, m, P, X,
-                                                                FStore<T>{Y, P});
+    ++h->launches;
+    spmm<T>(h, h->rp, h->ci, E.val, m, P, X, lk_d, nlk, FStore<T>{Y, P});
     LP_CUDA_TRY(cudaMemcpyAsync(KX, Y, sizeof(T) * (size_t)m * P, cudaMemcpyDeviceToDevice, st));
-    h->launches += 2;
     LP_CUDA_TRY(cudaGetLastError());
 
     std::vector<double> gh(P), wh((size_t)P * P);
@@ -333,22 +425,19 @@ lp_status fishnet_t(Handle* h, double eta, double omega, double normK, int P, in
     while (cols > 1) {
         const int j_top = cols;
         for (int t = 0; t < k_steps; ++t) {
-            k_spmm<T, FPrimal<T>><<<spmm_blocks(n), kFW * 32, 0, st>>>(
-                h->trp, h->tci, E.tval, n, cols, Y, FPrimal<T>{X, Xn, E.c, E.l, E.u, tau, cols});
-            k_spmm<T, FDual<T>><<<spmm_blocks(m), kFW * 32, 0, st>>>(
-                h->rp, h->ci, E.val, m, cols, Xn,
-                FDual<T>{Y, Yn, KX, E.q, h->sense, sigma, cols});
+            spmm<T>(h, h->trp, h->tci, E.tval, n, cols, Y, lt_d, nlt,
+                    FPrimal<T>{X, Xn, E.c, E.l, E.u, tau, cols});
+            spmm<T>(h, h->rp, h->ci, E.val, m, cols, Xn, lk_d, nlk,
+                    FDual<T>{Y, Yn, KX, E.q, h->sense, sigma, cols});
             std::swap(X, Xn);
             std::swap(Y, Yn);
-            h->launches += 2;
         }
         // |duality gap| of every column
-        k_spmm<T, FStore<T>><<<spmm_blocks(n), kFW * 32, 0, st>>>(h->trp, h->tci, E.tval, n,
-                                                                    cols, Y, FStore<T>{KTY, cols});
+        spmm<T>(h, h->trp, h->tci, E.tval, n, cols, Y, lt_d, nlt, FStore<T>{KTY, cols});
         k_gap_cols<T><<<nbC, kGapNT, 0, st>>>(n, cols, X, KTY, E.c, E.l, E.u, partC);
         k_gap_rows<T><<<nbR, kGapNT, 0, st>>>(m, cols, Y, E.q, partR);
         k_gap_final<<<1, 64, 0, st>>>(cols, partC, nbC, partR, nbR, gap);
-        h->launches += 4;
+        h->launches += 3;
         LP_CUDA_TRY(cudaGetLastError());
         LP_CUDA_TRY(cudaMemcpyAsync(gh.data(), gap, sizeof(double) * cols,
                                     cudaMemcpyDeviceToHost, st));

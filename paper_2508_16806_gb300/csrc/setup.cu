@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <queue>
+#include <utility>
 #include <type_traits>
 
 #include "common.cuh"
@@ -59,6 +61,50 @@ std::vector<int32_t> make_row_blocks(const int64_t* rp, int64_t rows, int cap, i
     }
     if (rows_acc > 0) b.push_back((int32_t)rows);
     return b;
+}
+
+#ifndef PDHG_TASK_ASSIGN
+#define PDHG_TASK_ASSIGN 1
+#endif
+
+void assign_tasks(const std::vector<int64_t>& task_nz, int cap, int warps,
+                  std::vector<int32_t>& wbeg, std::vector<int32_t>& perm)
+{
+    const int nt = (int)task_nz.size() - 1;
+    if (PDHG_TASK_ASSIGN == 0) {   // round robin: warp w takes tasks w, w + warps, ...
+        wbeg.assign((size_t)warps + 1, 0);
+        perm.clear();
+        for (int w = 0; w < warps; ++w) {
+            for (int t = w; t < nt; t += warps) perm.push_back(t);
+            wbeg[(size_t)w + 1] = (int32_t)perm.size();
+        }
+        return;
+    }
+    std::vector<int64_t> cost((size_t)std::max(nt, 0));
+    for (int t = 0; t < nt; ++t) {
+        const int64_t len = task_nz[(size_t)t + 1] - task_nz[(size_t)t];
+        cost[(size_t)t] = std::max<int64_t>(1, (len + cap - 1) / cap);
+    }
+    std::vector<int32_t> order((size_t)std::max(nt, 0));
+    for (int t = 0; t < nt; ++t) order[(size_t)t] = t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return cost[(size_t)a] > cost[(size_t)b]; });
+    using Slot = std::pair<int64_t, int32_t>;   // (load, warp)
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> pq;
+    for (int w = 0; w < warps; ++w) pq.push(Slot{0, w});
+    std::vector<int32_t> owner((size_t)std::max(nt, 0));
+    for (int32_t t : order) {
+        const Slot sl = pq.top();
+        pq.pop();
+        owner[(size_t)t] = sl.second;
+        pq.push(Slot{sl.first + cost[(size_t)t], sl.second});
+    }
+    wbeg.assign((size_t)warps + 1, 0);
+    for (int t = 0; t < nt; ++t) ++wbeg[(size_t)owner[(size_t)t] + 1];
+    for (int w = 0; w < warps; ++w) wbeg[(size_t)w + 1] += wbeg[(size_t)w];
+    std::vector<int32_t> cur(wbeg.begin(), wbeg.end() - 1);
+    perm.assign((size_t)std::max(nt, 0), 0);
+    for (int t = 0; t < nt; ++t) perm[(size_t)cur[(size_t)owner[(size_t)t]]++] = t;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -576,10 +622,10 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     ++h->launches;
     for (int it = 0; it < o->power_iters; ++it) {
         EpiStore<double> e1{b, t, nullptr, nullptr, go};
-        launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
+        launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
         ++h->launches;
         EpiStore<double> e2{t, b, nullptr, part, go};
-        launch_spmv<double>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, h->m,
+        launch_spmv<double>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m,
                             e2);
         ++h->launches;
         k_pow_normalize<<<1, kCtlNT, 0, st>>>(n, b, part, E.gT, go);
@@ -587,7 +633,7 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
         LP_CUDA_TRY(cudaGetLastError());
     }
     EpiStore<double> e3{b, t, nullptr, part, nullptr};
-    launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, h->n, e3);
+    launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e3);
     ++h->launches;
     k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.gK, part + E.gK + 4);
     ++h->launches;
@@ -614,16 +660,33 @@ lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
     for (size_t t = 0; t < bt.size(); ++t) nt[t] = h->h_trp[(size_t)bt[t]];
     int sms = 0;
     LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    dev_free(h, E.brow);
-    dev_free(h, E.bcol);
-    dev_free(h, E.bnzK);
-    dev_free(h, E.bnzT);
-    E.brow = E.bcol = nullptr;
+    const int gK = spmv_grid((int)bk.size() - 1, sms), gT = spmv_grid((int)bt.size() - 1, sms);
+    std::vector<int32_t> wk, pk, wt, pt;
+    assign_tasks(nk, sK.cap, gK * kTaskWarps, wk, pk);
+    assign_tasks(nt, sT.cap, gT * kTaskWarps, wt, pt);
+    for (void* p : {(void*)E.brow, (void*)E.bcol, (void*)E.bnzK, (void*)E.bnzT, (void*)E.wbegK,
+                    (void*)E.permK, (void*)E.wbegT, (void*)E.permT})
+        dev_free(h, p);
+    E.brow = E.bcol = E.wbegK = E.permK = E.wbegT = E.permT = nullptr;
     E.bnzK = E.bnzT = nullptr;
     LP_TRY(dev_alloc_n(h, &E.brow, bk.size()));
     LP_TRY(dev_alloc_n(h, &E.bcol, bt.size()));
     LP_TRY(dev_alloc_n(h, &E.bnzK, nk.size()));
     LP_TRY(dev_alloc_n(h, &E.bnzT, nt.size()));
+    LP_TRY(dev_alloc_n(h, &E.wbegK, wk.size()));
+    LP_TRY(dev_alloc_n(h, &E.permK, pk.size()));
+    LP_TRY(dev_alloc_n(h, &E.wbegT, wt.size()));
+    LP_TRY(dev_alloc_n(h, &E.permT, pt.size()));
+    LP_CUDA_TRY(cudaMemcpyAsync(E.wbegK, wk.data(), wk.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    if (!pk.empty())
+        LP_CUDA_TRY(cudaMemcpyAsync(E.permK, pk.data(), pk.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, h->stream));
+    LP_CUDA_TRY(cudaMemcpyAsync(E.wbegT, wt.data(), wt.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    if (!pt.empty())
+        LP_CUDA_TRY(cudaMemcpyAsync(E.permT, pt.data(), pt.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, h->stream));
     LP_CUDA_TRY(cudaMemcpyAsync(E.brow, bk.data(), bk.size() * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, h->stream));
     LP_CUDA_TRY(cudaMemcpyAsync(E.bcol, bt.data(), bt.size() * sizeof(int32_t),
@@ -635,8 +698,8 @@ lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
     LP_CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
     E.nblk = (int)bk.size() - 1;
     E.ntblk = (int)bt.size() - 1;
-    E.gK = spmv_grid(E.nblk, sms);
-    E.gT = spmv_grid(E.ntblk, sms);
+    E.gK = gK;
+    E.gT = gT;
     E.schedK = sK;
     E.schedT = sT;
     return LP_OK;

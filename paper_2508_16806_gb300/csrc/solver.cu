@@ -461,7 +461,7 @@ static void launch_dual(Handle* h, Engine<T>& E, cudaStream_t st)
 {
     EpiDual<T> ed{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS, E.q, h->sense,
                   E.partD};
-    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, h->n, ed);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed);
 }
 
 template <typename T>
@@ -469,7 +469,7 @@ static void launch_primal_t(Handle* h, Engine<T>& E, cudaStream_t st)
 {
     EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.partT,
                      E.partD, E.gK};
-    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
 }
 
 // one step attempt: 3 launches
@@ -490,9 +490,9 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
                                                      E.YS, E.XA, E.YA, E.l, E.u, h->sense, n, m);
     const int* gate = &E.ctrl->want_check;
     EpiStore<T> e1{E.XA, E.KXA, nullptr, nullptr, gate};
-    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
     EpiStore<T> e2{E.YA, E.KTYA, nullptr, nullptr, gate};
-    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
     k_check_rows<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YA,
                                              E.KXA, E.YANC, E.q, h->sense, E.Rt, E.Rinv, m,
                                              E.partR);
@@ -604,9 +604,9 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
                                                      E.l, E.u, h->sense, h->R, h->C, wxs, wys,
                                                      dwx, dwy, n, m);
     EpiStore<T> e1{E.X[0], E.KX[0], nullptr, nullptr, nullptr};
-    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
     EpiStore<T> e2{E.Y[0], E.KTY[0], nullptr, nullptr, nullptr};
-    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
     LP_CUDA_TRY(cudaGetLastError());
 
     // device trace buffer

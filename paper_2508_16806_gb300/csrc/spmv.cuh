@@ -256,6 +256,7 @@ __device__ __forceinline__ void stage_task(WarpStage<T>& W, int st, int64_t s, i
 template <typename T, class Epi, bool L1G>
 __global__ void __launch_bounds__(kSpmvNT, kSpmvMinBlocks)
 k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz, int ntasks,
+       const int32_t* __restrict__ wbeg, const int32_t* __restrict__ perm,
        const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
        int* err, Epi epi)
 {
@@ -268,7 +269,6 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
     WarpStage<T>& W = reinterpret_cast<WarpStage<T>*>(smem_raw)[warp];
     typename Epi::Acc acc;
     const T* __restrict__ xv = epi.xin();   // re-read per task: a batch's LPs differ
-    const int stride = gridDim.x * kTaskWarps;
     if (lane == 0) {
         mbar_init(&W.bar[0], 1);
         mbar_init(&W.bar[1], 1);
@@ -276,13 +276,19 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
     }
     __syncwarp();
     const uint64_t pol = evict_first_policy();
-    // the warp's tasks are t0, t0 + stride, ...; tasks the epilogue declares dead
-    // (a finished LP of a batch) are passed over
-    auto next_live = [&](int t) {
-        while (t < ntasks && !epi.live(t)) t += stride;
-        return t;
+    // the warp's tasks are perm[wbeg[w] .. wbeg[w + 1]) (assigned on the host by
+    // their chunk counts); tasks the epilogue declares dead (a finished LP of a
+    // batch) are passed over.  `ntasks` marks "no task".
+    const int gw = blockIdx.x * kTaskWarps + warp;
+    const int pend = wbeg[gw + 1];
+    auto next_live = [&](int p) {
+        while (p < pend && !epi.live(perm[p])) ++p;
+        return p;
     };
-    int task = next_live(blockIdx.x * kTaskWarps + warp);
+    auto task_at = [&](int p) { return p < pend ? perm[p] : ntasks; };
+    int pos = next_live(wbeg[gw]);
+    int task = task_at(pos);
+    int npos = pend;
     int nt = ntasks;    // the next live task after `task`
     // current task [s, e), current chunk [cs, ce); next task bounds [ns, ne)
     int64_t s = 0, e = 0, ns = 0, ne = 0, cs = 0, ce = 0;
@@ -292,7 +298,8 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         cs = s;
         ce = e - s > CAPW ? s + CAPW : e;
         if (lane == 0 && ce > cs) stage_task<T>(W, 0, cs, ce, val, ci, pol);
-        nt = next_live(task + stride);
+        npos = next_live(pos + 1);
+        nt = task_at(npos);
         if (nt < ntasks) {
             ns = task_nz[nt];
             ne = task_nz[nt + 1];
@@ -436,12 +443,14 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         } else {
             epi.task_done(task, acc);
             task = nt;
+            pos = npos;
             s = ns;
             e = ne;
             cs = xs;
             ce = xe;
             if (task < ntasks) {
-                nt = next_live(task + stride);
+                npos = next_live(pos + 1);
+                nt = task_at(npos);
                 if (nt < ntasks) {
                     ns = task_nz[nt];
                     ne = task_nz[nt + 1];
@@ -478,16 +487,17 @@ constexpr int64_t kL1GatherBytes = 96 * 1024;
 
 template <typename T, class Epi>
 inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
-                        const int64_t* task_nz, int ntasks, const int64_t* rp, const int32_t* ci,
-                        const T* val, int* err, int64_t x_len, const Epi& epi)
+                        const int64_t* task_nz, int ntasks, const int32_t* wbeg,
+                        const int32_t* perm, const int64_t* rp, const int32_t* ci, const T* val,
+                        int* err, int64_t x_len, const Epi& epi)
 {
     const size_t sm = spmv_smem_bytes<T>();
     if (x_len * (int64_t)sizeof(T) <= kL1GatherBytes)
-        k_spmv<T, Epi, true><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, rp, ci, val,
-                                                        err, epi);
+        k_spmv<T, Epi, true><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg, perm, rp,
+                                                        ci, val, err, epi);
     else
-        k_spmv<T, Epi, false><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, rp, ci, val,
-                                                         err, epi);
+        k_spmv<T, Epi, false><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg, perm,
+                                                         rp, ci, val, err, epi);
 }
 
 // The task hooks of an epilogue that serves a single LP: every task is live,
@@ -543,6 +553,14 @@ inline int spmv_grid(int ntasks, int num_sms)
 // holds <= cap nonzeros and <= max_rows rows; a row longer than cap gets a task
 // of its own.  Returns the task boundaries (ntasks + 1 entries).
 std::vector<int32_t> make_row_blocks(const int64_t* rp, int64_t rows, int cap, int max_rows);
+
+// Assigns tasks to the `warps` warps of a launch (host): a task costs its number
+// of chunks of at most `cap` nonzeros (task_nz: ntasks + 1 nonzero bounds);
+// longest first, each to the least-loaded warp (ties: lower warp), so one warp
+// does not collect several long rows.  wbeg[warps + 1] indexes perm, which lists
+// each warp's tasks in ascending order.
+void assign_tasks(const std::vector<int64_t>& task_nz, int cap, int warps,
+                  std::vector<int32_t>& wbeg, std::vector<int32_t>& perm);
 
 // Schedule autotuner (tune.cu).  Candidates: cap in {CAPW, CAPW / 2} nonzeros
 // and max_rows in {kTaskRows, 32, 16} rows per task.  build(cap, max_rows)

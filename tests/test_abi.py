@@ -38,7 +38,7 @@ def test_host_only_calls_without_gpu():
     o = L.lp_opts_default()
     assert o.tol == 1e-4 and o.check_every == 64 and o.eta_scale == 0.9
     assert o.beta_sufficient == 0.2 and o.beta_necessary == 0.8 and o.beta_artificial == 0.36
-    assert o.infeas_detect == 1 and o.infeas_tol == 1e-6 and o.autotune == 1
+    assert o.infeas_detect == 1 and o.infeas_tol == 1e-6 and o.autotune == 0
     assert L.lp_status_string(1) == "LP_OPTIMAL"
     assert L.lp_status_string(-1) == "LP_INVALID_ARGUMENT"
     assert L.load().lp_abi_version() == 3

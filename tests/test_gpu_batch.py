@@ -89,3 +89,13 @@ def test_lp_solve_batch_one_shot(L):
         assert res[k].status == L.LP_OPTIMAL
         xk, _, sk, _ = probs[k].solve(tol=1e-6)
         assert abs(float(LPS[k].c @ xs[k]) - float(LPS[k].c @ xk)) <= 1e-5 * (1 + abs(float(LPS[k].c @ xk)))
+
+
+def test_batch_autotuned_schedules(L, oracle_mod):
+    batch = L.Batch(LPS)
+    out = batch.solve(tol=1e-6, max_iters=500000, autotune=1)
+    for lp, (x, y, info) in zip(LPS, out):
+        assert info["status"] == L.LP_OPTIMAL, info
+        k = oracle_mod.kkt(lp, x, y)
+        assert max(k["rel_gap"], k["rel_pres"], k["rel_dres"]) <= 1e-6 * (1 + 1e-6)
+    batch.close()

@@ -256,3 +256,18 @@ def test_constraint_free_columns_and_free_variables(L, oracle_mod):
     xo, yo, io, tro = oracle_mod.solve(lp2, tol=1e-13, max_iters=500, trace_cap=64, **FIXED)
     assert rel(x, xo) <= 1e-10 and rel(y, yo) <= 1e-10
     _check_trace(tr, tro)
+
+
+@pytest.mark.parametrize("name", ["ragged", "powerlaw"])
+def test_autotuned_schedule_solves(L, oracle_mod, name):
+    """With the schedule autotuner on, the solve reaches the same tolerance and
+    objective (the task shapes change only the order of the row sums)."""
+    lp = PROBS[name]
+    prob = L.Problem(lp)
+    x, y, info, _ = prob.solve(tol=1e-7, autotune=1, max_iters=500000)
+    assert info["status"] == L.LP_OPTIMAL
+    k = oracle_mod.kkt(lp, x, y)
+    assert max(k["rel_gap"], k["rel_pres"], k["rel_dres"]) <= 1e-7 * (1 + 1e-6)
+    # a second solve on the same handle reuses the tuned schedule: bitwise repeatable
+    x2, y2, info2, _ = prob.solve(tol=1e-7, autotune=1, max_iters=500000)
+    assert np.array_equal(x, x2) and np.array_equal(y, y2)
