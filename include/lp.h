@@ -67,7 +67,7 @@ enum { LP_PREC_FP64 = 0, LP_PREC_MIXED = 1 };
 /* The LP.  Arrays: row_ptr[m+1] (row_ptr[0] = 0, non-decreasing,
  * row_ptr[m] = nnz), col_idx[nnz] in [0, n) (any order inside a row; duplicates
  * are summed), vals[nnz], sense[m], c[n], q[m], l[n], u[n] with l <= u and no
- * NaN anywhere.  Requirements: m >= 1, n >= 1, nnz < 2^31. */
+ * NaN anywhere.  Requirements: m >= 1, n >= 1, nnz < 2^31 - 64. */
 typedef struct {
     int64_t m, n, nnz;
     const int64_t* row_ptr;

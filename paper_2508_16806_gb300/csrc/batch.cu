@@ -817,6 +817,8 @@ lp_status batch_scale(BatchHandle* bh, const lp_opts* o, double* normK_dev)
     BatchSched<double>& S = bh->s64;
     LP_CUDA_TRY(cudaMemcpyAsync(E.val, h->val0, pad8(nnz) * sizeof(double),
                                 cudaMemcpyDeviceToDevice, st));
+    // tuned before the power iteration uses it (same order of sums in every solve)
+    if (o->autotune) LP_TRY(tune_batch<double>(bh));
     k_fill_f64<<<grid_n(m, 256, 65535), 256, 0, st>>>(h->R, m, 1.0);
     k_fill_f64<<<grid_n(n, 256, 65535), 256, 0, st>>>(h->C, n, 1.0);
     double* rn = h->scratch;
@@ -1156,7 +1158,7 @@ static lp_status batch_build(BatchHandle* bh, const lp_handle* hs, int B)
         if (g.stream != st) LP_CUDA_TRY(cudaStreamSynchronize(g.stream));
     }
     const int64_t m = M.row0[B], n = M.col0[B], nnz = M.nz0[B];
-    if (nnz >= ((int64_t)1 << 31) || m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31))
+    if (nnz >= ((int64_t)1 << 31) - 64 || m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31))
         return LP_INVALID_ARGUMENT;
     // stacked arrays in temporary buffers, then the usual device setup
     std::vector<void*> tmp;

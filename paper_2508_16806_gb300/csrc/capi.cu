@@ -123,7 +123,7 @@ lp_status lp_create(const lp_desc* d, void* cuda_stream, lp_handle* out)
 {
     if (!out) return LP_INVALID_ARGUMENT;
     *out = nullptr;
-    if (!d || d->m < 1 || d->n < 1 || d->nnz < 0 || d->nnz >= ((int64_t)1 << 31) ||
+    if (!d || d->m < 1 || d->n < 1 || d->nnz < 0 || d->nnz >= ((int64_t)1 << 31) - 64 ||
         d->n >= ((int64_t)1 << 31) || d->m >= ((int64_t)1 << 31))
         return LP_INVALID_ARGUMENT;
     if (!d->row_ptr || (d->nnz > 0 && (!d->col_idx || !d->vals)) || !d->sense || !d->c || !d->q ||
@@ -180,6 +180,9 @@ static lp_status prepare_fp64(Handle* h, const lp_opts* o, double* normK, double
                               double* omega0)
 {
     LP_TRY(setup_engine<double>(h, o));
+    // the FP64 schedule is tuned before its first use (the power iteration), so
+    // that every solve on this handle sums in the same order
+    if (o->autotune) LP_TRY(tune_engine<double>(h));
     LP_TRY(setup_scale(h, o, normK));
     double cs2 = 0.0, qs2 = 0.0;
     LP_TRY(sum_of_squares(h, h->e64.c, h->n, &cs2));

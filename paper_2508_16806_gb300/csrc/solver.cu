@@ -92,19 +92,26 @@ struct EpiDual {
     int cur; T sigma; T pw; int adapt;
     struct Pre { T y = 0, kx = 0, q = 0, ys = 0; uint8_t ge = 0; };
     struct Acc { T dy2 = T(0); };   // per-lane sums in T, reduced in FP64
+    // after begin(), the *0 members point at the current half and the *1 members
+    // at the other one (x' and the new y, K x' are written there)
     __device__ bool begin() {
         if (ctrl->skip) return false;
         cur = ctrl->cur;
+        if (cur) {
+            const T* t = xs0; xs0 = xs1; xs1 = t;
+            T* u = y0; y0 = y1; y1 = u;
+            u = kx0; kx0 = kx1; kx1 = u;
+        }
         sigma = (T)(ctrl->eta * ctrl->omega);
         pw = (T)ctrl->pend_w;
         adapt = ctrl->adaptive;
         return true;
     }
-    __device__ const T* xin() const { return cur ? xs0 : xs1; }   // x' lives in the other half
+    __device__ const T* xin() const { return xs1; }   // x' lives in the other half
     __device__ Pre load(int i) const {
         Pre p;
-        p.y = (cur ? y1 : y0)[i];
-        p.kx = (cur ? kx1 : kx0)[i];
+        p.y = y0[i];
+        p.kx = kx0[i];
         p.q = q[i];
         p.ge = sense[i];
         if (pw != T(0)) p.ys = ys[i];
@@ -114,8 +121,8 @@ struct EpiDual {
         if (pw != T(0)) ys[i] = p.ys + pw * p.y;
         T v = p.y + sigma * (p.q - (T(2) * kxn - p.kx));
         if (p.ge && v < T(0)) v = T(0);
-        (cur ? y0 : y1)[i] = v;
-        (cur ? kx0 : kx1)[i] = kxn;
+        y1[i] = v;
+        kx1[i] = kxn;
         const T d = v - p.y;
         a.dy2 += d * d;
     }
@@ -144,24 +151,31 @@ struct EpiPrimalT {
     int cur; int adapt;
     struct Pre { T x = 0, xn = 0, kt = 0; };
     struct Acc { T dx2 = T(0), inter = T(0); };   // per-lane sums in T, reduced in FP64
+    // after begin(), the *0 members point at the current half, the *1 members at
+    // the other one (y', x' and the new K^T y')
     __device__ bool begin() {
         if (ctrl->skip) return false;
         cur = ctrl->cur;
+        if (cur) {
+            const T* t = ys0; ys0 = ys1; ys1 = t;
+            t = x0; x0 = x1; x1 = t;
+            T* u = kty0; kty0 = kty1; kty1 = u;
+        }
         adapt = ctrl->adaptive;
         return true;
     }
-    __device__ const T* xin() const { return cur ? ys0 : ys1; }   // y'
+    __device__ const T* xin() const { return ys1; }   // y'
     __device__ Pre load(int j) const {
         Pre p;
         if (adapt) {
-            p.x = (cur ? x1 : x0)[j];
-            p.xn = (cur ? x0 : x1)[j];
-            p.kt = (cur ? kty1 : kty0)[j];
+            p.x = x0[j];
+            p.xn = x1[j];
+            p.kt = kty0[j];
         }
         return p;
     }
     __device__ void row(int j, T ktyn, const Pre& p, Acc& a) const {
-        (cur ? kty0 : kty1)[j] = ktyn;
+        kty1[j] = ktyn;
         if (adapt) {
             const T dx = p.xn - p.x;
             a.dx2 += dx * dx;
@@ -180,15 +194,23 @@ struct EpiPrimalT {
         __syncthreads();
         if (!last) return;
         __threadfence();
-        double dy2 = 0.0, dx2 = 0.0, inter = 0.0;
-        if (adapt) {
-            dy2 = block_sum_array<kSpmvNT>(partD, nD);
-            dx2 = block_sum_array<kSpmvNT>(part, gridDim.x);
-            inter = block_sum_array<kSpmvNT>(part + gridDim.x, gridDim.x);
+        // warps 0..2 sum the three partial arrays side by side (fixed order:
+        // lane-strided sums, then the warp's tree)
+        __shared__ double tot[3];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (adapt && warp < 3) {
+            const double* src = warp == 0 ? partD : part + (warp - 1) * gridDim.x;
+            const int cnt = warp == 0 ? nD : (int)gridDim.x;
+            double v = 0.0;
+            for (int i = lane; i < cnt; i += 32) v += __ldcg(src + i);
+            v = warp_sum(v);
+            if (lane == 0) tot[warp] = v;
         }
+        __syncthreads();
         if (threadIdx.x == 0) {
             ctrl->tick = 0;
-            step_decide(ctrl, adapt, dy2, dx2, inter);
+            if (adapt) step_decide(ctrl, adapt, tot[0], tot[1], tot[2]);
+            else step_decide(ctrl, adapt, 0.0, 0.0, 0.0);
         }
     }
 };

@@ -286,23 +286,23 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         return p;
     };
     auto task_at = [&](int p) { return p < pend ? perm[p] : ntasks; };
-    int pos = next_live(wbeg[gw]);
-    int task = task_at(pos);
-    int npos = pend;
+    int npos = next_live(wbeg[gw]);   // position of the current task, then of the next
+    int task = task_at(npos);
     int nt = ntasks;    // the next live task after `task`
     // current task [s, e), current chunk [cs, ce); next task bounds [ns, ne)
-    int64_t s = 0, e = 0, ns = 0, ne = 0, cs = 0, ce = 0;
+    // (32-bit: the library accepts fewer than 2^31 - 64 nonzeros)
+    int s = 0, e = 0, ns = 0, ne = 0, cs = 0, ce = 0;
     if (task < ntasks) {
-        s = task_nz[task];
-        e = task_nz[task + 1];
+        s = (int)task_nz[task];
+        e = (int)task_nz[task + 1];
         cs = s;
         ce = e - s > CAPW ? s + CAPW : e;
         if (lane == 0 && ce > cs) stage_task<T>(W, 0, cs, ce, val, ci, pol);
-        npos = next_live(pos + 1);
+        npos = next_live(npos + 1);
         nt = task_at(npos);
         if (nt < ntasks) {
-            ns = task_nz[nt];
-            ne = task_nz[nt + 1];
+            ns = (int)task_nz[nt];
+            ne = (int)task_nz[nt + 1];
         }
     }
     uint32_t par = 0;   // bit st: parity of the next wait on stage st
@@ -316,7 +316,7 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         const bool last = ce == e;
         const bool is_long = e - s > CAPW;
         // the next chunk: the rest of this long row, or the first chunk of the next task
-        int64_t xs = 0, xe = 0;
+        int xs = 0, xe = 0;
         bool have_next = false;
         if (!last) {
             xs = ce;
@@ -358,10 +358,10 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         // l, l + 32, l + 64, ... of the staged values; it reads each group's values and
         // column indices with one vector load apiece, gathers x, and writes the
         // products back in place (or adds them to its long-row sum)
-        const int64_t v0 = cs & ~(int64_t)(VA - 1);
-        const int d = (int)(v0 - (cs & ~(int64_t)3));   // index-buffer offset of v0
-        const int vo = (int)(cs - v0);
-        const int lim = vo + (int)(ce - cs);
+        const int v0 = cs & ~(VA - 1);
+        const int d = v0 - (cs & ~3);   // index-buffer offset of v0
+        const int vo = cs - v0;
+        const int lim = vo + (ce - cs);
         T* vbuf = W.v[st];
         const int* ibuf = W.i[st] + d;
         using VT = VecTraits<T>;
@@ -443,17 +443,16 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         } else {
             epi.task_done(task, acc);
             task = nt;
-            pos = npos;
             s = ns;
             e = ne;
             cs = xs;
             ce = xe;
             if (task < ntasks) {
-                npos = next_live(pos + 1);
+                npos = next_live(npos + 1);
                 nt = task_at(npos);
                 if (nt < ntasks) {
-                    ns = task_nz[nt];
-                    ne = task_nz[nt + 1];
+                    ns = (int)task_nz[nt];
+                    ne = (int)task_nz[nt + 1];
                 }
             }
         }
