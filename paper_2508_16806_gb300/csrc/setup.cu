@@ -351,19 +351,16 @@ __global__ void k_sum_final(const double* part, int count, double* out)
     if (threadIdx.x == 0) *out = s;
 }
 
-// power iteration step: b /= ||b||, or stop when ||b|| = 0
-__global__ void k_pow_normalize(int64_t n, double* b, const double* part, int nparts, int* go)
+// power iteration step: inv = 1 / ||b|| (the next K product is scaled by it,
+// which is the product with b / ||b||), or stop when ||b|| = 0
+__global__ void k_pow_inv_norm(const double* part, int nparts, double* inv, int* go)
 {
-    __shared__ double nb;
     if (*go == 0) return;
     const double s = block_sum_array<kCtlNT>(part, nparts);
-    if (threadIdx.x == 0) nb = sqrt(s);
-    __syncthreads();
-    if (nb == 0.0) {
-        if (threadIdx.x == 0) *go = 0;
-        return;
+    if (threadIdx.x == 0) {
+        if (s > 0.0) *inv = 1.0 / sqrt(s);
+        else *go = 0;
     }
-    for (int64_t j = threadIdx.x; j < n; j += kCtlNT) b[j] = b[j] / nb;
 }
 
 // ------------------------------------------------------------------ host
@@ -609,30 +606,35 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     ++h->launches;
     LP_CUDA_TRY(cudaGetLastError());
 
-    // Algorithm 2 on K~: b = 1; repeat b <- K~^T (K~ b), b <- b / ||b||; ||K~ b||
+    // Algorithm 2 on K~: b = 1; repeat b <- K~^T (K~ b), b <- b / ||b||; ||K~ b||.
+    // The normalisation is carried as a scale of the next K~ product
+    // (K~ (b / ||b||) = (K~ b) / ||b||), so b is never rewritten.
     double* b = E.XA;          // n
     double* t = E.KXA;         // m
     double* part = h->scratch;  // partials of ||b||^2 (gT) / ||t||^2 (gK)
     int* go = reinterpret_cast<int*>(h->scratch + std::max(E.gK, E.gT) + 8);
+    double* inv = h->scratch + std::max(E.gK, E.gT) + 16;   // 1 / ||b||
     LP_CUDA_TRY((spmv_prepare<double, EpiStore<double>>()));
     k_fill<double><<<grid_for(n), 256, 0, st>>>(b, n, 1.0);
+    ++h->launches;
+    k_fill<double><<<1, 32, 0, st>>>(inv, 1, 1.0);
     ++h->launches;
     LP_CUDA_TRY(cudaMemsetAsync(go, 0, sizeof(int), st));
     k_fill<int><<<1, 32, 0, st>>>(go, 1, 1);
     ++h->launches;
     for (int it = 0; it < o->power_iters; ++it) {
-        EpiStore<double> e1{b, t, nullptr, nullptr, go};
+        EpiStore<double> e1{b, t, inv, nullptr, go};
         launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
         ++h->launches;
         EpiStore<double> e2{t, b, nullptr, part, go};
         launch_spmv<double>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m,
                             e2);
         ++h->launches;
-        k_pow_normalize<<<1, kCtlNT, 0, st>>>(n, b, part, E.gT, go);
+        k_pow_inv_norm<<<1, kCtlNT, 0, st>>>(part, E.gT, inv, go);
         ++h->launches;
         LP_CUDA_TRY(cudaGetLastError());
     }
-    EpiStore<double> e3{b, t, nullptr, part, nullptr};
+    EpiStore<double> e3{b, t, inv, part, nullptr};
     launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e3);
     ++h->launches;
     k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.gK, part + E.gK + 4);

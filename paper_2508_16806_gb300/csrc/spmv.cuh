@@ -330,6 +330,10 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
         // an empty chunk (a task of empty rows) is neither copied nor waited for
         const bool next_staged = have_next && xe > xs;
         if (next_staged && lane == 0) stage_task<T>(W, st ^ 1, xs, xe, val, ci, pol);
+        // row starts of a short task: loaded now (low 32 bits: fewer than 2^31
+        // nonzeros), written to shared memory after the gathers are in flight, so
+        // that their latency hides behind the stage wait and the gathers
+        int rpl0 = 0, rpl1 = 0;
         if (first) {
             epi.task_start(task);
             xv = epi.xin();
@@ -337,8 +341,11 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
             nrows = task_row[task + 1] - r0;
             if (lane < nrows) pre0 = epi.load(r0 + lane);
             if (kTaskRows > 32 && lane + 32 < nrows) pre1 = epi.load(r0 + 32 + lane);
-            if (!is_long)
-                for (int t = lane; t <= nrows; t += 32) W.rps[t] = (int)(rp[r0 + t] - s);
+            if (!is_long) {
+                const int* rp32 = reinterpret_cast<const int*>(rp);
+                if (lane < nrows) rpl0 = rp32[2 * ((int64_t)r0 + lane)];
+                if (kTaskRows > 32 && lane + 32 < nrows) rpl1 = rp32[2 * ((int64_t)r0 + 32 + lane)];
+            }
             along = 0;
         }
         if (ce > cs) {
@@ -391,6 +398,11 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
                     vv[k][v] = T(0);
                 }
             }
+        }
+        if (first && !is_long) {
+            if (lane < nrows) W.rps[lane] = rpl0 - s;
+            if (kTaskRows > 32 && lane + 32 < nrows) W.rps[lane + 32] = rpl1 - s;
+            if (lane == 0) W.rps[nrows] = e - s;
         }
         if (is_long) {
 #pragma unroll
