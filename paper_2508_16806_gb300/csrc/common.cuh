@@ -103,8 +103,8 @@ struct Engine {
     // Ruiz factors R, C and their reciprocals in this precision (KKT checks)
     T* Rt = nullptr; T* Ct = nullptr; T* Rinv = nullptr; T* Cinv = nullptr;
     // reduction partials
-    double* partD = nullptr;   // [gK] (sized for the largest grid)
-    double* partT = nullptr;   // [2][gT] (sized for the largest grid)
+    double* partD = nullptr;   // [2][gK] Algorithm 5 partials of the K x' launch (largest grid)
+    double* partT = nullptr;   // [kEWGrid] ||x' - x||^2 partials of k_primal
     double* partR = nullptr;   // [kRowQ][kEWGrid]
     double* partC = nullptr;   // [kColQ][kEWGrid]
     Ctrl* ctrl = nullptr;

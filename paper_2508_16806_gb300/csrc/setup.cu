@@ -731,8 +731,8 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         int sms = 0;
         LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
         const size_t gmax = (size_t)spmv_grid(1 << 30, sms);
-        LP_TRY(dev_alloc_n(h, &E.partD, gmax + 8));
-        LP_TRY(dev_alloc_n(h, &E.partT, 2 * gmax + 8));
+        LP_TRY(dev_alloc_n(h, &E.partD, 2 * gmax + 8));
+        LP_TRY(dev_alloc_n(h, &E.partT, (size_t)kEWGrid + 8));
         LP_TRY(dev_alloc_n(h, &E.partR, kRowQ * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.partC, kColQ * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.ctrl, 1));

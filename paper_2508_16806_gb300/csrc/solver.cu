@@ -26,14 +26,16 @@ namespace pdhg {
 // ------------------------------------------------------------------ step kernels
 
 // x' = clamp(x - tau (c - K^T y), l, u); the pending averaged iterate is added to
-// the x sums on the way.  16-byte vector loads, scalar tail.
+// the x sums on the way, and (adaptive step) each block's partial of ||x' - x||^2
+// goes to part[blockIdx.x].  16-byte vector loads, scalar tail.
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0,
          const T* __restrict__ kty1, const T* __restrict__ c, const T* __restrict__ l,
-         const T* __restrict__ u, T* xs, int64_t n)
+         const T* __restrict__ u, T* xs, int64_t n, double* part)
 {
     if (ctrl->skip) return;
+    T dx2 = T(0);
     using VT = VecTraits<T>;
     constexpr int VEC = VT::N;
     const int cur = ctrl->cur;
@@ -63,6 +65,7 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
             if (v < lj[k]) v = lj[k];
             if (v > uj[k]) v = uj[k];
             o[k] = v;
+            dx2 += (v - xj[k]) * (v - xj[k]);
         }
         *reinterpret_cast<typename VT::V*>(xn + t * VEC) = VT::pack(o);
     }
@@ -75,6 +78,11 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
         if (v < lo) v = lo;
         if (v > hi) v = hi;
         xn[j] = v;
+        dx2 += (v - xj) * (v - xj);
+    }
+    if (ctrl->adaptive) {
+        const double t[1] = {(double)dx2};
+        block_partials<1, kEW>(t, part, gridDim.x);
     }
 }
 
@@ -91,7 +99,9 @@ struct EpiDual {
     double* part;
     int cur; T sigma; T pw; int adapt;
     struct Pre { T y = 0, kx = 0, q = 0, ys = 0; uint8_t ge = 0; };
-    struct Acc { T dy2 = T(0); };   // per-lane sums in T, reduced in FP64
+    // per-lane sums in T, reduced in FP64: ||y' - y||^2 and the Algorithm 5
+    // interaction (y' - y)^T K (x' - x) = sum_i dy_i ((K x')_i - (K x)_i)
+    struct Acc { T dy2 = T(0), inter = T(0); };
     // after begin(), the *0 members point at the current half and the *1 members
     // at the other one (x' and the new y, K x' are written there)
     __device__ bool begin() {
@@ -125,69 +135,51 @@ struct EpiDual {
         kx1[i] = kxn;
         const T d = v - p.y;
         a.dy2 += d * d;
+        a.inter += d * (kxn - p.kx);
     }
     __device__ void finish(Acc& a) const {
         if (adapt) {
-            const double t[1] = {(double)a.dy2};
-            block_partials<1, kSpmvNT>(t, part, gridDim.x);
+            const double t[2] = {(double)a.dy2, (double)a.inter};
+            block_partials<2, kSpmvNT>(t, part, gridDim.x);
         }
     }
 };
 
-// K^T y' SpMV + Algorithm 5 terms; the last block to finish sums every block's
-// partials (fixed order) and takes the step decision, so the attempt needs no
-// separate control launch.  No block waits for another: the last block is the
-// one whose ticket completes the count.
+// K^T y' SpMV; the last block to finish sums the Algorithm 5 partials of the
+// attempt (||x' - x||^2 from k_primal, ||y' - y||^2 and the interaction from the
+// K x' launch; fixed order) and takes the step decision, so the attempt needs
+// no separate control launch.  No block waits for another: the last block is
+// the one whose ticket completes the count.
 template <typename T>
 struct EpiPrimalT {
     PDHG_SINGLE_LP_TASK_HOOKS
     Ctrl* ctrl;
     const T* ys0; const T* ys1;     // Y[0], Y[1]
-    const T* x0; const T* x1;
     T* kty0; T* kty1;
-    double* part;                   // [2][gridDim.x]
-    const double* partD;            // dy^2 partials of the K x' launch
+    const double* partP;            // ||x' - x||^2 partials of k_primal [nP]
+    int nP;
+    const double* partD;            // [2][nD] partials of the K x' launch
     int nD;
     int cur; int adapt;
-    struct Pre { T x = 0, xn = 0, kt = 0; };
-    struct Acc { T dx2 = T(0), inter = T(0); };   // per-lane sums in T, reduced in FP64
+    struct Pre {};
+    struct Acc {};
     // after begin(), the *0 members point at the current half, the *1 members at
-    // the other one (y', x' and the new K^T y')
+    // the other one (y' and the new K^T y')
     __device__ bool begin() {
         if (ctrl->skip) return false;
         cur = ctrl->cur;
         if (cur) {
             const T* t = ys0; ys0 = ys1; ys1 = t;
-            t = x0; x0 = x1; x1 = t;
             T* u = kty0; kty0 = kty1; kty1 = u;
         }
         adapt = ctrl->adaptive;
         return true;
     }
     __device__ const T* xin() const { return ys1; }   // y'
-    __device__ Pre load(int j) const {
-        Pre p;
-        if (adapt) {
-            p.x = x0[j];
-            p.xn = x1[j];
-            p.kt = kty0[j];
-        }
-        return p;
-    }
-    __device__ void row(int j, T ktyn, const Pre& p, Acc& a) const {
-        kty1[j] = ktyn;
-        if (adapt) {
-            const T dx = p.xn - p.x;
-            a.dx2 += dx * dx;
-            a.inter += dx * (ktyn - p.kt);
-        }
-    }
-    __device__ void finish(Acc& a) const {
+    __device__ Pre load(int) const { return Pre{}; }
+    __device__ void row(int j, T ktyn, const Pre&, Acc&) const { kty1[j] = ktyn; }
+    __device__ void finish(Acc&) const {
         __shared__ int last;
-        if (adapt) {
-            const double t[2] = {(double)a.dx2, (double)a.inter};
-            block_partials<2, kSpmvNT>(t, part, gridDim.x);
-        }
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) last = atomicAdd(&ctrl->tick, 1u) == gridDim.x - 1;
@@ -199,8 +191,8 @@ struct EpiPrimalT {
         __shared__ double tot[3];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (adapt && warp < 3) {
-            const double* src = warp == 0 ? partD : part + (warp - 1) * gridDim.x;
-            const int cnt = warp == 0 ? nD : (int)gridDim.x;
+            const double* src = warp == 0 ? partD : warp == 1 ? partD + nD : partP;
+            const int cnt = warp == 2 ? nP : nD;
             double v = 0.0;
             for (int i = lane; i < cnt; i += 32) v += __ldcg(src + i);
             v = warp_sum(v);
@@ -209,7 +201,7 @@ struct EpiPrimalT {
         __syncthreads();
         if (threadIdx.x == 0) {
             ctrl->tick = 0;
-            if (adapt) step_decide(ctrl, adapt, tot[0], tot[1], tot[2]);
+            if (adapt) step_decide(ctrl, adapt, tot[0], tot[2], tot[1]);
             else step_decide(ctrl, adapt, 0.0, 0.0, 0.0);
         }
     }
@@ -465,17 +457,21 @@ static inline int ew_grid(int64_t count)
 
 __global__ void k_read_clock(unsigned long long* t) { *t = global_ns(); }
 
+#ifndef PDHG_PRIMAL_GRID
+#define PDHG_PRIMAL_GRID 608   // 152 SMs x 4 blocks: one wave of the partial-reducing primal step
+#endif
 template <typename T>
 static int primal_grid(int64_t n)
 {
-    return ew_grid((n + VecTraits<T>::N - 1) / VecTraits<T>::N);
+    const int g = ew_grid((n + VecTraits<T>::N - 1) / VecTraits<T>::N);
+    return g < PDHG_PRIMAL_GRID ? g : PDHG_PRIMAL_GRID;
 }
 
 template <typename T>
 static void launch_primal(Handle* h, Engine<T>& E, cudaStream_t st)
 {
     k_primal<T><<<primal_grid<T>(h->n), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1],
-                                                       E.c, E.l, E.u, E.XS, h->n);
+                                                       E.c, E.l, E.u, E.XS, h->n, E.partT);
 }
 
 template <typename T>
@@ -489,7 +485,7 @@ static void launch_dual(Handle* h, Engine<T>& E, cudaStream_t st)
 template <typename T>
 static void launch_primal_t(Handle* h, Engine<T>& E, cudaStream_t st)
 {
-    EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.partT,
+    EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.KTY[0], E.KTY[1], E.partT, primal_grid<T>(h->n),
                      E.partD, E.gK};
     launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
 }
@@ -813,7 +809,7 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes)
                    (double)m * (7 * s + 1);
         // K^T y' + step terms: values + indices + row pointers + y'; K^T y' written;
         // x, x', K^T y read
-        bytes[2] = (double)nnz * (s + 4) + (double)(n + 1) * 8 + (double)m * s + (double)n * 4 * s;
+        bytes[2] = (double)nnz * (s + 4) + (double)(n + 1) * 8 + (double)m * s + (double)n * s;
         bytes[3] = 0.0;
     }
     return LP_OK;
