@@ -701,8 +701,8 @@ lp_status build_sched(BatchHandle* bh, SchedParams pK, SchedParams pT)
     S.ntT = (int)lT.size();
     int sms = 0;
     LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    S.gK = spmv_grid(S.ntK, sms);
-    S.gT = spmv_grid(S.ntT, sms);
+    S.gK = spmv_grid<T>(S.ntK, sms);
+    S.gT = spmv_grid<T>(S.ntT, sms);
     std::vector<int32_t> wk, pk, wt, pt;
     assign_tasks(nK, pK.cap, S.gK * kTaskWarps, wk, pk);
     assign_tasks(nT, pT.cap, S.gT * kTaskWarps, wt, pt);

@@ -662,7 +662,7 @@ lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
     for (size_t t = 0; t < bt.size(); ++t) nt[t] = h->h_trp[(size_t)bt[t]];
     int sms = 0;
     LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    const int gK = spmv_grid((int)bk.size() - 1, sms), gT = spmv_grid((int)bt.size() - 1, sms);
+    const int gK = spmv_grid<T>((int)bk.size() - 1, sms), gT = spmv_grid<T>((int)bt.size() - 1, sms);
     std::vector<int32_t> wk, pk, wt, pt;
     assign_tasks(nk, sK.cap, gK * kTaskWarps, wk, pk);
     assign_tasks(nt, sT.cap, gT * kTaskWarps, wt, pt);
@@ -730,7 +730,7 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         for (T** p : vm) LP_TRY(dev_alloc_n(h, p, (size_t)m));
         int sms = 0;
         LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-        const size_t gmax = (size_t)spmv_grid(1 << 30, sms);
+        const size_t gmax = (size_t)spmv_grid<float>(1 << 30, sms);
         LP_TRY(dev_alloc_n(h, &E.partD, 2 * gmax + 8));
         LP_TRY(dev_alloc_n(h, &E.partT, (size_t)kEWGrid + 8));
         LP_TRY(dev_alloc_n(h, &E.partR, kRowQ * (size_t)kEWGrid));

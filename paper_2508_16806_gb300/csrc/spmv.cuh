@@ -78,6 +78,11 @@ constexpr int kSpmvNT = kTaskWarps * 32;
 #define PDHG_SPMV_MIN_BLOCKS 4
 #endif
 constexpr int kSpmvMinBlocks = PDHG_SPMV_MIN_BLOCKS;   // resident blocks per SM the registers allow
+#ifndef PDHG_SPMV_MIN_BLOCKS_F64
+#define PDHG_SPMV_MIN_BLOCKS_F64 PDHG_SPMV_MIN_BLOCKS
+#endif
+template <typename T> struct MinBlocks { static constexpr int value = PDHG_SPMV_MIN_BLOCKS; };
+template <> struct MinBlocks<double> { static constexpr int value = PDHG_SPMV_MIN_BLOCKS_F64; };
 #ifndef PDHG_SPMV_CARVEOUT
 #define PDHG_SPMV_CARVEOUT -1
 #endif
@@ -88,7 +93,11 @@ constexpr int kSpmvCarveout = PDHG_SPMV_CARVEOUT;
 #define PDHG_SPMV_UNROLL 2
 #endif
 // 16-byte loads of values (and of column indices) per lane and task
+#ifndef PDHG_SPMV_UNROLL_F64
+#define PDHG_SPMV_UNROLL_F64 PDHG_SPMV_UNROLL
+#endif
 template <typename T> struct Unroll { static constexpr int value = PDHG_SPMV_UNROLL; };
+template <> struct Unroll<double> { static constexpr int value = PDHG_SPMV_UNROLL_F64; };
 // nonzeros per warp task: one pass of U vector loads per lane covers the task's
 // aligned range, whose start may sit up to VEC - 1 elements before the first nonzero
 // (PDHG_SPMV_CAP > 0 lowers it, trading nonzeros per stage for a smaller
@@ -275,7 +284,7 @@ __device__ __forceinline__ void stage_task(WarpStage<T>& W, int st, int64_t s, i
 // *err and abandons the launch's remaining work after a second bounded wait for
 // the copy in flight.
 template <typename T, class Epi, bool L1G>
-__global__ void __launch_bounds__(kSpmvNT, kSpmvMinBlocks)
+__global__ void __launch_bounds__(kSpmvNT, MinBlocks<T>::value)
 k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz, int ntasks,
        const int32_t* __restrict__ wbeg, const int32_t* __restrict__ perm,
        const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
@@ -571,11 +580,12 @@ struct EpiStore {
 #ifndef PDHG_SPMV_WAVES
 #define PDHG_SPMV_WAVES 1
 #endif
+template <typename T>
 inline int spmv_grid(int ntasks, int num_sms)
 {
     const int full = (ntasks + kTaskWarps - 1) / kTaskWarps;
     if (PDHG_SPMV_WAVES <= 0) return full > 0 ? full : 1;
-    const int wave = num_sms * kSpmvMinBlocks * PDHG_SPMV_WAVES;
+    const int wave = num_sms * MinBlocks<T>::value * PDHG_SPMV_WAVES;
     return full < wave ? (full > 0 ? full : 1) : wave;
 }
 

@@ -36,7 +36,7 @@ lp_status tune_schedule(int sms, cudaStream_t st, const RowBlockBuilder& build,
             const int nt = (int)b.size() - 1;
             std::vector<int64_t> nz(b.size());
             for (size_t t = 0; t < b.size(); ++t) nz[t] = h_rp[(size_t)b[t]];
-            const int grid = spmv_grid(nt, sms);
+            const int grid = spmv_grid<T>(nt, sms);
             std::vector<int32_t> wb, pm;
             assign_tasks(nz, caps[ci_], grid * kTaskWarps, wb, pm);
             int32_t *tb = nullptr, *wbd = nullptr, *pmd = nullptr;
