@@ -43,9 +43,12 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="powerlaw", choices=["powerlaw", "small", "batch"],
+    p.add_argument("--workload", default="powerlaw",
+                   choices=["powerlaw", "small", "dispatch", "batch", "adjoint"],
                    help="powerlaw: the 1M x 2M LP (default bench line); small: 200 x 400; "
-                        "batch: 512 LPs solved by one lp_batch_solve (extra line)")
+                        "dispatch: the 615,001 x 5,000 dispatch-shaped LP; batch: 512 LPs "
+                        "solved by one lp_batch_solve; adjoint: lp_grad of 500 unrolled "
+                        "iterations on the 100k x 200k LP (extra lines)")
     p.add_argument("--tol", type=float, default=1e-4)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -173,6 +176,10 @@ def workload(name, seed_offset=0):
     if name == "small":
         lp = synth.small_dense_lp(20250816 + seed_offset)
         return lp, "lp200x400 (100 >= / 100 = rows, 2% N(0,1) sparsity, planted optimum)"
+    if name == "dispatch":
+        lp = synth.dispatch_lp(seed=20250818 + seed_offset)
+        return lp, ("dispatch-shaped LP 615,001 x 5,000 (1 balance row, 15,000 flow rows x 41 "
+                    "contingency blocks, 10-200 coefficients per row, costs U[10,100])")
     os.makedirs(CACHE, exist_ok=True)
     path = os.path.join(CACHE, f"powerlaw_{20250817 + seed_offset}.npz")
     desc = ("powerlaw LP 1,000,000 x 2,000,000 (row lengths alpha 2.1 on 4..5000, "
@@ -324,6 +331,82 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """lp_grad (hand-written adjoint) of 500 unrolled fixed-step iterations with a
+    checkpoint every 50 on the 100,000 x 200,000 LP (20 nonzeros per row), FP32
+    with FP64 accumulation of the gradients, device buffers, CUDA events; then
+    64 instances at m = 5,000 one after another."""
+    import torch
+    from paper_2508_16806_gb300 import lp as L
+    from paper_2508_16806_gb300 import synth
+    from paper_2508_16806_gb300 import autograd as AG
+    L.load()
+    K, ckpt = 500, 50
+    lp, xt = synth.adjoint_lp()
+    prob = L.Problem(lp, device_copy=True)
+    o = L.lp_opts_default(precision=L.LP_PREC_MIXED)
+    dev = dict(device="cuda", dtype=torch.float64)
+    xK = torch.empty(lp.n, **dev)
+    yK = torch.empty(lp.m, **dev)
+    assert L.lp_unroll(prob.handle, o, K, xK.data_ptr(), yK.data_ptr(), L.LP_MEM_DEVICE) == 0
+    g = 2.0 * (xK - torch.tensor(xt, **dev))
+    dc = torch.empty(lp.n, **dev)
+    dq = torch.empty(lp.m, **dev)
+    dv = torch.empty(lp.nnz, **dev)
+
+    def one():
+        s = L.lp_grad(prob.handle, o, K, ckpt, g.data_ptr(), dc.data_ptr(), dq.data_ptr(),
+                      dv.data_ptr(), xK.data_ptr(), L.LP_MEM_DEVICE)
+        assert s == 0, s
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    s_ = 4
+    pair = 2 * lp.nnz * (s_ + 4)
+    # per unrolled step: forward, its recompute in the reverse sweep, the reverse
+    # K^T / K products (one SpMV pair each), the SDDMM for dA (row, column, FP64
+    # accumulator read and write, four gathered values) and about 20 vector
+    # values per row and column
+    per_step = 3 * pair + lp.nnz * (4 + 4 + 16 + 4 * s_) + 20 * s_ * (lp.n + lp.m)
+    t_batch = time.perf_counter()
+    for k in range(64):
+        lpk, xk = synth.adjoint_lp(5000, 10000, 20, seed=20250820 + k)
+        pk = L.Problem(lpk, device_copy=True)
+        xs, _, _ = AG.unroll(pk, K, precision=L.LP_PREC_MIXED)
+        AG.grad(pk, K, ckpt, 2.0 * (xs - xk), precision=L.LP_PREC_MIXED)
+        pk.close()
+    torch.cuda.synchronize()
+    batch_s = time.perf_counter() - t_batch
+    line = {"metric": "lp_grad time, 500 unrolled iterations (s)", "value": ms / 1e3,
+            "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "planted LP 100,000 x 200,000, 20 nonzeros per row, "
+                                   "x_target ~ U[0,1]", "K": K, "checkpoint_every": ckpt,
+                       "nnz": lp.nnz},
+            "unrolled_steps_per_s": K / (ms / 1e3),
+            "effective_gbs": per_step * K / (ms / 1e3) / 1e9,
+            "bytes_model": "per step 3 SpMV pairs (forward, recompute, reverse) + SDDMM "
+                           "nnz*(4+4+16+4s) + 20 s (n + m); working set largely L2-resident",
+            "batch_64_at_m5000_s": batch_s,
+            "batch_64_note": "64 instances one after another: generate, create, unroll, "
+                             "grad (host buffers), destroy",
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    prob.close()
+
+
 def fishnet_schedule(P):
     """Point counts of the rounds of Algorithm 7 (cull to half; repopulate back
     at odd rounds while more than two points entered the round)."""
@@ -414,6 +497,9 @@ def main():
     if args.workload == "batch" and args.impl == "ours":
         run_batch(args)
         return
+    if args.workload == "adjoint" and args.impl == "ours":
+        run_adjoint(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -478,7 +564,8 @@ def main():
     dom = rows["fp32"][dom_name]
     iter_ms = sum(r["ms"] for r in rows["fp32"].values())
     iter_bytes = sum(r["bytes"] for r in rows["fp32"].values())
-    traffic = NCU_TRAFFIC.get(dom_name)
+    # the ncu counters were taken on the power-law LP only
+    traffic = NCU_TRAFFIC.get(dom_name) if args.workload == "powerlaw" else None
     roofline = {"bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": dom["gbs"] / peak, "traffic": traffic, "kernel": dom_name,
                 "peak_source": peak_src,
@@ -526,7 +613,10 @@ def main():
                        "precision": "FP32 matrix/iterates/SpMV accumulation, FP64 reductions",
                        "step": "one lp_solve: Ruiz + power iteration + restarted adaptive PDHG "
                                "to tol (setup included)",
-                       "l2": "inputs larger than L2 (FP32 K and K^T 160 MB + vectors)",
+                       "l2": (f"inputs larger than L2 (FP32 K and K^T "
+                              f"{2 * lp.nnz * 8 / 1e6:.0f} MB + vectors)"
+                              if 2 * lp.nnz * 8 > 129e6 else
+                              "inputs smaller than L2 (launch-bound case)"),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "statuses": statuses, "iters_to_tol": iters,
             "pdhg_iters_per_s": iters / (ms / 1e3),
