@@ -53,7 +53,8 @@ class _Opts(C.Structure):
                 ("beta_artificial", C.c_double), ("eps_zero", C.c_double),
                 ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("omega0", C.c_double), ("eta0", C.c_double),
-                ("infeas_detect", C.c_int32), ("pad", C.c_int32), ("infeas_tol", C.c_double)]
+                ("infeas_detect", C.c_int32), ("pad", C.c_int32), ("infeas_tol", C.c_double),
+                ("halpern", C.c_int32), ("pad2", C.c_int32), ("reflect", C.c_double)]
 
 
 class _Info(C.Structure):
@@ -71,7 +72,7 @@ DEFAULTS = dict(tol=1e-4, max_iters=100000, check_every=64, ruiz_iters=10, ruiz_
                 pock_chambolle=0, power_iters=100, adaptive_step=1, primal_weight_update=1,
                 restarts=1, eta_scale=0.9, beta_sufficient=0.2, beta_necessary=0.8,
                 beta_artificial=0.36, eps_zero=1e-6, omega0=0.0, eta0=0.0,
-                infeas_detect=1, infeas_tol=1e-6)
+                infeas_detect=1, infeas_tol=1e-6, halpern=0, reflect=1.0)
 
 
 def _load():
@@ -100,6 +101,12 @@ def _load():
                                      C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                      P(C.c_int32)]
         _lib.orc_fishnet.restype = C.c_int
+        _lib.orc_pnorm2.argtypes = [P(_Lp)] + [C.c_void_p] * 3 + [C.c_double, C.c_double]
+        _lib.orc_pnorm2.restype = C.c_double
+        _lib.orc_halpern_step.argtypes = ([P(_Lp)] + [C.c_void_p] * 9 +
+                                          [C.c_double, C.c_double, C.c_int64, C.c_double] +
+                                          [C.c_void_p] * 4)
+        _lib.orc_halpern_step.restype = C.c_double
         _lib.orc_unrolled_forward.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_unrolled_adjoint.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
@@ -197,6 +204,26 @@ def pdhg_step(lp, x, y, tau, sigma, vals=None, c=None, q=None, l=None, u=None):
     return xn, yn
 
 
+def pnorm2(lp, dx, dy, tau, sigma, vals=None):
+    """||(dx, dy)||_P^2 = ||dx||^2 / tau + ||dy||^2 / sigma + 2 dy^T K dx."""
+    b = _Bound(lp, vals)
+    dx, dy = _f64(dx), _f64(dy)
+    return float(_load().orc_pnorm2(C.byref(b.st), _ptr(b.v), _ptr(dx), _ptr(dy), tau, sigma))
+
+
+def halpern_step(lp, x, y, xanc, yanc, tau, sigma, k, rho, vals=None, c=None, q=None, l=None,
+                 u=None):
+    """One inner step of restarted Halpern PDHG: returns (T(z), z_next, ||z - T(z)||_P)
+    with T(z) = (xh, yh) and z_next = (xn, yn)."""
+    b = _Bound(lp, vals, c, q, l, u)
+    x, y, xa, ya = _f64(x), _f64(y), _f64(xanc), _f64(yanc)
+    xh, yh, xn, yn = np.empty(lp.n), np.empty(lp.m), np.empty(lp.n), np.empty(lp.m)
+    r = _load().orc_halpern_step(C.byref(b.st), _ptr(b.v), _ptr(b.c), _ptr(b.q), _ptr(b.l),
+                                 _ptr(b.u), _ptr(x), _ptr(y), _ptr(xa), _ptr(ya), tau, sigma,
+                                 int(k), float(rho), _ptr(xh), _ptr(yh), _ptr(xn), _ptr(yn))
+    return (xh, yh), (xn, yn), float(r)
+
+
 def _opts(o, x0a=None, y0a=None):
     return _Opts(o["tol"], int(o["max_iters"]), int(o["check_every"]), int(o["ruiz_iters"]),
                  o["ruiz_tol"], int(o["pock_chambolle"]), int(o["power_iters"]),
@@ -204,11 +231,13 @@ def _opts(o, x0a=None, y0a=None):
                  o["eta_scale"], o["beta_sufficient"], o["beta_necessary"],
                  o["beta_artificial"], o["eps_zero"],
                  None if x0a is None else _ptr(x0a), None if y0a is None else _ptr(y0a),
-                 o["omega0"], o["eta0"], int(o["infeas_detect"]), 0, o["infeas_tol"])
+                 o["omega0"], o["eta0"], int(o["infeas_detect"]), 0, o["infeas_tol"],
+                 int(o["halpern"]), 0, float(o["reflect"]))
 
 
 def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
-    """Restarted PDHG.  Returns (x, y, info dict, trace list of dicts)."""
+    """Restarted PDHG (halpern=1: the restarted Halpern variant with reflection
+    ``reflect``).  Returns (x, y, info dict, trace list of dicts)."""
     o = dict(DEFAULTS)
     o.update(kw)
     b = _Bound(lp)

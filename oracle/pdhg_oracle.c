@@ -26,6 +26,10 @@
  *                             (Section 2.4.3, Algorithm 4), adaptive step
  *                             (Algorithm 5), termination (Section 2.3.2)
  *   orc_infeasibility         Algorithm 6 (infeasibility detection, Section 2.4.5)
+ *   orc_pnorm2 /
+ *   orc_halpern_step /
+ *   orc_solve_halpern         restarted (reflected) Halpern PDHG, the variant the
+ *                             Conclusion names as future work (Lu and Yang, 2024)
  *   orc_fishnet               Algorithm 7 (fishnet casting, Section 2.5)
  *   orc_unrolled_forward /
  *   orc_unrolled_adjoint      K fixed-step iterations and their exact reverse-mode
@@ -72,6 +76,9 @@ typedef struct {
     int32_t infeas_detect;    /* Algorithm 6 at every check */
     int32_t pad;
     double infeas_tol;        /* tol of Algorithm 6 */
+    int32_t halpern;          /* 1: the restarted Halpern variant (orc_solve_halpern) */
+    int32_t pad2;
+    double reflect;           /* rho in [0, 1] of the Halpern variant */
 } orc_opts;
 
 typedef struct {
@@ -434,9 +441,13 @@ static void* xalloc(int64_t count) { return calloc((size_t)(count > 0 ? count : 
  *     iterate becomes the candidate, omega is updated by Algorithm 4 (reading:
  *     ratio Delta_y / Delta_x, smoothing 1/2) and the averages are reset.
  */
+int orc_solve_halpern(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
+                      orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len);
+
 int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
               orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len)
 {
+    if (o->halpern) return orc_solve_halpern(lp, o, x_out, y_out, info, trace, trace_cap, trace_len);
     const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
     double* vs = (double*)xalloc(nnz);
     double* R = (double*)xalloc(m);
@@ -644,6 +655,216 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
     free(x); free(y); free(xn); free(yn); free(xsum); free(ysum); free(xa); free(ya);
     free(xanc); free(yanc); free(dx); free(Kdx); free(xu); free(yu);
     free(xp); free(yp); free(ddx); free(ddy); free(dlam); free(lam1); free(tmpn);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* restarted (reflected) Halpern PDHG                                  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The Conclusion names restarted Halpern PDHG (Lu and Yang, 2024) as a way to
+ * extend the solver; the paper prints no algorithm for it.  This is the
+ * published method restated on the operator of Algorithm 1.
+ *
+ * T(z), z = (x, y): one fixed-step PDHG step (orc_pdhg_step, theta = 1).  With
+ * F(z) = (c - K^T y + N_X(x), K x - q + N_Y(y)) the step satisfies
+ * 0 in F(T z) + P (T z - z) for P = [[I / tau, K^T], [K, I / sigma]], so T is
+ * firmly nonexpansive in the P-norm when tau sigma ||K||^2 < 1, and
+ * ||(dx, dy)||_P^2 = ||dx||^2 / tau + ||dy||^2 / sigma + 2 dy^T K dx.
+ */
+double orc_pnorm2(const orc_lp* lp, const double* vals, const double* dx, const double* dy,
+                  double tau, double sigma)
+{
+    const int64_t m = lp->m, n = lp->n;
+    double* Kdx = (double*)xalloc(m);
+    orc_spmv(lp, vals, dx, Kdx);
+    const double v = dot(n, dx, dx) / tau + dot(m, dy, dy) / sigma + 2.0 * dot(m, dy, Kdx);
+    free(Kdx);
+    return v;
+}
+
+/*
+ * One inner step from z = (x, y) with anchor z0 = (xanc, yanc), inner index
+ * k (0 at the anchor) and reflection rho:
+ *   (xh, yh) = T(z)
+ *   z_next = (k + 1) / (k + 2) * ((1 + rho) T(z) - rho z) + 1 / (k + 2) * z0
+ * rho = 0 is plain Halpern on T; rho = 1 is Halpern on the reflection 2T - I
+ * (nonexpansive).  Returns the fixed-point residual ||z - T(z)||_P.
+ */
+double orc_halpern_step(const orc_lp* lp, const double* vals, const double* c, const double* q,
+                        const double* l, const double* u, const double* x, const double* y,
+                        const double* xanc, const double* yanc, double tau, double sigma,
+                        int64_t k, double rho, double* xh, double* yh, double* xn, double* yn)
+{
+    const int64_t m = lp->m, n = lp->n;
+    orc_pdhg_step(lp, vals, c, q, l, u, x, y, tau, sigma, xh, yh);
+    const double lam = (double)(k + 1) / (double)(k + 2);
+    for (int64_t j = 0; j < n; ++j)
+        xn[j] = lam * ((1.0 + rho) * xh[j] - rho * x[j]) + (1.0 - lam) * xanc[j];
+    for (int64_t i = 0; i < m; ++i)
+        yn[i] = lam * ((1.0 + rho) * yh[i] - rho * y[i]) + (1.0 - lam) * yanc[i];
+    double* dx = (double*)xalloc(n);
+    double* dy = (double*)xalloc(m);
+    for (int64_t j = 0; j < n; ++j) dx[j] = xh[j] - x[j];
+    for (int64_t i = 0; i < m; ++i) dy[i] = yh[i] - y[i];
+    const double r2 = orc_pnorm2(lp, vals, dx, dy, tau, sigma);
+    free(dx);
+    free(dy);
+    return sqrt(r2 > 0.0 ? r2 : 0.0);
+}
+
+/*
+ * Restarted Halpern PDHG on the scaled problem of orc_solve (same steps 1-4:
+ * Ruiz, eta = eta_scale / ||K~||_2 kept fixed, omega, start point and anchor).
+ * adaptive_step and infeas_detect are not used (Algorithm 5 changes T from step
+ * to step; Algorithm 6 is defined on the differences of plain PDHG iterates).
+ *  - Each iteration is one orc_halpern_step; k counts them, epoch_k counts those
+ *    since the last restart (the inner index of the step).  r_0 is the residual
+ *    ||z - T(z)||_P of the first step of an epoch (at its anchor).
+ *  - The candidate of a check is T(z) of the step just taken (at the start check:
+ *    the start point).  Checks: at the start, every check_every iterations and at
+ *    max_iters; termination (Section 2.3.2) on the unscaled candidate.
+ *  - Restart criteria on the residual r of the step just taken (Lu and Yang):
+ *    r <= beta_s r_0, or r <= beta_n r_0 and r > r at the previous check of the
+ *    epoch, or epoch_k > beta_a k (the paper's artificial criterion).  At a
+ *    restart the iterate and the anchor become the candidate T(z) and omega is
+ *    updated by Algorithm 4 from the candidate's distance to the old anchor.
+ *  - Trace: kkt_cur is KKT_omega of the Halpern iterate z_next, kkt_avg and
+ *    kkt_cand that of the candidate (cand_is_avg = 1).
+ */
+int orc_solve_halpern(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
+                      orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len)
+{
+    const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
+    double* vs = (double*)xalloc(nnz);
+    double* R = (double*)xalloc(m);
+    double* C = (double*)xalloc(n);
+    double *cs = (double*)xalloc(n), *qs = (double*)xalloc(m);
+    double *ls = (double*)xalloc(n), *us = (double*)xalloc(n);
+    double *x = (double*)xalloc(n), *y = (double*)xalloc(m);
+    double *xh = (double*)xalloc(n), *yh = (double*)xalloc(m);
+    double *xn = (double*)xalloc(n), *yn = (double*)xalloc(m);
+    double *xanc = (double*)xalloc(n), *yanc = (double*)xalloc(m);
+    double *xu = (double*)xalloc(n), *yu = (double*)xalloc(m);
+    double kc[8], ka[8], kk[8];
+    int64_t tl = 0;
+
+    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, vs, R, C);
+    for (int64_t j = 0; j < n; ++j) {
+        cs[j] = C[j] * lp->c[j];
+        ls[j] = lp->l[j] / C[j];
+        us[j] = lp->u[j] / C[j];
+    }
+    for (int64_t i = 0; i < m; ++i) qs[i] = R[i] * lp->q[i];
+    const double normK = orc_power_norm(lp, vs, o->power_iters);
+    double eta = normK > 0.0 ? o->eta_scale / normK : 1.0;
+    if (o->eta0 > 0.0) eta = o->eta0;
+    const double nc = nrm2(n, cs), nq = nrm2(m, qs);
+    double omega = (nc > o->eps_zero && nq > o->eps_zero) ? nc / nq : 1.0;
+    if (o->omega0 > 0.0) omega = o->omega0;
+    for (int64_t j = 0; j < n; ++j) x[j] = clamp(o->x0 ? o->x0[j] / C[j] : 0.0, ls[j], us[j]);
+    for (int64_t i = 0; i < m; ++i) {
+        double y0 = o->y0 ? o->y0[i] / R[i] : 0.0;
+        if (lp->sense[i] && y0 < 0.0) y0 = 0.0;
+        y[i] = y0;
+    }
+    memcpy(xanc, x, sizeof(double) * (size_t)n);
+    memcpy(yanc, y, sizeof(double) * (size_t)m);
+    /* the start check's candidate is the start point */
+    memcpy(xh, x, sizeof(double) * (size_t)n);
+    memcpy(yh, y, sizeof(double) * (size_t)m);
+    memcpy(xn, x, sizeof(double) * (size_t)n);
+    memcpy(yn, y, sizeof(double) * (size_t)m);
+    int64_t k = 0, epoch_k = 0, nrestarts = 0;
+    double r = 0.0, r0 = 0.0, r_prev = INFINITY;
+    int status = 0, first = 1;
+    double rel[3] = {0, 0, 0}, pobj = 0, dobj = 0;
+
+    for (;;) {
+        if (!first) {
+            const double tau = eta / omega, sigma = eta * omega;
+            r = orc_halpern_step(lp, vs, cs, qs, ls, us, x, y, xanc, yanc, tau, sigma, epoch_k,
+                                 o->reflect, xh, yh, xn, yn);
+            if (epoch_k == 0) r0 = r;
+            ++k;
+            ++epoch_k;
+        }
+        const int do_check = first || (k % o->check_every == 0) || (k >= o->max_iters);
+        int restart = 0;
+        if (do_check) {
+            orc_kkt(lp, vs, cs, qs, ls, us, xn, yn, omega, kc);
+            orc_kkt(lp, vs, cs, qs, ls, us, xh, yh, omega, ka);
+            for (int64_t j = 0; j < n; ++j) xu[j] = C[j] * xh[j];
+            for (int64_t i = 0; i < m; ++i) yu[i] = R[i] * yh[i];
+            orc_kkt(lp, lp->vals, lp->c, lp->q, lp->l, lp->u, xu, yu, omega, kk);
+            rel[0] = kk[4]; rel[1] = kk[5]; rel[2] = kk[6];
+            pobj = kk[0]; dobj = kk[1];
+            const int converged = rel[0] <= o->tol && rel[1] <= o->tol && rel[2] <= o->tol;
+            if (!first && !converged && o->restarts) {
+                const int crit1 = r <= o->beta_sufficient * r0;
+                const int crit2 = r <= o->beta_necessary * r0 && r > r_prev;
+                const int crit3 = (double)epoch_k > o->beta_artificial * (double)k;
+                restart = crit1 || crit2 || crit3;
+            }
+            if (restart) {
+                if (o->primal_weight_update) {
+                    /* Algorithm 4 on the candidate's distance to the anchor */
+                    double ddx = 0.0, ddy = 0.0;
+                    for (int64_t j = 0; j < n; ++j) ddx += (xh[j] - xanc[j]) * (xh[j] - xanc[j]);
+                    for (int64_t i = 0; i < m; ++i) ddy += (yh[i] - yanc[i]) * (yh[i] - yanc[i]);
+                    ddx = sqrt(ddx);
+                    ddy = sqrt(ddy);
+                    if (ddx > o->eps_zero && ddy > o->eps_zero)
+                        omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(omega));
+                }
+                memcpy(xanc, xh, sizeof(double) * (size_t)n);
+                memcpy(yanc, yh, sizeof(double) * (size_t)m);
+                epoch_k = 0;
+                r_prev = INFINITY;
+                ++nrestarts;
+            } else if (!first) {
+                r_prev = r;
+            }
+            if (trace && tl < trace_cap) {
+                orc_trace* t = &trace[tl];
+                t->k = (double)k; t->attempts = (double)k; t->restart = restart;
+                t->cand_is_avg = 1; t->omega = omega; t->eta = eta;
+                t->kkt_cur = kc[7]; t->kkt_avg = ka[7];
+                t->rel_gap = rel[0]; t->rel_pres = rel[1]; t->rel_dres = rel[2];
+                t->kkt_cand = ka[7];
+            }
+            ++tl;
+            if (converged || k >= o->max_iters) {
+                memcpy(x_out, xu, sizeof(double) * (size_t)n);
+                memcpy(y_out, yu, sizeof(double) * (size_t)m);
+                status = converged ? 1 : 4;
+                break;
+            }
+            first = 0;
+        }
+        if (restart) {
+            memcpy(x, xh, sizeof(double) * (size_t)n);
+            memcpy(y, yh, sizeof(double) * (size_t)m);
+        } else {
+            memcpy(x, xn, sizeof(double) * (size_t)n);
+            memcpy(y, yn, sizeof(double) * (size_t)m);
+        }
+    }
+
+    if (info) {
+        info->status = status;
+        info->iters = k;
+        info->attempts = k;
+        info->restarts = nrestarts;
+        info->pobj = pobj; info->dobj = dobj;
+        info->rel_gap = rel[0]; info->rel_pres = rel[1]; info->rel_dres = rel[2];
+        info->omega = omega; info->eta = eta; info->norm_K = normK;
+    }
+    if (trace_len) *trace_len = tl;
+    free(vs); free(R); free(C); free(cs); free(qs); free(ls); free(us);
+    free(x); free(y); free(xh); free(yh); free(xn); free(yn); free(xanc); free(yanc);
+    free(xu); free(yu);
     return status;
 }
 
