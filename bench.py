@@ -50,6 +50,11 @@ def parse():
                         "solved by one lp_batch_solve; adjoint: lp_grad of 500 unrolled "
                         "iterations on the 100k x 200k LP (extra lines)")
     p.add_argument("--tol", type=float, default=1e-4)
+    p.add_argument("--method", default="pdhg", choices=["pdhg", "halpern"],
+                   help="pdhg: the paper's restarted adaptive PDHG (the bench line); halpern: "
+                        "restarted reflected Halpern PDHG in the timed loop")
+    p.add_argument("--no-halpern", action="store_true",
+                   help="skip the restarted Halpern PDHG measurement (extra key)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fishnet", action="store_true",
@@ -74,14 +79,42 @@ def kernel_profile(args):
     lp, desc = workload(args.workload)
     stream = torch.cuda.Stream()
     prob = L.Problem(lp, device_copy=True, stream=stream)
-    prob.solve(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=64)
+    halp = int(args.method == "halpern")
+    prob.solve(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=64, halpern=halp)
     ms, by = prob.profile_step(L.LP_PREC_MIXED, reps=3)
-    line = {"kernel_profile": desc, "ms": ms, "bytes": by}
+    line = {"kernel_profile": desc, "method": args.method, "ms": ms, "bytes": by}
     if args.fp64_profile:
-        prob.solve(tol=args.tol, precision=L.LP_PREC_FP64, max_iters=64)
+        prob.solve(tol=args.tol, precision=L.LP_PREC_FP64, max_iters=64, halpern=halp)
         line["ms_fp64"], line["bytes_fp64"] = prob.profile_step(L.LP_PREC_FP64, reps=3)
     print(json.dumps(line), flush=True)
     prob.close()
+
+
+def halpern_leg(L, prob, stream, opts):
+    """Restarted reflected Halpern PDHG (fixed eta = 0.9 / ||K~||) on the same LP,
+    tolerance and precision: one warm-up solve (its loop graph), one timed with
+    CUDA events on the solver's stream (outside the bench line's timed region)."""
+    import torch
+    o = dict(opts, halpern=1, time_limit_s=300.0)
+    prob.solve(**dict(o, max_iters=64))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    _, _, info, _ = prob.solve(**o)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    out = {"time_to_tol_s": ev0.elapsed_time(ev1) / 1e3, "iters": int(info["iters"]),
+           "fp64_iters": int(info["fp64_iters"]), "restarts": int(info["restarts"]),
+           "status": L.STATUS[info["status"]], "reflect": 1.0, "reflect_fp32": 0.5,
+           "setup_s": info["setup_s"]}
+    # its step kernels (FP32), CUDA events on the solver's stream
+    prob.solve(**dict(o, max_iters=256))
+    ms_k, by_k = prob.profile_step(L.LP_PREC_MIXED, reps=30)
+    names = ["primal_halpern", "spmv_K_halpern_dual", "spmv_KT_step"]
+    out["kernels"] = {nm: {"ms": a, "bytes": b, "gbs": b / (a * 1e-3) / 1e9 if a > 0 else None}
+                      for nm, a, b in zip(names, ms_k, by_k)}
+    return out
 
 
 def max_over_ranks(value, world):
@@ -518,7 +551,7 @@ def main():
     stream = torch.cuda.Stream()
     prob = L.Problem(lp, device_copy=True, stream=stream)
     opts = dict(tol=args.tol, precision=L.LP_PREC_MIXED, max_iters=2_000_000,
-                loop_mode=1 if args.host_loop else 0)
+                loop_mode=1 if args.host_loop else 0, halpern=int(args.method == "halpern"))
 
     def barrier():
         if world > 1:
@@ -589,6 +622,10 @@ def main():
         e2e = {"value": min(times), "unit": "s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    halp = None
+    if not args.no_halpern and args.method == "pdhg":
+        halp = halpern_leg(L, prob, stream, opts)
+
     fish = None
     if not args.no_fishnet:
         fish = fishnet_leg(L, lp, prob, stream, opts, iters, ms / 1e3, rank)
@@ -611,8 +648,10 @@ def main():
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "nnz": lp.nnz, "tol": args.tol,
                        "precision": "FP32 matrix/iterates/SpMV accumulation, FP64 reductions",
-                       "step": "one lp_solve: Ruiz + power iteration + restarted adaptive PDHG "
-                               "to tol (setup included)",
+                       "step": ("one lp_solve: Ruiz + power iteration + restarted adaptive PDHG "
+                                "to tol (setup included)" if args.method == "pdhg" else
+                                "one lp_solve: Ruiz + power iteration + restarted reflected "
+                                "Halpern PDHG to tol (setup included)"),
                        "l2": (f"inputs larger than L2 (FP32 K and K^T "
                               f"{2 * lp.nnz * 8 / 1e6:.0f} MB + vectors)"
                               if 2 * lp.nnz * 8 > 129e6 else
@@ -633,6 +672,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fishnet": fish,
+            "halpern": halp,
         }
         print(json.dumps(line), flush=True)
     prob.close()

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define LP_ABI_VERSION 3
+#define LP_ABI_VERSION 4
 
 typedef struct lp_problem_s* lp_handle;
 
@@ -123,7 +123,22 @@ typedef struct {
                                     beat the default by 3 %); the summation order, and so the
                                     last bits of the result, then depends on that timing.
                                     0 (default): the largest tasks (the compiled defaults) */
-    int32_t reserved_opts2;      /* must be 0 */
+    int32_t halpern;             /* 1: restarted (reflected) Halpern PDHG, the variant the
+                                    Conclusion names as future work (Lu and Yang, 2024), in
+                                    place of the averaged restarts: every iteration maps
+                                    z -> (k+1)/(k+2) ((1+rho) T(z) - rho z) + 1/(k+2) z_anchor,
+                                    T one fixed-step PDHG step (eta = eta_scale / ||K~||_2,
+                                    adaptive_step ignored), k the iterations since the last
+                                    restart; the candidate of a check is T(z) of the last
+                                    iteration; restarts (to that candidate) follow the three
+                                    criteria of Section 2.4.2 on the fixed-point residual
+                                    ||z - T(z)||_P, P = [[I/tau, K~^T], [K~, I/sigma]];
+                                    Algorithm 4 at restarts; Algorithm 6 is not run.
+                                    lp_solve only: lp_solve_batch and lp_batch_solve return
+                                    LP_NOT_SUPPORTED, the other entry points ignore it.
+                                    0 (default): off */
+    double halpern_reflect;      /* rho in [0, 1] (default 1: Halpern on 2T - I); the FP32
+                                    phase of LP_PREC_MIXED uses min(rho, 1/2) */
 } lp_opts;
 
 /* One record per KKT check (the start, every check_every accepted
@@ -269,7 +284,8 @@ lp_status lp_update_values(lp_handle h, const double* vals, const double* c, con
                            const double* l, const double* u, int32_t memory_space);
 
 /* Measurement hook: runs `reps` PDHG step attempts of the given precision on
- * the state left by the last lp_solve of that precision, timing each kernel
+ * the state left by the last lp_solve of that precision (the Halpern step
+ * kernels when that solve ran lp_opts.halpern = 1), timing each kernel
  * class with CUDA events on the handle's stream.  ms_out (host, 4 doubles)
  * receives the mean milliseconds per launch of: [0] primal update,
  * [1] K x' SpMV + dual update, [2] K^T y' SpMV + step terms, [3] step control.

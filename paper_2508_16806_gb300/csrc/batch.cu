@@ -1291,6 +1291,7 @@ lp_status lp_batch_solve(lp_batch b, const lp_opts* o, lp_result* rs)
     if (!(o->tol >= 0.0) || o->max_iters < 0 || o->check_every < 1 || o->ruiz_iters < 0 ||
         o->power_iters < 0 || !(o->eta_scale > 0.0) || !(o->time_limit_s > 0.0))
         return LP_INVALID_ARGUMENT;
+    if (o->halpern) return LP_NOT_SUPPORTED;   // the batched loop runs averaged PDHG restarts
     for (int k = 0; k < b->b.meta.B; ++k)
         if (rs[k].memory_space != LP_MEM_HOST && rs[k].memory_space != LP_MEM_DEVICE)
             return LP_INVALID_ARGUMENT;

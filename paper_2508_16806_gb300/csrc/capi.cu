@@ -32,6 +32,8 @@ void free_all(Handle* h)
     h->stream = nullptr;
 }
 
+constexpr double kFp32MaxReflect = 0.5;
+
 lp_status check_opts(const lp_opts* o)
 {
     if (!o) return LP_INVALID_ARGUMENT;
@@ -43,6 +45,9 @@ lp_status check_opts(const lp_opts* o)
     if (o->infeas_detect != 0 && o->infeas_detect != 1) return LP_INVALID_ARGUMENT;
     if (o->infeas_detect && !(o->infeas_tol > 0.0)) return LP_INVALID_ARGUMENT;
     if (o->autotune != 0 && o->autotune != 1) return LP_INVALID_ARGUMENT;
+    if (o->halpern != 0 && o->halpern != 1) return LP_INVALID_ARGUMENT;
+    if (o->halpern && !(o->halpern_reflect >= 0.0 && o->halpern_reflect <= 1.0))
+        return LP_INVALID_ARGUMENT;
     return LP_OK;
 }
 
@@ -96,6 +101,8 @@ void lp_opts_default(lp_opts* o)
     o->infeas_detect = 1;
     o->infeas_tol = 1e-6;
     o->autotune = 0;
+    o->halpern = 0;
+    o->halpern_reflect = 1.0;
 }
 
 const char* lp_status_string(lp_status s)
@@ -220,6 +227,10 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
     if (o->precision == LP_PREC_MIXED) {
         lp_opts o32 = *o;
         o32.tol = std::max(o->tol, o->polish_switch_tol);
+        // FP32 Halpern iterations take rho <= 1/2: (1 + rho) T - rho I is then
+        // averaged, so FP32 rounding does not accumulate over a long epoch (with
+        // rho near 1 the FP32 iterates can stall above the hand-over tolerance)
+        o32.halpern_reflect = std::min(o->halpern_reflect, kFp32MaxReflect);
         LP_TRY(run_solve<float>(h, &o32, eta0, omega0, nullptr, nullptr, o->x0, o->y0,
                                 o->warm_memory_space, 0, 0, 0, r->trace, r->trace_cap, 0, &c));
         r->trace_len = c.trace_len;

@@ -43,6 +43,10 @@ struct Ctrl {
     double qnorm, cnorm;         // ||q||_2, ||c||_2 of the unscaled problem
     double time_limit_ns;
     double infeas_tol;   // Algorithm 6 tolerance (normalised directions)
+    // restarted Halpern variant: reflection rho, the fixed-point residual
+    // ||z - T(z)||_P of the last iteration, of the first iteration of the epoch,
+    // and of the last iteration before the previous check of the epoch
+    double reflect, fpr, fpr0, fpr_prev;
     // counters
     long long k, attempts, epoch_k, restarts, max_iters, t0_ns, trace_len, trace_cap;
     int cur;             // which half of each double buffer holds the current iterate
@@ -55,6 +59,7 @@ struct Ctrl {
     int restart;         // the last check restarted
     int adaptive, pwu, restarts_on, check_every;
     int infeas;          // Algorithm 6 at every check
+    int halpern;         // restarted Halpern iterations instead of averaged PDHG restarts
     int rejects;         // consecutive rejected attempts (a guard against a stuck loop)
     unsigned int tick;   // finished blocks of the current K^T launch (last one runs the step control)
     long long bodies;    // loop-body executions (for the launch count)
@@ -91,6 +96,7 @@ struct Engine {
     T *XA = nullptr, *YA = nullptr;      // averages
     T *KXA = nullptr, *KTYA = nullptr;   // their products
     T *XANC = nullptr, *YANC = nullptr;  // restart anchor
+    T* KXANC = nullptr;                  // K x of the anchor (Halpern iterations)
     // warp-task schedules for this precision's task capacity
     int32_t* brow = nullptr;   int nblk = 0;    // K rows: task boundaries, task count
     int32_t* bcol = nullptr;   int ntblk = 0;   // K^T rows
@@ -116,6 +122,7 @@ struct Engine {
     int graph_slots = -1;
     bool graph_conditional = false;
     int graph_host_loop = -1;
+    int graph_halpern = -1;
     cudaGraphExec_t body_exec = nullptr;   // host-loop fallback
 };
 

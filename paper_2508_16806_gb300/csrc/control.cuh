@@ -123,6 +123,7 @@ __device__ __forceinline__ bool infeas_active(const Ctrl& c)
 
 // Algorithm 5 decision (or the plain swap of a fixed step), by one thread.
 // The paper's k is read as the 1-based index of the iteration being taken.
+// Halpern iterations (fixed step) also record the fixed-point residual.
 __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, double dx2, double inter)
 {
     const double eta = ctrl->eta, omega = ctrl->omega;
@@ -143,12 +144,25 @@ __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, d
             return;
         }
     }
+    if (ctrl->halpern) {
+        // fixed-point residual of this iteration in the PDHG metric:
+        // ||(dx, dy)||_P^2 = ||dx||^2 / tau + ||dy||^2 / sigma + 2 dy^T K dx
+        const double r2 = (omega * dx2 + dy2 / omega) / eta + 2.0 * inter;
+        if (!isfinite(r2)) {
+            ctrl->status = LP_NUMERICAL_ERROR;
+            ctrl->done = 1;
+            ctrl->skip = 1;
+            return;
+        }
+        ctrl->fpr = sqrt(r2 > 0.0 ? r2 : 0.0);
+        if (ctrl->epoch_k == 0) ctrl->fpr0 = ctrl->fpr;
+    }
     ctrl->attempts += 1;
     if (accept) {
         ctrl->cur ^= 1;
         ctrl->k += 1;
         ctrl->epoch_k += 1;
-        ctrl->pend_w = eta;
+        ctrl->pend_w = ctrl->halpern ? 0.0 : eta;
         ctrl->W += eta;
         ctrl->Winv = 1.0 / ctrl->W;
         ctrl->rejects = 0;
@@ -193,9 +207,13 @@ __device__ __forceinline__ void check_decide(Ctrl* ctrl, const double* r, const 
     // average
     const double pobj_a = cc[7], dobj_a = r[6] + cc[8];
     const double gap_a = dobj_a - pobj_a;
-    const double kkt_a = ctrl->W > 0.0 ? sqrt(w * w * r[4] + cc[5] / (w * w) + gap_a * gap_a)
-                                       : INFINITY;
-    const int cand_avg = !(kkt_c < kkt_a);
+    // (Halpern iterations: the "average" slot holds T(z) of the last iteration,
+    // which is always the candidate)
+    const int halp = ctrl->halpern;
+    const double kkt_a = (halp || ctrl->W > 0.0)
+                             ? sqrt(w * w * r[4] + cc[5] / (w * w) + gap_a * gap_a)
+                             : INFINITY;
+    const int cand_avg = halp ? 1 : !(kkt_c < kkt_a);
     const double kkt_cand = cand_avg ? kkt_a : kkt_c;
     const double pobj = cand_avg ? pobj_a : pobj_c;
     const double dobj = cand_avg ? dobj_a : dobj_c;
@@ -225,10 +243,18 @@ __device__ __forceinline__ void check_decide(Ctrl* ctrl, const double* r, const 
     if (first) {
         ctrl->kkt_anchor = kkt_cand;
     } else if (!converged && !infeasible && ctrl->restarts_on) {
-        const int c1 = kkt_cand <= ctrl->beta_s * ctrl->kkt_anchor;
-        const int c2 = kkt_cand <= ctrl->beta_n * ctrl->kkt_anchor && kkt_cand > ctrl->kkt_prev;
         const int c3 = (double)ctrl->epoch_k > ctrl->beta_a * (double)ctrl->k;
-        restart = c1 || c2 || c3;
+        if (halp) {
+            // the same criteria on the fixed-point residual (restarted Halpern PDHG)
+            const double fr = ctrl->fpr, f0 = ctrl->fpr0;
+            const int c1 = fr <= ctrl->beta_s * f0;
+            const int c2 = fr <= ctrl->beta_n * f0 && fr > ctrl->fpr_prev;
+            restart = c1 || c2 || c3;
+        } else {
+            const int c1 = kkt_cand <= ctrl->beta_s * ctrl->kkt_anchor;
+            const int c2 = kkt_cand <= ctrl->beta_n * ctrl->kkt_anchor && kkt_cand > ctrl->kkt_prev;
+            restart = c1 || c2 || c3;
+        }
     }
     double omega = w;
     if (restart) {
@@ -240,12 +266,14 @@ __device__ __forceinline__ void check_decide(Ctrl* ctrl, const double* r, const 
         }
         ctrl->kkt_anchor = kkt_cand;
         ctrl->kkt_prev = INFINITY;
+        ctrl->fpr_prev = INFINITY;
         ctrl->epoch_k = 0;
         ctrl->W = 0.0;
         ctrl->Winv = 0.0;
         ctrl->restarts += 1;
     } else if (!first) {
         ctrl->kkt_prev = kkt_cand;
+        ctrl->fpr_prev = ctrl->fpr;
     }
     ctrl->omega = omega;
     ctrl->restart = restart;

@@ -726,7 +726,8 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         T** vn[] = {&E.c, &E.l, &E.u, &E.X[0], &E.X[1], &E.KTY[0], &E.KTY[1],
                     &E.XS, &E.XA, &E.KTYA, &E.XANC};
         for (T** p : vn) LP_TRY(dev_alloc_n(h, p, (size_t)n));
-        T** vm[] = {&E.q, &E.Y[0], &E.Y[1], &E.KX[0], &E.KX[1], &E.YS, &E.YA, &E.KXA, &E.YANC};
+        T** vm[] = {&E.q,  &E.Y[0], &E.Y[1], &E.KX[0], &E.KX[1],
+                    &E.YS, &E.YA,   &E.KXA,  &E.YANC,  &E.KXANC};
         for (T** p : vm) LP_TRY(dev_alloc_n(h, p, (size_t)m));
         int sms = 0;
         LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));

@@ -13,6 +13,17 @@
 // criteria and the primal-weight update (Algorithm 4).  The whole loop is a CUDA
 // graph whose body is (check_every + spare) attempt slots plus the check, inside
 // a conditional WHILE node; k_set_cond writes the loop condition on the device.
+//
+// Restarted Halpern PDHG (the variant the Conclusion names as future work; Lu
+// and Yang, 2024) runs in the same loop with its own two step kernels:
+//   k_primal_halpern        x^ = clamp(x - tau (c - K^T y), l, u) -> XA (the K launch's input),
+//                           x+ = lam ((1 + rho) x^ - rho x) + (1 - lam) x_anchor
+//   k_spmv<HalpernDual>     K x^, y^ = proj_Y(y + sigma (q - (2 K x^ - K x))),
+//                           y+ and K x+ by the same combination (K x of the anchor kept),
+//                           y^ -> YA on the iteration before a check
+//   k_spmv<PrT>             K^T y+; the last block records ||z - T(z)||_P
+// with lam = (k + 1) / (k + 2), k the iterations since the last restart.  The
+// check then evaluates T(z) = (XA, YA) in the slot of the average.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -86,6 +97,67 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
     }
 }
 
+// Halpern iteration, primal half: x^ = clamp(x - tau (c - K^T y), l, u) (the
+// primal part of T(z)) goes to xh, the input of the K x^ launch, and the next
+// iterate x+ = a x^ - b x + g x_anchor to the other half of X, with
+// a = lam (1 + rho), b = lam rho, g = 1 - lam, lam = (k + 1) / (k + 2), k the
+// iterations since the last restart.  Block partials of ||x^ - x||^2 (the
+// fixed-point residual) go to part[blockIdx.x].
+template <typename T>
+__global__ void __launch_bounds__(kEW)
+k_primal_halpern(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0,
+                 const T* __restrict__ kty1, const T* __restrict__ c, const T* __restrict__ l,
+                 const T* __restrict__ u, const T* __restrict__ xanc, T* __restrict__ xh,
+                 int64_t n, double* part)
+{
+    if (ctrl->skip) return;
+    T dx2 = T(0);
+    using VT = VecTraits<T>;
+    constexpr int VEC = VT::N;
+    const int cur = ctrl->cur;
+    const T tau = (T)(ctrl->eta / ctrl->omega);
+    const double lam = (double)(ctrl->epoch_k + 1) / (double)(ctrl->epoch_k + 2);
+    const T a = (T)(lam * (1.0 + ctrl->reflect)), b = (T)(lam * ctrl->reflect);
+    const T g = (T)(1.0 - lam);
+    const T* x = cur ? x1 : x0;
+    T* xn = cur ? x0 : x1;
+    const T* kty = cur ? kty1 : kty0;
+    const int64_t nv = n / VEC;
+    for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < nv; t += (int64_t)gridDim.x * kEW) {
+        T xj[VEC], kj[VEC], cj[VEC], lj[VEC], uj[VEC], aj[VEC], h[VEC], o[VEC];
+        VT::unpack(*reinterpret_cast<const typename VT::V*>(x + t * VEC), xj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(kty + t * VEC)), kj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(c + t * VEC)), cj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(l + t * VEC)), lj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(u + t * VEC)), uj);
+        VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(xanc + t * VEC)), aj);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            T v = xj[k] - tau * (cj[k] - kj[k]);
+            if (v < lj[k]) v = lj[k];
+            if (v > uj[k]) v = uj[k];
+            h[k] = v;
+            o[k] = a * v - b * xj[k] + g * aj[k];
+            dx2 += (v - xj[k]) * (v - xj[k]);
+        }
+        *reinterpret_cast<typename VT::V*>(xh + t * VEC) = VT::pack(h);
+        *reinterpret_cast<typename VT::V*>(xn + t * VEC) = VT::pack(o);
+    }
+    for (int64_t j = nv * VEC + (int64_t)blockIdx.x * kEW + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * kEW) {
+        const T xj = x[j];
+        T v = xj - tau * (c[j] - kty[j]);
+        const T lo = l[j], hi = u[j];
+        if (v < lo) v = lo;
+        if (v > hi) v = hi;
+        xh[j] = v;
+        xn[j] = a * v - b * xj + g * xanc[j];
+        dx2 += (v - xj) * (v - xj);
+    }
+    const double t[1] = {(double)dx2};
+    block_partials<1, kEW>(t, part, gridDim.x);
+}
+
 // K x' SpMV + dual step: y' = proj_Y(y + sigma (q - (2 K x' - K x)))
 template <typename T>
 struct EpiDual {
@@ -145,10 +217,72 @@ struct EpiDual {
     }
 };
 
+// Halpern iteration, dual half: K x^ SpMV, then
+// y^ = proj_Y(y + sigma (q - (2 K x^ - K x))), the next iterate
+// y+ = a y^ - b y + g y_anchor and its product K x+ = a K x^ - b K x + g K x_anchor
+// (linearity: no product of x+ is formed).  y^ is stored on the iteration that
+// precedes a check (its candidate T(z)).  Partials: ||y^ - y||^2 and
+// (y^ - y)^T K (x^ - x) = sum_i dy_i ((K x^)_i - (K x)_i).
+template <typename T>
+struct EpiHalpernDual {
+    PDHG_SINGLE_LP_TASK_HOOKS
+    const Ctrl* ctrl;
+    const T* xh;                    // x^ (gathered)
+    T* y0; T* y1; T* kx0; T* kx1;   // Y[0], Y[1], KX[0], KX[1]
+    const T* yanc; const T* kxanc;
+    T* yh;
+    const T* q;
+    const uint8_t* sense;
+    double* part;
+    T sigma, a, b, g; int hat;
+    // the anchor terms are read in row(): a smaller Pre keeps the SpMV's two
+    // prefetched rows per lane in registers
+    struct Pre { T y = 0, kx = 0, q = 0; uint8_t ge = 0; };
+    struct Acc { T dy2 = T(0), inter = T(0); };
+    __device__ bool begin() {
+        if (ctrl->skip) return false;
+        if (ctrl->cur) {
+            T* t = y0; y0 = y1; y1 = t;
+            t = kx0; kx0 = kx1; kx1 = t;
+        }
+        sigma = (T)(ctrl->eta * ctrl->omega);
+        const double lam = (double)(ctrl->epoch_k + 1) / (double)(ctrl->epoch_k + 2);
+        a = (T)(lam * (1.0 + ctrl->reflect));
+        b = (T)(lam * ctrl->reflect);
+        g = (T)(1.0 - lam);
+        const long long k1 = ctrl->k + 1;
+        hat = k1 % ctrl->check_every == 0 || k1 >= ctrl->max_iters;
+        return true;
+    }
+    __device__ const T* xin() const { return xh; }
+    __device__ Pre load(int i) const {
+        Pre p;
+        p.y = y0[i];
+        p.kx = kx0[i];
+        p.q = q[i];
+        p.ge = sense[i];
+        return p;
+    }
+    __device__ void row(int i, T kxh, const Pre& p, Acc& acc) const {
+        T v = p.y + sigma * (p.q - (T(2) * kxh - p.kx));
+        if (p.ge && v < T(0)) v = T(0);
+        const T d = v - p.y;
+        acc.dy2 += d * d;
+        acc.inter += d * (kxh - p.kx);
+        y1[i] = a * v - b * p.y + g * yanc[i];
+        kx1[i] = a * kxh - b * p.kx + g * kxanc[i];
+        if (hat) yh[i] = v;
+    }
+    __device__ void finish(Acc& acc) const {
+        const double t[2] = {(double)acc.dy2, (double)acc.inter};
+        block_partials<2, kSpmvNT>(t, part, gridDim.x);
+    }
+};
+
 // K^T y' SpMV; the last block to finish sums the Algorithm 5 partials of the
 // attempt (||x' - x||^2 from k_primal, ||y' - y||^2 and the interaction from the
-// K x' launch; fixed order) and takes the step decision, so the attempt needs
-// no separate control launch.  No block waits for another: the last block is
+// K x' launch; fixed order; the same terms of a Halpern iteration) and takes
+// the step decision, so the attempt needs no separate control launch.  No block waits for another: the last block is
 // the one whose ticket completes the count.
 template <typename T>
 struct EpiPrimalT {
@@ -160,7 +294,7 @@ struct EpiPrimalT {
     int nP;
     const double* partD;            // [2][nD] partials of the K x' launch
     int nD;
-    int cur; int adapt;
+    int cur; int adapt; int halp;
     struct Pre {};
     struct Acc {};
     // after begin(), the *0 members point at the current half, the *1 members at
@@ -173,6 +307,7 @@ struct EpiPrimalT {
             T* u = kty0; kty0 = kty1; kty1 = u;
         }
         adapt = ctrl->adaptive;
+        halp = ctrl->halpern;
         return true;
     }
     __device__ const T* xin() const { return ys1; }   // y'
@@ -190,7 +325,8 @@ struct EpiPrimalT {
         // lane-strided sums, then the warp's tree)
         __shared__ double tot[3];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (adapt && warp < 3) {
+        const bool sums = adapt || halp;
+        if (sums && warp < 3) {
             const double* src = warp == 0 ? partD : warp == 1 ? partD + nD : partP;
             const int cnt = warp == 2 ? nP : nD;
             double v = 0.0;
@@ -201,7 +337,7 @@ struct EpiPrimalT {
         __syncthreads();
         if (threadIdx.x == 0) {
             ctrl->tick = 0;
-            if (adapt) step_decide(ctrl, adapt, tot[0], tot[2], tot[1]);
+            if (sums) step_decide(ctrl, adapt, tot[0], tot[2], tot[1]);
             else step_decide(ctrl, adapt, 0.0, 0.0, 0.0);
         }
     }
@@ -212,6 +348,7 @@ struct EpiPrimalT {
 // Adds the pending iterate to the sums and materialises the averages.  An
 // average of points of X (resp. Y) lies in X (resp. Y); the projection applied
 // here only removes the rounding of the running sums (it matters for FP32 sums).
+// Halpern iterations have no averages: only the start check copies z to XA, YA.
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y0, const T* y1,
@@ -224,6 +361,16 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
     const T winv = (T)ctrl->Winv;
     const T* x = cur ? x1 : x0;
     const T* y = cur ? y1 : y0;
+    if (ctrl->halpern) {
+        // XA, YA hold T(z) of the last iteration; the start check takes the start point
+        if (!ctrl->first) return;
+        for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < n + m;
+             t += (int64_t)gridDim.x * kEW) {
+            if (t < n) xa[t] = x[t];
+            else ya[t - n] = y[t - n];
+        }
+        return;
+    }
     for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < n + m;
          t += (int64_t)gridDim.x * kEW) {
         if (t < n) {
@@ -340,12 +487,13 @@ k_check_ctrl(Ctrl* ctrl, const double* partR, const double* partC, int nparts,
     check_decide(ctrl, r, cc, trace);
 }
 
-// At a restart the iterate becomes the candidate and the anchor; sums reset.
+// At a restart the iterate becomes the candidate and the anchor (with its K x);
+// sums reset.
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_restart_apply(const Ctrl* __restrict__ ctrl, T* x0, T* x1, T* y0, T* y1, T* kx0, T* kx1,
                 T* kty0, T* kty1, const T* xa, const T* ya, const T* kxa, const T* ktya,
-                T* xanc, T* yanc, T* xs, T* ys, int64_t n, int64_t m)
+                T* xanc, T* yanc, T* kxanc, T* xs, T* ys, int64_t n, int64_t m)
 {
     if (!ctrl->want_check || !ctrl->restart) return;
     const int cur = ctrl->cur, avg = ctrl->cand_avg;
@@ -367,12 +515,15 @@ k_restart_apply(const Ctrl* __restrict__ ctrl, T* x0, T* x1, T* y0, T* y1, T* kx
         } else {
             const int64_t i = t - n;
             T v = y[i];
+            T kv = kx[i];
             if (avg) {
                 v = ya[i];
                 y[i] = v;
-                kx[i] = kxa[i];
+                kv = kxa[i];
+                kx[i] = kv;
             }
             yanc[i] = v;
+            kxanc[i] = kv;
             ys[i] = T(0);
         }
     }
@@ -490,12 +641,33 @@ static void launch_primal_t(Handle* h, Engine<T>& E, cudaStream_t st)
     launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
 }
 
+template <typename T>
+static void launch_primal_halpern(Handle* h, Engine<T>& E, cudaStream_t st)
+{
+    k_primal_halpern<T><<<primal_grid<T>(h->n), kEW, 0, st>>>(
+        E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c, E.l, E.u, E.XANC, E.XA, h->n, E.partT);
+}
+
+template <typename T>
+static void launch_dual_halpern(Handle* h, Engine<T>& E, cudaStream_t st)
+{
+    EpiHalpernDual<T> ed{E.ctrl, E.XA, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YANC, E.KXANC, E.YA,
+                         E.q, h->sense, E.partD};
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val,
+                   h->dev_err, h->n, ed);
+}
+
 // one step attempt: 3 launches
 template <typename T>
-static void launch_attempt(Handle* h, Engine<T>& E, cudaStream_t st)
+static void launch_attempt(Handle* h, Engine<T>& E, cudaStream_t st, bool halpern)
 {
-    launch_primal<T>(h, E, st);
-    launch_dual<T>(h, E, st);
+    if (halpern) {
+        launch_primal_halpern<T>(h, E, st);
+        launch_dual_halpern<T>(h, E, st);
+    } else {
+        launch_primal<T>(h, E, st);
+        launch_dual<T>(h, E, st);
+    }
     launch_primal_t<T>(h, E, st);
 }
 
@@ -520,15 +692,16 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
     k_check_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partR, E.partC, kEWGrid, E.trace);
     k_restart_apply<T><<<ew_grid(n + m), kEW, 0, st>>>(
         E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.KTY[0], E.KTY[1], E.XA, E.YA,
-        E.KXA, E.KTYA, E.XANC, E.YANC, E.XS, E.YS, n, m);
+        E.KXA, E.KTYA, E.XANC, E.YANC, E.KXANC, E.XS, E.YS, n, m);
     k_set_cond<<<1, 1, 0, st>>>(E.ctrl, hd, use_handle, in_body);
 }
 
 template <typename T>
-static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots, int host_loop)
+static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots, int host_loop,
+                             int halpern)
 {
     if ((E.exec || E.body_exec) && E.graph_check_every == check_every && E.graph_slots == slots &&
-        E.graph_host_loop == host_loop)
+        E.graph_host_loop == host_loop && E.graph_halpern == halpern)
         return LP_OK;
     if (E.exec) {
         cudaGraphExecDestroy(E.exec);
@@ -564,7 +737,7 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
     if (conditional) {
         LP_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal));
-        for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st);
+        for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st, halpern != 0);
         launch_check<T>(h, E, st, hd, 1, 1);
         cudaGraph_t captured = nullptr;
         LP_CUDA_TRY(cudaStreamEndCapture(st, &captured));
@@ -573,7 +746,7 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
     } else {
         cudaGraphDestroy(graph);
         LP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st);
+        for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st, halpern != 0);
         launch_check<T>(h, E, st, hd, 0, 1);
         cudaGraph_t g2 = nullptr;
         LP_CUDA_TRY(cudaStreamEndCapture(st, &g2));
@@ -584,6 +757,7 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
     E.graph_check_every = check_every;
     E.graph_slots = slots;
     E.graph_host_loop = host_loop;
+    E.graph_halpern = halpern;
     return LP_OK;
 }
 
@@ -600,6 +774,7 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     LP_CUDA_TRY((spmv_prepare<T, EpiStore<T>>()));
     LP_CUDA_TRY((spmv_prepare<T, EpiDual<T>>()));
     LP_CUDA_TRY((spmv_prepare<T, EpiPrimalT<T>>()));
+    LP_CUDA_TRY((spmv_prepare<T, EpiHalpernDual<T>>()));
     LP_TRY(engine_factors<T>(h));
     if (o->autotune) LP_TRY(tune_engine<T>(h));
     // warm start from the caller (unscaled) must be on the device
@@ -626,6 +801,8 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     EpiStore<T> e2{E.Y[0], E.KTY[0], nullptr, nullptr, nullptr};
     launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
     LP_CUDA_TRY(cudaGetLastError());
+    if (m > 0)
+        LP_CUDA_TRY(cudaMemcpyAsync(E.KXANC, E.KX[0], sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
 
     // device trace buffer
     long long cap = trace_host ? std::max<long long>(0, trace_cap_host - trace_off) : 0;
@@ -657,10 +834,14 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     c.first = 1;
     c.want_check = 1;
     c.skip = 1;
-    c.adaptive = o->adaptive_step ? 1 : 0;
+    const int halpern = o->halpern ? 1 : 0;
+    c.halpern = halpern;
+    c.reflect = o->halpern_reflect;
+    c.fpr_prev = INFINITY;
+    c.adaptive = o->adaptive_step && !halpern ? 1 : 0;
     c.pwu = o->primal_weight_update ? 1 : 0;
     c.restarts_on = o->restarts ? 1 : 0;
-    c.infeas = o->infeas_detect ? 1 : 0;
+    c.infeas = o->infeas_detect && !halpern ? 1 : 0;
     c.infeas_tol = o->infeas_tol;
     c.check_every = o->check_every;
     {
@@ -679,8 +860,8 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     LP_CUDA_TRY(cudaGetLastError());
     h->launches += 3 + 1 + 9;   // start state, its two products, the clock read, the start check
 
-    const int slots = o->check_every + (o->adaptive_step ? 4 : 0);
-    LP_TRY(build_graph<T>(h, E, o->check_every, slots, o->loop_mode == 1 ? 1 : 0));
+    const int slots = o->check_every + (c.adaptive ? 4 : 0);
+    LP_TRY(build_graph<T>(h, E, o->check_every, slots, o->loop_mode == 1 ? 1 : 0, halpern));
     if (E.graph_conditional) {
         LP_CUDA_TRY(cudaGraphLaunch(E.exec, st));
         LP_CUDA_TRY(cudaMemcpyAsync(out, E.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -777,11 +958,14 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes)
     cudaEvent_t ev[4];
     for (auto& e : ev) LP_CUDA_TRY(cudaEventCreate(&e));
     double acc[3] = {0, 0, 0};
+    const bool halp = E.graph_halpern == 1;   // the loop of the last lp_solve
     for (int r = 0; r < reps + 2; ++r) {
         cudaEventRecord(ev[0], st);
-        launch_primal<T>(h, E, st);
+        if (halp) launch_primal_halpern<T>(h, E, st);
+        else launch_primal<T>(h, E, st);
         cudaEventRecord(ev[1], st);
-        launch_dual<T>(h, E, st);
+        if (halp) launch_dual_halpern<T>(h, E, st);
+        else launch_dual<T>(h, E, st);
         cudaEventRecord(ev[2], st);
         launch_primal_t<T>(h, E, st);
         cudaEventRecord(ev[3], st);
@@ -802,9 +986,11 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes)
     if (bytes) {
         const double s = sizeof(T);
         // primal: read x, c, l, u, K^T y, x-sum; write x', x-sum
+        // (Halpern: read x, c, l, u, K^T y, x-anchor; write x^, x+: the same count)
         bytes[0] = (double)n * 8 * s;
         // K x' + dual: values + indices + row pointers (int64) + x' (each element
         // gathered at least once) + y, q, K x, y-sum, sense read; y', K x', y-sum written
+        // (Halpern: y, q, K x, y-anchor, K x-anchor, sense read; y+, K x+ written)
         bytes[1] = (double)nnz * (s + 4) + (double)(m + 1) * 8 + (double)n * s +
                    (double)m * (7 * s + 1);
         // K^T y' + step terms: values + indices + row pointers + y'; K^T y' written;

@@ -53,7 +53,7 @@ class LpOpts(C.Structure):
                 ("warm_memory_space", C.c_int32), ("loop_mode", C.c_int32),
                 ("infeas_detect", C.c_int32), ("reserved_opts", C.c_int32),
                 ("infeas_tol", C.c_double), ("autotune", C.c_int32),
-                ("reserved_opts2", C.c_int32)]
+                ("halpern", C.c_int32), ("halpern_reflect", C.c_double)]
 
 
 TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",

@@ -39,9 +39,10 @@ def test_host_only_calls_without_gpu():
     assert o.tol == 1e-4 and o.check_every == 64 and o.eta_scale == 0.9
     assert o.beta_sufficient == 0.2 and o.beta_necessary == 0.8 and o.beta_artificial == 0.36
     assert o.infeas_detect == 1 and o.infeas_tol == 1e-6 and o.autotune == 0
+    assert o.halpern == 0 and o.halpern_reflect == 1.0
     assert L.lp_status_string(1) == "LP_OPTIMAL"
     assert L.lp_status_string(-1) == "LP_INVALID_ARGUMENT"
-    assert L.load().lp_abi_version() == 3
+    assert L.load().lp_abi_version() == 4
 
 
 def test_binding_mirrors_struct_sizes():
@@ -53,8 +54,9 @@ def test_binding_mirrors_struct_sizes():
 #include <stddef.h>
 #include "lp.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(lp_desc), sizeof(lp_opts), sizeof(lp_result),
-         sizeof(lp_trace_rec), offsetof(lp_result, x), offsetof(lp_opts, x0));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(lp_desc), sizeof(lp_opts), sizeof(lp_result),
+         sizeof(lp_trace_rec), offsetof(lp_result, x), offsetof(lp_opts, x0),
+         offsetof(lp_opts, halpern_reflect));
   return 0;
 }
 '''
@@ -65,5 +67,6 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         got = [int(t) for t in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(L.LpDesc), ctypes.sizeof(L.LpOpts), ctypes.sizeof(L.LpResult),
-            ctypes.sizeof(L.LpTraceRec), L.LpResult.x.offset, L.LpOpts.x0.offset]
+            ctypes.sizeof(L.LpTraceRec), L.LpResult.x.offset, L.LpOpts.x0.offset,
+            L.LpOpts.halpern_reflect.offset]
     assert got == want
