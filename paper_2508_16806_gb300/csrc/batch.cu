@@ -228,8 +228,8 @@ struct EpiBDual {
     __device__ void task_start(int t) {
         const Ctrl& c = ctrl[task_lp[t]];
         cur = c.cur;
-        sigma = (T)(c.eta * c.omega);
-        pw = (T)c.pend_w;
+        sigma = step_scalars<T>(c).sigma;
+        pw = step_scalars<T>(c).pw;
         adapt = c.adaptive;
     }
     __device__ Pre load(int i) const {
@@ -318,8 +318,9 @@ kb_primal(const Ctrl* __restrict__ ctrl, const int32_t* __restrict__ lp_col, T* 
         const Ctrl& C = ctrl[lp_col[j]];
         if (C.skip) continue;
         const int cur = C.cur;
-        const T tau = (T)(C.eta / C.omega);
-        const T pw = (T)C.pend_w;
+        const StepScalars<T>& sc = step_scalars<T>(C);
+        const T tau = sc.tau;
+        const T pw = sc.pw;
         const T xj = (cur ? x1 : x0)[j];
         if (pw != T(0)) xs[j] += pw * xj;
         T v = xj - tau * (c[j] - (cur ? kty1 : kty0)[j]);
@@ -377,10 +378,10 @@ kb_check_prep(const Ctrl* __restrict__ ctrl, const int32_t* lp_row, const int32_
         if (t < n) {
             const Ctrl& C = ctrl[lp_col[t]];
             if (!C.want_check) continue;
-            const T pw = (T)C.pend_w;
+            const T pw = step_scalars<T>(C).pw;
             T s = xs[t];
             if (pw != T(0)) { s += pw * (C.cur ? x1 : x0)[t]; xs[t] = s; }
-            T a = s * (T)C.Winv;
+            T a = s * step_scalars<T>(C).winv;
             if (a < l[t]) a = l[t];
             if (a > u[t]) a = u[t];
             xa[t] = a;
@@ -388,10 +389,10 @@ kb_check_prep(const Ctrl* __restrict__ ctrl, const int32_t* lp_row, const int32_
             const int64_t i = t - n;
             const Ctrl& C = ctrl[lp_row[i]];
             if (!C.want_check) continue;
-            const T pw = (T)C.pend_w;
+            const T pw = step_scalars<T>(C).pw;
             T s = ys[i];
             if (pw != T(0)) { s += pw * (C.cur ? y1 : y0)[i]; ys[i] = s; }
-            T a = s * (T)C.Winv;
+            T a = s * step_scalars<T>(C).winv;
             if (sense[i] && a < T(0)) a = T(0);
             ya[i] = a;
         }
@@ -558,6 +559,7 @@ __global__ void kb_init_ctrl(Ctrl* ctrl, int B, const double* normK, const doubl
         c.qnorm = qn[k];
         c.cnorm = cn[k];
         c.t0_ns = (long long)t0;
+        refresh_scalars(c);
         ctrl[k] = c;
     }
 }

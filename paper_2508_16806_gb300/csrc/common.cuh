@@ -28,6 +28,14 @@ constexpr int kRunning = -100;
 // --------------------------------------------------------------- control block
 // One per handle and precision, in device memory.  Written only by
 // single-thread sections of control kernels, read by all kernels of a step.
+// Step scalars of one control block in one precision: tau = eta / omega,
+// sigma = eta * omega, the pending averaging weight, 1 / W and the Halpern
+// weights lam (1 + rho), lam rho, 1 - lam with lam = (k + 1) / (k + 2).
+template <typename T>
+struct StepScalars {
+    T tau, sigma, pw, winv, ha, hb, hg;
+};
+
 struct Ctrl {
     // step state
     double eta, omega;
@@ -64,7 +72,36 @@ struct Ctrl {
     unsigned int tick;   // finished blocks of the current K^T launch (last one runs the step control)
     long long bodies;    // loop-body executions (for the launch count)
     long long t_done_ns; // device clock when the loop finished for this LP
+    // the step scalars, formed in FP64 once per change of eta, omega, pend_w, W or
+    // epoch_k (refresh_scalars) and read by every thread of the step and check
+    // kernels: GB300's FP64 pipe is narrow, and an FP64 division in every thread
+    // (or for every element of a batch) costs microseconds per launch
+    StepScalars<float> s32;
+    StepScalars<double> s64;
 };
+
+__host__ __device__ inline void refresh_scalars(Ctrl& c)
+{
+    const double tau = c.eta / c.omega, sigma = c.eta * c.omega;
+    const double lam = (double)(c.epoch_k + 1) / (double)(c.epoch_k + 2);
+    const double ha = lam * (1.0 + c.reflect), hb = lam * c.reflect, hg = 1.0 - lam;
+    c.s64 = StepScalars<double>{tau, sigma, c.pend_w, c.Winv, ha, hb, hg};
+    c.s32 = StepScalars<float>{(float)tau, (float)sigma, (float)c.pend_w, (float)c.Winv,
+                               (float)ha, (float)hb, (float)hg};
+}
+
+template <typename T>
+__device__ __forceinline__ const StepScalars<T>& step_scalars(const Ctrl& c);
+template <>
+__device__ __forceinline__ const StepScalars<float>& step_scalars<float>(const Ctrl& c)
+{
+    return c.s32;
+}
+template <>
+__device__ __forceinline__ const StepScalars<double>& step_scalars<double>(const Ctrl& c)
+{
+    return c.s64;
+}
 
 // ------------------------------------------------------------- device buffers
 

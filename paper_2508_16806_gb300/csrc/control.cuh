@@ -171,6 +171,7 @@ __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, d
         ctrl->rejects += 1;
     }
     ctrl->eta = eta_next;
+    refresh_scalars(*ctrl);
     if (ctrl->k % ctrl->check_every == 0 || ctrl->k >= ctrl->max_iters) {
         ctrl->want_check = 1;
         ctrl->skip = 1;
@@ -287,6 +288,7 @@ __device__ __forceinline__ void check_decide(Ctrl* ctrl, const double* r, const 
     ctrl->pobj = pobj;
     ctrl->dobj = dobj;
     ctrl->pend_w = 0.0;
+    refresh_scalars(*ctrl);
     ctrl->first = 0;
     if (trace && ctrl->trace_len < ctrl->trace_cap) {
         lp_trace_rec* t = trace + ctrl->trace_len;

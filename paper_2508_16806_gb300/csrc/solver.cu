@@ -50,8 +50,9 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
     using VT = VecTraits<T>;
     constexpr int VEC = VT::N;
     const int cur = ctrl->cur;
-    const T tau = (T)(ctrl->eta / ctrl->omega);
-    const T pw = (T)ctrl->pend_w;
+    const StepScalars<T>& sc = step_scalars<T>(*ctrl);
+    const T tau = sc.tau;
+    const T pw = sc.pw;
     const T* x = cur ? x1 : x0;
     T* xn = cur ? x0 : x1;
     const T* kty = cur ? kty1 : kty0;
@@ -115,10 +116,8 @@ k_primal_halpern(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restric
     using VT = VecTraits<T>;
     constexpr int VEC = VT::N;
     const int cur = ctrl->cur;
-    const T tau = (T)(ctrl->eta / ctrl->omega);
-    const double lam = (double)(ctrl->epoch_k + 1) / (double)(ctrl->epoch_k + 2);
-    const T a = (T)(lam * (1.0 + ctrl->reflect)), b = (T)(lam * ctrl->reflect);
-    const T g = (T)(1.0 - lam);
+    const StepScalars<T>& sc = step_scalars<T>(*ctrl);
+    const T tau = sc.tau, a = sc.ha, b = sc.hb, g = sc.hg;
     const T* x = cur ? x1 : x0;
     T* xn = cur ? x0 : x1;
     const T* kty = cur ? kty1 : kty0;
@@ -184,8 +183,9 @@ struct EpiDual {
             T* u = y0; y0 = y1; y1 = u;
             u = kx0; kx0 = kx1; kx1 = u;
         }
-        sigma = (T)(ctrl->eta * ctrl->omega);
-        pw = (T)ctrl->pend_w;
+        const StepScalars<T>& sc = step_scalars<T>(*ctrl);
+        sigma = sc.sigma;
+        pw = sc.pw;
         adapt = ctrl->adaptive;
         return true;
     }
@@ -245,11 +245,11 @@ struct EpiHalpernDual {
             T* t = y0; y0 = y1; y1 = t;
             t = kx0; kx0 = kx1; kx1 = t;
         }
-        sigma = (T)(ctrl->eta * ctrl->omega);
-        const double lam = (double)(ctrl->epoch_k + 1) / (double)(ctrl->epoch_k + 2);
-        a = (T)(lam * (1.0 + ctrl->reflect));
-        b = (T)(lam * ctrl->reflect);
-        g = (T)(1.0 - lam);
+        const StepScalars<T>& sc = step_scalars<T>(*ctrl);
+        sigma = sc.sigma;
+        a = sc.ha;
+        b = sc.hb;
+        g = sc.hg;
         const long long k1 = ctrl->k + 1;
         hat = k1 % ctrl->check_every == 0 || k1 >= ctrl->max_iters;
         return true;
@@ -357,8 +357,9 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
 {
     if (!ctrl->want_check) return;
     const int cur = ctrl->cur;
-    const T pw = (T)ctrl->pend_w;
-    const T winv = (T)ctrl->Winv;
+    const StepScalars<T>& sc = step_scalars<T>(*ctrl);
+    const T pw = sc.pw;
+    const T winv = sc.winv;
     const T* x = cur ? x1 : x0;
     const T* y = cur ? y1 : y0;
     if (ctrl->halpern) {
@@ -844,6 +845,7 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     c.infeas = o->infeas_detect && !halpern ? 1 : 0;
     c.infeas_tol = o->infeas_tol;
     c.check_every = o->check_every;
+    refresh_scalars(c);
     {
         // the time origin is the device clock read now
         unsigned long long* tns = reinterpret_cast<unsigned long long*>(h->scratch);
