@@ -66,7 +66,8 @@ class _Info(C.Structure):
 
 
 TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",
-                "kkt_cur", "kkt_avg", "rel_gap", "rel_pres", "rel_dres", "kkt_cand")
+                "kkt_cur", "kkt_avg", "rel_gap", "rel_pres", "rel_dres", "kkt_cand",
+                "fpr", "fpr0")
 
 DEFAULTS = dict(tol=1e-4, max_iters=100000, check_every=64, ruiz_iters=10, ruiz_tol=1e-4,
                 pock_chambolle=0, power_iters=100, adaptive_step=1, primal_weight_update=1,

@@ -91,10 +91,13 @@ typedef struct {
     double omega, eta, norm_K;
 } orc_info;
 
-/* One record per termination / restart check. */
+/* One record per termination / restart check.  fpr and fpr0: the Halpern
+ * variant's fixed-point residual of the last iteration and of its epoch's first
+ * iteration (0 for restarted PDHG). */
 typedef struct {
     double k, attempts, restart, cand_is_avg, omega, eta;
     double kkt_cur, kkt_avg, rel_gap, rel_pres, rel_dres, kkt_cand;
+    double fpr, fpr0;
 } orc_trace;
 
 /* ------------------------------------------------------------------ */
@@ -590,6 +593,7 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
                 t->kkt_cur = kc[7]; t->kkt_avg = kkt_avg;
                 t->rel_gap = rel[0]; t->rel_pres = rel[1]; t->rel_dres = rel[2];
                 t->kkt_cand = kkt_c;
+                t->fpr = 0.0; t->fpr0 = 0.0;
             }
             ++tl;
             if (converged || infeasible || k >= o->max_iters) {
@@ -833,6 +837,7 @@ int orc_solve_halpern(const orc_lp* lp, const orc_opts* o, double* x_out, double
                 t->kkt_cur = kc[7]; t->kkt_avg = ka[7];
                 t->rel_gap = rel[0]; t->rel_pres = rel[1]; t->rel_dres = rel[2];
                 t->kkt_cand = ka[7];
+                t->fpr = r; t->fpr0 = r0;
             }
             ++tl;
             if (converged || k >= o->max_iters) {

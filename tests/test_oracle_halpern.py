@@ -187,3 +187,32 @@ def test_restarted_halpern_matches_vertex_optimum(oracle_mod, seed):
     x, y, info, _ = oracle_mod.solve(lp, tol=1e-9, max_iters=500000, halpern=1)
     assert info["status"] == 1
     assert float(lp.c @ x) == pytest.approx(f_exact, rel=1e-6, abs=1e-7)
+
+
+@pytest.mark.parametrize("check_every", [1, 64])
+def test_halpern_restart_records_follow_the_criteria(oracle_mod, check_every):
+    """Replay of the restart decisions from the logged residuals: each check's
+    restart flag equals the three criteria (beta 0.2 / 0.8 / 0.36) on the
+    residual r of the iteration just taken, r0 of the epoch's first iteration and
+    r at the epoch's previous check; with a check after every iteration, r0 of
+    the first record of an epoch is that record's own r."""
+    lp = synth.small_dense_lp()
+    tol = 1e-8
+    _, _, info, trace = oracle_mod.solve(lp, tol=tol, max_iters=300000, halpern=1,
+                                         check_every=check_every)
+    assert info["status"] == 1
+    prev = math.inf
+    epoch_start = 0
+    for j, t in enumerate(trace[1:], start=1):
+        converged = max(t["rel_gap"], t["rel_pres"], t["rel_dres"]) <= tol
+        r, r0 = t["fpr"], t["fpr0"]
+        if check_every == 1 and t["k"] == epoch_start + 1:
+            assert r0 == r
+        expect = (not converged) and (r <= 0.2 * r0 or (r <= 0.8 * r0 and r > prev)
+                                      or (t["k"] - epoch_start) > 0.36 * t["k"])
+        assert bool(t["restart"]) == expect, (j, t)
+        if t["restart"]:
+            prev, epoch_start = math.inf, t["k"]
+        else:
+            prev = r
+    assert info["restarts"] == sum(int(t["restart"]) for t in trace) > 0
