@@ -34,7 +34,7 @@ CACHE = os.environ.get("PDHG_BENCH_CACHE", "/tmp/pdhg_bench_cache")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture of the current kernel source; None when
 # the kernel changed after the capture.  Summary: profiles/spmv_powerlaw_1Mx2M_fp32.md
-NCU_TRAFFIC = {"spmv_KT_step": 186396160, "spmv_K_dual": 200115968}
+NCU_TRAFFIC = {"spmv_KT_step": 186126336, "spmv_K_dual": 200254976}
 
 
 def parse():
