@@ -134,6 +134,7 @@ struct Engine {
     T *KXA = nullptr, *KTYA = nullptr;   // their products
     T *XANC = nullptr, *YANC = nullptr;  // restart anchor
     T* KXANC = nullptr;                  // K x of the anchor (Halpern iterations)
+    T* XH = nullptr;                     // x^ of the last Halpern iteration (K launch input)
     // warp-task schedules for this precision's task capacity
     int32_t* brow = nullptr;   int nblk = 0;    // K rows: task boundaries, task count
     int32_t* bcol = nullptr;   int ntblk = 0;   // K^T rows

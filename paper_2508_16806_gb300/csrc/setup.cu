@@ -724,7 +724,7 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         LP_CUDA_TRY(cudaMemsetAsync(E.val, 0, pad8(nnz) * sizeof(T), h->stream));
         LP_CUDA_TRY(cudaMemsetAsync(E.tval, 0, pad8(nnz) * sizeof(T), h->stream));
         T** vn[] = {&E.c, &E.l, &E.u, &E.X[0], &E.X[1], &E.KTY[0], &E.KTY[1],
-                    &E.XS, &E.XA, &E.KTYA, &E.XANC};
+                    &E.XS, &E.XA, &E.KTYA, &E.XANC, &E.XH};
         for (T** p : vn) LP_TRY(dev_alloc_n(h, p, (size_t)n));
         T** vm[] = {&E.q,  &E.Y[0], &E.Y[1], &E.KX[0], &E.KX[1],
                     &E.YS, &E.YA,   &E.KXA,  &E.YANC,  &E.KXANC};

@@ -16,8 +16,9 @@
 //
 // Restarted Halpern PDHG (the variant the Conclusion names as future work; Lu
 // and Yang, 2024) runs in the same loop with its own two step kernels:
-//   k_primal_halpern        x^ = clamp(x - tau (c - K^T y), l, u) -> XA (the K launch's input),
-//                           x+ = lam ((1 + rho) x^ - rho x) + (1 - lam) x_anchor
+//   k_primal_halpern        x^ = clamp(x - tau (c - K^T y), l, u) -> XH (the K launch's input;
+//                           also -> XA before a check), x+ = lam ((1 + rho) x^ - rho x)
+//                           + (1 - lam) x_anchor
 //   k_spmv<HalpernDual>     K x^, y^ = proj_Y(y + sigma (q - (2 K x^ - K x))),
 //                           y+ and K x+ by the same combination (K x of the anchor kept),
 //                           y^ -> YA on the iteration before a check
@@ -99,19 +100,23 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
 }
 
 // Halpern iteration, primal half: x^ = clamp(x - tau (c - K^T y), l, u) (the
-// primal part of T(z)) goes to xh, the input of the K x^ launch, and the next
-// iterate x+ = a x^ - b x + g x_anchor to the other half of X, with
-// a = lam (1 + rho), b = lam rho, g = 1 - lam, lam = (k + 1) / (k + 2), k the
-// iterations since the last restart.  Block partials of ||x^ - x||^2 (the
+// primal part of T(z)) goes to xh, the input of the K x^ launch, and on the
+// iteration before a check also to xa (the check's candidate, left untouched
+// until the next check so that a loop stopped in between returns a matching
+// pair); the next iterate x+ = a x^ - b x + g x_anchor goes to the other half of
+// X, with a = lam (1 + rho), b = lam rho, g = 1 - lam, lam = (k + 1) / (k + 2), k
+// the iterations since the last restart.  Block partials of ||x^ - x||^2 (the
 // fixed-point residual) go to part[blockIdx.x].
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_primal_halpern(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0,
                  const T* __restrict__ kty1, const T* __restrict__ c, const T* __restrict__ l,
                  const T* __restrict__ u, const T* __restrict__ xanc, T* __restrict__ xh,
-                 int64_t n, double* part)
+                 T* __restrict__ xa, int64_t n, double* part)
 {
     if (ctrl->skip) return;
+    const long long k1 = ctrl->k + 1;
+    const bool hat = k1 % ctrl->check_every == 0 || k1 >= ctrl->max_iters;
     T dx2 = T(0);
     using VT = VecTraits<T>;
     constexpr int VEC = VT::N;
@@ -140,6 +145,7 @@ k_primal_halpern(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restric
             dx2 += (v - xj[k]) * (v - xj[k]);
         }
         *reinterpret_cast<typename VT::V*>(xh + t * VEC) = VT::pack(h);
+        if (hat) *reinterpret_cast<typename VT::V*>(xa + t * VEC) = VT::pack(h);
         *reinterpret_cast<typename VT::V*>(xn + t * VEC) = VT::pack(o);
     }
     for (int64_t j = nv * VEC + (int64_t)blockIdx.x * kEW + threadIdx.x; j < n;
@@ -150,6 +156,7 @@ k_primal_halpern(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restric
         if (v < lo) v = lo;
         if (v > hi) v = hi;
         xh[j] = v;
+        if (hat) xa[j] = v;
         xn[j] = a * v - b * xj + g * xanc[j];
         dx2 += (v - xj) * (v - xj);
     }
@@ -363,7 +370,8 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
     const T* x = cur ? x1 : x0;
     const T* y = cur ? y1 : y0;
     if (ctrl->halpern) {
-        // XA, YA hold T(z) of the last iteration; the start check takes the start point
+        // XA, YA hold T(z) of the iteration before this check; the start check
+        // takes the start point
         if (!ctrl->first) return;
         for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < n + m;
              t += (int64_t)gridDim.x * kEW) {
@@ -646,13 +654,14 @@ template <typename T>
 static void launch_primal_halpern(Handle* h, Engine<T>& E, cudaStream_t st)
 {
     k_primal_halpern<T><<<primal_grid<T>(h->n), kEW, 0, st>>>(
-        E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c, E.l, E.u, E.XANC, E.XA, h->n, E.partT);
+        E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c, E.l, E.u, E.XANC, E.XH, E.XA, h->n,
+        E.partT);
 }
 
 template <typename T>
 static void launch_dual_halpern(Handle* h, Engine<T>& E, cudaStream_t st)
 {
-    EpiHalpernDual<T> ed{E.ctrl, E.XA, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YANC, E.KXANC, E.YA,
+    EpiHalpernDual<T> ed{E.ctrl, E.XH, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YANC, E.KXANC, E.YA,
                          E.q, h->sense, E.partD};
     launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val,
                    h->dev_err, h->n, ed);

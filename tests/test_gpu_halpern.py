@@ -143,6 +143,22 @@ def test_halpern_then_pdhg_on_one_handle(L, oracle_mod):
     assert rel(a[0], ao[0]) <= 1e-9 and rel(b[0], bo[0]) <= 1e-9
 
 
+def test_halpern_stop_between_checks_returns_last_candidate(L, oracle_mod):
+    """A loop stopped between two checks (by the time limit, after about two
+    thousand iterations) returns the candidate of the last check: its x and y
+    belong together, so the oracle's FP64 termination quantities of the returned
+    pair are the ones that check reported."""
+    lp = PROBS["powerlaw"]
+    prob = L.Problem(lp)
+    x, y, info, tr = prob.solve(tol=1e-14, max_iters=10**9, time_limit_s=0.05, halpern=1,
+                                trace_cap=100000)
+    assert info["status"] == L.LP_TIME_LIMIT
+    assert len(tr) > 3
+    k = oracle_mod.kkt(lp, x, y)
+    for f in ("rel_gap", "rel_pres", "rel_dres"):
+        assert k[f] == pytest.approx(info[f], rel=1e-6, abs=1e-12), (f, k[f], info[f])
+
+
 def test_halpern_options_validated(L):
     prob = L.Problem(PROBS["lp200x400"])
     for bad in (dict(halpern=2), dict(halpern=1, halpern_reflect=1.5),
