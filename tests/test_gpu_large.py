@@ -69,6 +69,21 @@ def test_batch_512_mixed_to_1e4(L, oracle_mod):
         assert max(kk["rel_gap"], kk["rel_pres"], kk["rel_dres"]) <= 1.5e-4
 
 
+def test_powerlaw_1Mx2M_halpern_mixed_to_1e4(L, oracle_mod):
+    """Restarted Halpern PDHG on C1 in the bench leg's configuration (mixed path,
+    FP32 phase with rho = 1/2): the oracle's FP64 evaluation of the returned
+    point confirms 1e-4 and the objective matches the planted optimum."""
+    lp = synth.power_law_lp()
+    prob = L.Problem(lp)
+    x, y, info, _ = prob.solve(tol=1e-4, precision=L.LP_PREC_MIXED, time_limit_s=300,
+                               halpern=1)
+    prob.close()
+    assert info["status"] == L.LP_OPTIMAL, info
+    k = oracle_mod.kkt(lp, x, y)
+    assert max(k["rel_gap"], k["rel_pres"], k["rel_dres"]) <= 1.5e-4, k
+    assert abs(float(lp.c @ x) - lp.f_star) / (1 + abs(lp.f_star)) < 1e-3
+
+
 def test_powerlaw_1Mx2M_mixed_to_1e6(L, oracle_mod):
     """C1 to the tighter tolerance: the FP32 phase hands over at 1e-5 and the
     FP64 polish finishes; the oracle's FP64 evaluation confirms 1e-6."""
