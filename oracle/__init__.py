@@ -9,10 +9,11 @@ it (plain C, -O2, no architecture flags, so it builds the same on x86-64 and
 aarch64).  Every wrapper below converts numpy arrays and calls the C function
 of the same role; see the C file for the paper passages each follows.
 
-Parity status: every function is pinned by the not-gpu tests except the
-restart / primal-weight / adaptive-step decision logic of ``solve``, which the
-paper pins only through its own rules ("parity unpinned" beyond the invariant
-that every accepted step size satisfies eta <= eta_bar).
+Parity status: every function is pinned by the not-gpu tests.  Algorithm 4
+and Algorithm 5 are pinned by hand-worked values (tests/golden/step_rules_hand.json)
+both as functions and at their call sites inside ``solve``, by the invariant
+that every accepted step size satisfies eta <= eta_bar, and by planted-mistake
+tests that compile broken copies of the oracle and check that the pins fail.
 """
 from __future__ import annotations
 
@@ -76,10 +77,10 @@ DEFAULTS = dict(tol=1e-4, max_iters=100000, check_every=64, ruiz_iters=10, ruiz_
                 infeas_detect=1, infeas_tol=1e-6, halpern=0, reflect=1.0)
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
+def _bind(lib):
+    """Declares the C signatures on a loaded oracle library."""
+    if True:
+        _lib = lib
         P = C.POINTER
         _lib.orc_spmv.argtypes = [P(_Lp), C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_spmv_t.argtypes = [P(_Lp), C.c_void_p, C.c_void_p, C.c_void_p]
@@ -113,7 +114,49 @@ def _load():
         _lib.orc_unrolled_adjoint.argtypes = [P(_Lp), C.c_double, C.c_double, C.c_int32,
                                               C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_solve_logged.argtypes = [P(_Lp), P(_Opts), C.c_void_p, C.c_void_p, P(_Info),
+                                          C.c_void_p, C.c_int64, P(C.c_int64), C.c_void_p,
+                                          C.c_int64, P(C.c_int64)]
+        _lib.orc_solve_logged.restype = C.c_int
+        _lib.orc_primal_weight.argtypes = [C.c_double] * 4
+        _lib.orc_primal_weight.restype = C.c_double
+        _lib.orc_step_rule.argtypes = [C.c_double] * 5 + [C.c_int64, P(C.c_double),
+                                                           P(C.c_double)]
+        _lib.orc_step_rule.restype = C.c_int
+    return lib
+
+
+_override = None   # a library loaded by use_library (planted-mistake tests)
+
+
+def _load():
+    global _lib
+    if _override is not None:
+        return _override
+    if _lib is None:
+        _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+class use_library:
+    """Context manager: every wrapper of this module calls the oracle library
+    at `path` (a separately compiled copy of pdhg_oracle.c) instead of the
+    default one.  The planted-mistake tests use it to run the pins against
+    deliberately broken copies of the oracle."""
+
+    def __init__(self, path):
+        self.lib = _bind(C.CDLL(path))
+
+    def __enter__(self):
+        global _override
+        self.prev = _override
+        _override = self.lib
+        return self.lib
+
+    def __exit__(self, *exc):
+        global _override
+        _override = self.prev
+        return False
 
 
 def _f64(a):
@@ -255,6 +298,51 @@ def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
     d = {f: getattr(info, f) for f, _ in _Info._fields_ if f != "pad"}
     trace = [dict(zip(TRACE_FIELDS, r.tolist())) for r in tr[: min(tl.value, trace_cap)]]
     return x, y, d, trace
+
+
+ATTEMPT_FIELDS = ("k", "eta", "eta_bar", "eta_next", "accept", "omega", "dx2", "dy2", "inter")
+
+
+def solve_logged(lp, attempt_cap=100000, trace_cap=100000, x0=None, y0=None, **kw):
+    """``solve`` plus one record per step attempt (ATTEMPT_FIELDS: accepted
+    iterations before the attempt, the eta tried, Algorithm 5's eta_bar and
+    eta', the outcome, omega and the three terms ||dx||^2, ||dy||^2, dy^T K dx on
+    the scaled problem).  Returns (x, y, info, trace, attempts)."""
+    o = dict(DEFAULTS)
+    o.update(kw)
+    b = _Bound(lp)
+    x0a = None if x0 is None else _f64(x0)
+    y0a = None if y0 is None else _f64(y0)
+    opts = _opts(o, x0a, y0a)
+    x = np.empty(lp.n)
+    y = np.empty(lp.m)
+    info = _Info()
+    tr = np.zeros((trace_cap, len(TRACE_FIELDS)))
+    tl = C.c_int64(0)
+    al = np.zeros((attempt_cap, len(ATTEMPT_FIELDS)))
+    an = C.c_int64(0)
+    _load().orc_solve_logged(C.byref(b.st), C.byref(opts), _ptr(x), _ptr(y), C.byref(info),
+                             _ptr(tr), trace_cap, C.byref(tl), _ptr(al), attempt_cap,
+                             C.byref(an))
+    d = {f: getattr(info, f) for f, _ in _Info._fields_ if f != "pad"}
+    trace = [dict(zip(TRACE_FIELDS, r.tolist())) for r in tr[: min(tl.value, trace_cap)]]
+    attempts = [dict(zip(ATTEMPT_FIELDS, r.tolist())) for r in al[: min(an.value, attempt_cap)]]
+    return x, y, d, trace, attempts
+
+
+def primal_weight(omega, dx, dy, eps_zero=1e-6):
+    """Algorithm 4: the primal weight after a restart whose anchors moved by
+    dx (primal) and dy (dual)."""
+    return float(_load().orc_primal_weight(omega, dx, dy, eps_zero))
+
+
+def step_rule(eta, omega, dx2, dy2, inter, accepted):
+    """Algorithm 5 on one attempt: (accept, eta_bar, eta')."""
+    eb = C.c_double(0.0)
+    en = C.c_double(0.0)
+    a = _load().orc_step_rule(eta, omega, dx2, dy2, inter, int(accepted), C.byref(eb),
+                              C.byref(en))
+    return bool(a), eb.value, en.value
 
 
 def fishnet(lp, P, k_steps, G, Z, **kw):

@@ -22,6 +22,8 @@
  *                             Section 2.3.2, and the KKT_omega error of Section 2.4.2
  *   orc_pdhg_step             one PDHG step, Algorithm 1 with theta = 1 in the sign
  *                             form of Appendix D (c - K^T y, q - K xbar)
+ *   orc_primal_weight         Algorithm 4 (primal weight update, Section 2.4.3)
+ *   orc_step_rule             Algorithm 5 (adaptive step size: eta_bar, eta', accept)
  *   orc_solve                 Algorithm 1 + restarts (Section 2.4.2), primal weight
  *                             (Section 2.4.3, Algorithm 4), adaptive step
  *                             (Algorithm 5), termination (Section 2.3.2)
@@ -90,6 +92,8 @@ typedef struct {
     double pobj, dobj, rel_gap, rel_pres, rel_dres;
     double omega, eta, norm_K;
 } orc_info;
+
+#define ORC_ATTEMPT_FIELDS 9
 
 /* One record per termination / restart check.  fpr and fpr0: the Halpern
  * variant's fixed-point residual of the last iteration and of its epoch's first
@@ -416,6 +420,50 @@ int orc_infeasibility(const orc_lp* lp, const double* dx, const double* dy, cons
 }
 
 /* ------------------------------------------------------------------ */
+/* Algorithm 4 and Algorithm 5 as functions of their scalar inputs     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Algorithm 4 (primal weight update at a restart, Section 2.4.3).
+ * dx = ||x_new_anchor - x_old_anchor||_2, dy = ||y_new_anchor - y_old_anchor||_2.
+ * reading: the printed ratio log(dy / dy) is garbled; the update is the
+ * log-space average (smoothing 1/2) of the old weight and dy / dx, and it is
+ * skipped when either distance is at most eps_zero.
+ */
+double orc_primal_weight(double omega, double dx, double dy, double eps_zero)
+{
+    if (dx > eps_zero && dy > eps_zero)
+        return exp(0.5 * log(dy / dx) + 0.5 * log(omega));
+    return omega;
+}
+
+/*
+ * Algorithm 5 (adaptive step size): one attempt taken with step eta and primal
+ * weight omega moved the iterate by (dx, dy); dx2 = ||dx||^2, dy2 = ||dy||^2,
+ * inter = dy^T K dx.
+ *   eta_bar  = ||(dx, dy)||_omega^2 / (2 |inter|), ||(dx, dy)||_omega^2 = omega dx2 + dy2 / omega
+ *              (+infinity when inter = 0)
+ *   eta'     = min((1 - (k + 1)^-0.3) eta_bar, (1 + (k + 1)^-0.6) eta)
+ *   accepted when eta <= eta_bar.
+ * reading: the paper's k is the 1-based index of the iteration being taken, so
+ * with `accepted` iterations done so far k = accepted + 1 and the base of the
+ * two powers is accepted + 2 (with a 0-based k the first step would get
+ * eta' = 0).  Returns 1 when the attempt is accepted; writes eta_bar and eta'.
+ */
+int orc_step_rule(double eta, double omega, double dx2, double dy2, double inter,
+                  int64_t accepted, double* eta_bar_out, double* eta_next_out)
+{
+    const double movement = omega * dx2 + dy2 / omega;
+    const double eta_bar = inter != 0.0 ? movement / (2.0 * fabs(inter)) : INFINITY;
+    const double kp1 = (double)accepted + 2.0;
+    const double e1 = (1.0 - pow(kp1, -0.3)) * eta_bar;
+    const double e2 = (1.0 + pow(kp1, -0.6)) * eta;
+    *eta_bar_out = eta_bar;
+    *eta_next_out = e1 < e2 ? e1 : e2;
+    return eta <= eta_bar;
+}
+
+/* ------------------------------------------------------------------ */
 /* the restarted, adaptive solver                                      */
 /* ------------------------------------------------------------------ */
 
@@ -447,10 +495,29 @@ static void* xalloc(int64_t count) { return calloc((size_t)(count > 0 ? count : 
 int orc_solve_halpern(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
                       orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len);
 
+/*
+ * alog (optional, alog_cap records of ORC_ATTEMPT_FIELDS doubles): one record
+ * per step attempt, [0] accepted iterations before the attempt, [1] eta tried,
+ * [2] eta_bar, [3] eta', [4] accepted (1/0), [5] omega, [6] ||dx||^2,
+ * [7] ||dy||^2, [8] dy^T K dx (NaN in [2], [6..8] for fixed steps); *alog_len
+ * receives the number of attempts (may exceed alog_cap).  Scaled problem.
+ */
+int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
+                     orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len,
+                     double* alog, int64_t alog_cap, int64_t* alog_len);
+
 int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
               orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len)
 {
+    return orc_solve_logged(lp, o, x_out, y_out, info, trace, trace_cap, trace_len, NULL, 0, NULL);
+}
+
+int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
+                     orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len,
+                     double* alog, int64_t alog_cap, int64_t* alog_len)
+{
     if (o->halpern) return orc_solve_halpern(lp, o, x_out, y_out, info, trace, trace_cap, trace_len);
+    int64_t al = 0;   /* attempts logged */
     const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
     double* vs = (double*)xalloc(nnz);
     double* R = (double*)xalloc(m);
@@ -571,8 +638,7 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
                     for (int64_t i = 0; i < m; ++i) ddy += (y[i] - yanc[i]) * (y[i] - yanc[i]);
                     ddx = sqrt(ddx);
                     ddy = sqrt(ddy);
-                    if (ddx > o->eps_zero && ddy > o->eps_zero)
-                        omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(omega));
+                    omega = orc_primal_weight(omega, ddx, ddy, o->eps_zero);
                 }
                 memcpy(xanc, x, sizeof(double) * (size_t)n);
                 memcpy(yanc, y, sizeof(double) * (size_t)m);
@@ -612,7 +678,15 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
             orc_pdhg_step(lp, vs, cs, qs, ls, us, x, y, tau, sigma, xn, yn);
             ++attempts;
             used = eta;
-            if (!o->adaptive_step) break;
+            if (!o->adaptive_step) {
+                if (alog && al < alog_cap) {
+                    double* r = alog + ORC_ATTEMPT_FIELDS * al;
+                    r[0] = (double)k; r[1] = eta; r[2] = NAN; r[3] = eta; r[4] = 1.0;
+                    r[5] = omega; r[6] = NAN; r[7] = NAN; r[8] = NAN;
+                }
+                ++al;
+                break;
+            }
             /* Algorithm 5 */
             double dx2 = 0.0, dy2 = 0.0;
             for (int64_t j = 0; j < n; ++j) { dx[j] = xn[j] - x[j]; dx2 += dx[j] * dx[j]; }
@@ -623,13 +697,14 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
                 dy2 += d * d;
                 inter += d * Kdx[i];
             }
-            double movement = omega * dx2 + dy2 / omega;   /* ||(dx, dy)||_omega^2 */
-            double eta_bar = inter != 0.0 ? movement / (2.0 * fabs(inter)) : INFINITY;
-            double kp1 = (double)(k + 1) + 1.0;            /* the paper's (k + 1), k 1-based */
-            double e1 = (1.0 - pow(kp1, -0.3)) * eta_bar;
-            double e2 = (1.0 + pow(kp1, -0.6)) * eta;
-            double eta_next = e1 < e2 ? e1 : e2;
-            int accept = eta <= eta_bar;
+            double eta_bar = 0.0, eta_next = 0.0;
+            const int accept = orc_step_rule(eta, omega, dx2, dy2, inter, k, &eta_bar, &eta_next);
+            if (alog && al < alog_cap) {
+                double* r = alog + ORC_ATTEMPT_FIELDS * al;
+                r[0] = (double)k; r[1] = eta; r[2] = eta_bar; r[3] = eta_next; r[4] = accept;
+                r[5] = omega; r[6] = dx2; r[7] = dy2; r[8] = inter;
+            }
+            ++al;
             eta = eta_next;            /* eta' is used by the next attempt either way */
             if (accept) break;
         }
@@ -654,6 +729,7 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
         info->rel_gap = rel[0]; info->rel_pres = rel[1]; info->rel_dres = rel[2];
         info->omega = omega; info->eta = eta; info->norm_K = normK;
     }
+    if (alog_len) *alog_len = al;
     if (trace_len) *trace_len = tl;
     free(vs); free(R); free(C); free(cs); free(qs); free(ls); free(us);
     free(x); free(y); free(xn); free(yn); free(xsum); free(ysum); free(xa); free(ya);
@@ -819,8 +895,7 @@ int orc_solve_halpern(const orc_lp* lp, const orc_opts* o, double* x_out, double
                     for (int64_t i = 0; i < m; ++i) ddy += (yh[i] - yanc[i]) * (yh[i] - yanc[i]);
                     ddx = sqrt(ddx);
                     ddy = sqrt(ddy);
-                    if (ddx > o->eps_zero && ddy > o->eps_zero)
-                        omega = exp(0.5 * log(ddy / ddx) + 0.5 * log(omega));
+                    omega = orc_primal_weight(omega, ddx, ddy, o->eps_zero);
                 }
                 memcpy(xanc, xh, sizeof(double) * (size_t)n);
                 memcpy(yanc, yh, sizeof(double) * (size_t)m);
