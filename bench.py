@@ -32,9 +32,14 @@ FALLBACK_HBM_GBS = 6800.0
 CACHE = os.environ.get("PDHG_BENCH_CACHE", "/tmp/pdhg_bench_cache")
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from one ncu capture of the current kernel source; None when
-# the kernel changed after the capture.  Summary: profiles/spmv_powerlaw_1Mx2M_fp32.md
-NCU_TRAFFIC = {"spmv_KT_step": 186126336, "spmv_K_dual": 200254976}
+# step kernels from one ncu capture of the current kernel source (absent when
+# the kernel changed after the capture).  Summary: profiles/spmv_powerlaw_1Mx2M_fp32.md
+NCU_TRAFFIC = {}
+
+# kernel classes of lp_profile_step: a PDHG attempt is the K-side SpMV with the
+# dual step and the Algorithm 5 decision, then the K^T-side SpMV with the fused
+# primal step (no separate primal launch); a Halpern iteration has three
+STEP_NAMES = ["primal_update", "spmv_K_dual", "spmv_KT_primal", "step_control"]
 
 
 def parse():
@@ -56,7 +61,12 @@ def parse():
     p.add_argument("--no-halpern", action="store_true",
                    help="skip the restarted Halpern PDHG measurement (extra key)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-samples", type=int, default=7,
+                   help="oracle samples of 32 iterations for the CPU baseline")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the other workloads of the default line (the dispatch-shaped "
+                        "LP, the 512-LP batch with its FP64 comparisons, lp_grad)")
     p.add_argument("--no-fishnet", action="store_true",
                    help="skip the Algorithm 7 warm-start measurement (extra key)")
     p.add_argument("--fp64-profile", action="store_true",
@@ -66,6 +76,9 @@ def parse():
                         "for kernel profilers; prints its time")
     p.add_argument("--host-loop", action="store_true",
                    help="host-driven loop graph (lp_opts.loop_mode = 1), for ncu launch lists")
+    p.add_argument("--gather-ceiling", action="store_true",
+                   help="time the minimal gather loop (lp_profile_gather) over K and K^T of "
+                        "the workload beside the step kernels (no bench line)")
     p.add_argument("--kernel-profile", action="store_true",
                    help="short run for ncu: one 64-iteration mixed solve, then 3 timed step "
                         "attempts of each kernel class (no bench line)")
@@ -86,6 +99,40 @@ def kernel_profile(args):
     if args.fp64_profile:
         prob.solve(tol=args.tol, precision=L.LP_PREC_FP64, max_iters=64, halpern=halp)
         line["ms_fp64"], line["bytes_fp64"] = prob.profile_step(L.LP_PREC_FP64, reps=3)
+    print(json.dumps(line), flush=True)
+    prob.close()
+
+
+def gather_ceiling(prob, prec, lp, reps=20):
+    """lp_profile_gather: the minimal gather loop over the nonzeros of K and of
+    K^T (milliseconds per launch, CUDA events on the solver's stream) and the
+    rate of gathers it reaches, for 4 and 8 resident blocks per SM."""
+    out = {}
+    for bps in (4, 8):
+        ms = prob.profile_gather(prec, reps=reps, blocks_per_sm=bps)
+        for side, t in zip(("K", "KT"), ms):
+            cur = out.get(side)
+            if cur is None or t < cur["ms"]:
+                out[side] = {"ms": t, "gathers_per_s": lp.nnz / (t * 1e-3),
+                             "blocks_per_sm": bps}
+    return out
+
+
+def kernel_profile_gather(args):
+    """--gather-ceiling: one mixed solve of 64 iterations (the vectors), then the
+    gather ceiling and the step kernels of both precisions (no bench line)."""
+    import torch
+    from paper_2508_16806_gb300 import lp as L
+    L.load()
+    lp, desc = workload(args.workload)
+    stream = torch.cuda.Stream()
+    prob = L.Problem(lp, device_copy=True, stream=stream)
+    line = {"gather_ceiling": desc}
+    for prec, tag in ((L.LP_PREC_MIXED, "fp32"), (L.LP_PREC_FP64, "fp64")):
+        prob.solve(tol=args.tol, precision=prec, max_iters=64)
+        line[tag] = gather_ceiling(prob, prec, lp)
+        ms, by = prob.profile_step(prec, reps=20)
+        line[tag]["step_ms"] = dict(zip(STEP_NAMES, ms))
     print(json.dumps(line), flush=True)
     prob.close()
 
@@ -111,7 +158,7 @@ def halpern_leg(L, prob, stream, opts):
     # its step kernels (FP32), CUDA events on the solver's stream
     prob.solve(**dict(o, max_iters=256))
     ms_k, by_k = prob.profile_step(L.LP_PREC_MIXED, reps=30)
-    names = ["primal_halpern", "spmv_K_halpern_dual", "spmv_KT_step"]
+    names = ["primal_halpern", "spmv_K_halpern_dual", "spmv_KT_halpern"]
     out["kernels"] = {nm: {"ms": a, "bytes": b, "gbs": b / (a * 1e-3) / 1e9 if a > 0 else None}
                       for nm, a, b in zip(names, ms_k, by_k)}
     return out
@@ -292,74 +339,138 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def oracle_estimate(lp, iters_to_tol, small_sample=False):
-    """Times the FP64 CPU oracle on a bounded sample of the workload and scales
-    it to a time-to-tolerance estimate (seconds): Ruiz (10 passes, timed in
-    full), 100 power iterations (per-iteration time from a short run), and
-    iters_to_tol PDHG iterations (per-iteration time from the difference of a
-    4- and a 12-iteration run, plus one KKT check per 64 iterations costed as
-    two iterations)."""
-    import oracle
-    oracle.build()
-    t = time.perf_counter()
-    oracle.ruiz(lp, 10, 1e-4)
-    t_ruiz = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.power_norm(lp, 1)
-    t1 = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.power_norm(lp, 3)
-    t3 = time.perf_counter() - t
-    t_pow = max(t3 - t1, 0.0) / 2
-    a, b = (4, 12)
-    t = time.perf_counter()
-    oracle.solve(lp, tol=0.0, max_iters=a, check_every=a, ruiz_iters=0, power_iters=1)
-    ta = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.solve(lp, tol=0.0, max_iters=b, check_every=b, ruiz_iters=0, power_iters=1)
-    tb = time.perf_counter() - t
-    t_iter = max(tb - ta, 1e-9) / (b - a)
-    est = t_ruiz + 100 * t_pow + iters_to_tol * t_iter * (1 + 2 / 64)
-    sample = (f"Ruiz 10 passes ({t_ruiz:.2f} s), power iteration per-step {t_pow:.3f} s x 100, "
-              f"PDHG {t_iter:.3f} s/iteration from a {a}- vs {b}-iteration run, scaled to "
-              f"{iters_to_tol} iterations (+1 check per 64 iterations)")
-    return est, t_iter, sample
+ORACLE_SAMPLE_ITERS = 32
 
 
-def reference_iterations(tol):
+class OracleTimer:
+    """Times the FP64 CPU oracle (one host core) on the workload, piece by piece.
+
+    setup(): Ruiz (10 passes of Algorithm 3), one power iteration (Algorithm 2)
+    and a run that stops at its start check (one power iteration + one KKT
+    check), each timed once.
+    sample(): one oracle run of ORACLE_SAMPLE_ITERS accepted iterations of the
+    restarted adaptive loop (no Ruiz, one power iteration, a check at the start
+    and at the end); the per-iteration time follows from it and the setup runs:
+    t_iter = (T_sample - 2 T_start + t_pow) / ORACLE_SAMPLE_ITERS, where
+    T_start = t_pow + t_check.
+    estimate(N): Ruiz + 100 power iterations + N iterations + one check per 64
+    iterations: the oracle's time to tolerance for a run of N iterations,
+    estimated from the measured pieces (the run itself takes hours)."""
+
+    def __init__(self, lp):
+        import oracle
+        oracle.build()
+        self.oracle = oracle
+        self.lp = lp
+        self.t_iter = []
+
+    def setup(self):
+        o, lp = self.oracle, self.lp
+        t = time.perf_counter()
+        o.ruiz(lp, 10, 1e-4)
+        self.t_ruiz = time.perf_counter() - t
+        t = time.perf_counter()
+        o.power_norm(lp, 1)
+        self.t_pow = time.perf_counter() - t
+        t = time.perf_counter()
+        o.solve(lp, tol=0.0, max_iters=0, check_every=64, ruiz_iters=0, power_iters=1)
+        self.t_start = time.perf_counter() - t
+        self.t_check = max(self.t_start - self.t_pow, 0.0)
+
+    def sample(self):
+        k = ORACLE_SAMPLE_ITERS
+        t = time.perf_counter()
+        self.oracle.solve(self.lp, tol=0.0, max_iters=k, check_every=k, ruiz_iters=0,
+                          power_iters=1)
+        ts = time.perf_counter() - t
+        self.t_iter.append(max(ts - 2 * self.t_start + self.t_pow, 1e-9) / k)
+        return ts
+
+    def iter_s(self):
+        return statistics.mean(self.t_iter)
+
+    def estimate(self, iters):
+        return (self.t_ruiz + 100 * self.t_pow + iters * self.iter_s() +
+                (iters / 64 + 1) * self.t_check)
+
+    def describe(self, iters, src):
+        return (f"measured on {len(self.t_iter)} oracle runs of {ORACLE_SAMPLE_ITERS} accepted "
+                f"iterations of the restarted adaptive loop ({len(self.t_iter) * ORACLE_SAMPLE_ITERS} "
+                f"iterations: {1.0 / self.iter_s():.4g} iterations/s, {self.iter_s():.4g} s each), "
+                f"one KKT check {self.t_check:.4g} s, Ruiz {self.t_ruiz:.4g} s, one power iteration "
+                f"{self.t_pow:.4g} s; the time to tolerance is estimated from these measured "
+                f"pieces x the {iters} iterations of the {src} (+ one check per 64 iterations, "
+                f"Ruiz, 100 power iterations)")
+
+
+def cpu_info():
+    out = {"nproc": os.cpu_count()}
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "cpu implementer")):
+                out.setdefault("cpu", ln.split(":", 1)[1].strip())
+        out["machine"] = os.uname().machine
+    except Exception:
+        pass
+    return out
+
+
+def reference_iterations(tol, lp):
+    """Iterations the FP64 oracle takes to tol on this LP: a stored run of the
+    oracle to tolerance (oracle/reference_runs.json, matched by nnz), or, for a
+    small LP, a run made here."""
     path = os.path.join(ROOT, "oracle", "reference_runs.json")
     try:
         for r in json.load(open(path)):
-            if abs(r["tol"] - tol) < 1e-15 and r["status"] == 1:
+            if abs(r["tol"] - tol) < 1e-15 and r["status"] == 1 and r.get("nnz") == lp.nnz:
                 return int(r["iters"]), "oracle run to tolerance (oracle/reference_runs.json)"
     except Exception:
         pass
+    if lp.nnz < 1_000_000:
+        import oracle
+        oracle.build()
+        _, _, info, _ = oracle.solve(lp, tol=tol, max_iters=2_000_000)
+        if info["status"] == 1:
+            return int(info["iters"]), "oracle run to tolerance in this process"
     return None, None
 
 
 def run_reference(args):
+    """The oracle arm: each step is one measured oracle sample of the workload
+    (OracleTimer.sample, about 7 s on the 1M x 2M LP); ms_per_step is that
+    measured time; value is the oracle's estimated time to tolerance from the
+    measured pieces (the same metric and unit as the GPU arm)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     lp, desc = workload(args.workload)
-    iters, src = reference_iterations(args.tol)
+    iters, src = reference_iterations(args.tol, lp)
     if iters is None:
         iters, src = 5000, "assumed 5000 iterations (no stored oracle run)"
-    vals = []
-    sample = ""
+    ot = OracleTimer(lp)
+    ot.setup()
+    steps = []
     for s in range(args.warmup + args.steps):
-        est, t_iter, sample = oracle_estimate(lp, iters)
+        ts = ot.sample()
         if s >= args.warmup:
-            vals.append(est)
-    v = float(statistics.mean(vals))
+            steps.append(ts)
+        else:
+            ot.t_iter.pop()
+    v = float(ot.estimate(iters))
+    sample = ot.describe(iters, src)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(steps) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": desc, "tol": args.tol, "iterations_to_tol": iters,
-                       "iterations_source": src},
+                       "iterations_source": src,
+                       "step": f"one oracle run of {ORACLE_SAMPLE_ITERS} accepted iterations "
+                               "(measured); value = estimated time to tolerance"},
+            "oracle_iters_per_s": 1.0 / ot.iter_s(),
+            "value_is_estimate": True,
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, **cpu_info()},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -438,6 +549,153 @@ def run_adjoint(args):
             "clocks": clk}
     print(json.dumps(line), flush=True)
     prob.close()
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def fp64_error(lp, x, y, info=None):
+    """The oracle's FP64 termination quantities (Section 2.3.2) of a returned
+    point, its objective against the planted optimum, and the solver's own
+    figures beside them."""
+    import oracle
+    oracle.build()
+    k = oracle.kkt(lp, x, y)
+    out = {f: k[f] for f in ("rel_gap", "rel_pres", "rel_dres")}
+    out["max"] = max(out.values())
+    if lp.x_star is not None:
+        f = lp.f_star
+        out["objective_rel_err_vs_planted"] = abs(float(lp.c @ x) - f) / (1 + abs(f))
+    if info is not None:
+        out["reported"] = {f: info[f] for f in ("rel_gap", "rel_pres", "rel_dres")}
+    return out
+
+
+def timed_solve(prob, stream, **opts):
+    """One lp_solve timed with CUDA events on the solver's stream."""
+    import torch
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    x, y, info, _ = prob.solve(**opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, x, y, info
+
+
+def dispatch_leg(L, tol):
+    """The 615,001 x 5,000 dispatch-shaped LP to tol: the mixed path and the
+    plain FP64 path (one warm-up solve each builds the loop graphs), with the
+    oracle's FP64 error of each result."""
+    import torch
+    from paper_2508_16806_gb300 import synth
+    lp = synth.dispatch_lp()
+    stream = torch.cuda.Stream()
+    prob = L.Problem(lp, device_copy=True, stream=stream)
+    out = {"workload": "dispatch-shaped LP 615,001 x 5,000 (nnz %d)" % lp.nnz}
+    for prec, tag in ((L.LP_PREC_MIXED, "mixed"), (L.LP_PREC_FP64, "fp64")):
+        prob.solve(tol=tol, precision=prec, max_iters=64)
+        t, x, y, info = timed_solve(prob, stream, tol=tol, precision=prec, max_iters=2_000_000)
+        out[tag] = {"time_to_tol_s": t, "iters": int(info["iters"]),
+                    "fp64_iters": int(info["fp64_iters"]), "status": L.STATUS[info["status"]],
+                    "fp64_error": fp64_error(lp, x, y, info)}
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["time_to_tol_s"] / out["mixed"]["time_to_tol_s"]
+    prob.close()
+    return out
+
+
+def batch_leg(L, tol):
+    """The 512 planted LPs: one lp_batch_solve (mixed, autotuned schedules) after
+    a warm-up, CUDA events; per-LP device time to tol; the same 512 LPs by the
+    batched FP64 path and by a loop of plain FP64 single solves (the north
+    star's comparison: each lp_solve timed with CUDA events, creation apart);
+    the oracle's FP64 error on a sample of 16 batch results."""
+    import torch
+    from paper_2508_16806_gb300 import synth
+    lps = synth.batch_lps()
+    batch = L.Batch(lps)
+    out = {"workload": "512 planted LPs, m log-uniform 500..50,000, n = 2m, 5-20 nnz/row",
+           "nnz": int(sum(lp.nnz for lp in lps))}
+    for prec, tag in ((L.LP_PREC_MIXED, "mixed"), (L.LP_PREC_FP64, "fp64")):
+        opts = dict(tol=tol, precision=prec, max_iters=2_000_000, autotune=1)
+        batch.solve(**opts)
+        e0, e1 = _events()
+        torch.cuda.synchronize()
+        e0.record(batch.stream)
+        res = batch.solve(**opts)
+        e1.record(batch.stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        per = sorted(info["solve_s"] for _, _, info in res)
+        out["batched_" + tag] = {
+            "time_s": t, "lps_per_s": len(lps) / t,
+            "per_lp_time_to_tol_s": {"p50": per[len(per) // 2],
+                                     "p99": per[min(len(per) - 1, int(0.99 * len(per)))]},
+            "statuses": sorted({L.STATUS[i["status"]] for _, _, i in res})}
+        if tag == "mixed":
+            rng = np.random.default_rng(0)
+            errs = [fp64_error(lps[k], res[k][0], res[k][1])["max"]
+                    for k in rng.choice(len(lps), 16, replace=False)]
+            out["batched_mixed"]["fp64_error_max_of_16"] = max(errs)
+    batch.close()
+    # plain FP64 single solves of the same LPs
+    stream = torch.cuda.Stream()
+    solve_s, wall0, statuses = [], time.perf_counter(), set()
+    for lp in lps:
+        p = L.Problem(lp, device_copy=True, stream=stream)
+        t, _, _, info = timed_solve(p, stream, tol=tol, precision=L.LP_PREC_FP64,
+                                    max_iters=2_000_000)
+        solve_s.append(t)
+        statuses.add(L.STATUS[info["status"]])
+        p.close()
+    loop = sum(solve_s)
+    out["fp64_single_solves"] = {"time_s": loop, "wall_s_with_create": time.perf_counter() - wall0,
+                                 "lps_per_s": len(lps) / loop,
+                                 "per_lp_p50_s": sorted(solve_s)[len(solve_s) // 2],
+                                 "statuses": sorted(statuses)}
+    out["batched_mixed_speedup_vs_fp64_single"] = loop / out["batched_mixed"]["time_s"]
+    return out
+
+
+def adjoint_leg(L, reps=3):
+    """lp_grad of 500 unrolled FP32 iterations (checkpoint every 50) on the
+    100,000 x 200,000 LP, device buffers, CUDA events (mean of reps after one
+    warm-up)."""
+    import torch
+    from paper_2508_16806_gb300 import synth
+    K, ckpt = 500, 50
+    lp, xt = synth.adjoint_lp()
+    prob = L.Problem(lp, device_copy=True)
+    o = L.lp_opts_default(precision=L.LP_PREC_MIXED)
+    dev = dict(device="cuda", dtype=torch.float64)
+    xK = torch.empty(lp.n, **dev)
+    yK = torch.empty(lp.m, **dev)
+    assert L.lp_unroll(prob.handle, o, K, xK.data_ptr(), yK.data_ptr(), L.LP_MEM_DEVICE) == 0
+    g = 2.0 * (xK - torch.tensor(xt, **dev))
+    dc = torch.empty(lp.n, **dev)
+    dq = torch.empty(lp.m, **dev)
+    dv = torch.empty(lp.nnz, **dev)
+
+    def one():
+        s = L.lp_grad(prob.handle, o, K, ckpt, g.data_ptr(), dc.data_ptr(), dq.data_ptr(),
+                      dv.data_ptr(), xK.data_ptr(), L.LP_MEM_DEVICE)
+        assert s == 0, s
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    prob.close()
+    return {"workload": "planted LP 100,000 x 200,000, 20 nonzeros per row, K = 500, "
+                        "checkpoint every 50, FP32", "lp_grad_s": ms / 1e3,
+            "unrolled_steps_per_s": K / (ms / 1e3), "nnz": lp.nnz}
 
 
 def fishnet_schedule(P):
@@ -527,6 +785,9 @@ def main():
     if args.kernel_profile:
         kernel_profile(args)
         return
+    if args.gather_ceiling:
+        kernel_profile_gather(args)
+        return
     if args.workload == "batch" and args.impl == "ours":
         run_batch(args)
         return
@@ -567,7 +828,7 @@ def main():
     infos = []
     ev0.record(stream)
     for _ in range(args.steps):
-        _, _, info, _ = prob.solve(**opts)
+        x_last, y_last, info, _ = prob.solve(**opts)
         infos.append(info)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -578,22 +839,29 @@ def main():
     launches = int(sum(i["kernel_launches"] for i in infos))
     statuses = sorted({L.STATUS[i["status"]] for i in infos})
 
-    # plain FP64 path on the same LP (outside the timed region)
-    t0 = time.perf_counter()
-    _, _, i64, _ = prob.solve(tol=args.tol, precision=L.LP_PREC_FP64, max_iters=2_000_000)
-    torch.cuda.synchronize()
-    fp64_s = time.perf_counter() - t0
+    # plain FP64 path on the same LP (outside the timed region; one warm-up
+    # solve of 64 iterations builds its loop graph)
+    prob.solve(tol=args.tol, precision=L.LP_PREC_FP64, max_iters=64)
+    fp64_s, x64, y64, i64 = timed_solve(prob, stream, tol=args.tol, precision=L.LP_PREC_FP64,
+                                        max_iters=2_000_000)
+    # the oracle's FP64 evaluation of both returned points (rank 0)
+    err_mixed = err_fp64 = None
+    if rank == 0:
+        err_mixed = fp64_error(lp, x_last, y_last, infos[-1])
+        err_fp64 = fp64_error(lp, x64, y64, i64)
 
     # per-kernel timing of one step attempt (CUDA events on the solver's stream)
     peak, peak_src = measured_peak()
     rows = {}
+    gather = {}
     for prec, tag in ((L.LP_PREC_MIXED, "fp32"), (L.LP_PREC_FP64, "fp64")):
         prob.solve(tol=args.tol, precision=prec, max_iters=256)
         ms_k, by_k = prob.profile_step(prec, reps=30)
-        names = ["primal_update", "spmv_K_dual", "spmv_KT_step", "step_control"]
         rows[tag] = {n: {"ms": a, "bytes": b, "gbs": (b / (a * 1e-3) / 1e9) if a > 0 else None}
-                     for n, a, b in zip(names, ms_k, by_k)}
-    dom_name = max(("spmv_K_dual", "spmv_KT_step"), key=lambda n: rows["fp32"][n]["ms"])
+                     for n, a, b in zip(STEP_NAMES, ms_k, by_k) if a > 0}
+        if args.workload == "powerlaw":
+            gather[tag] = gather_ceiling(prob, prec, lp)
+    dom_name = max(("spmv_K_dual", "spmv_KT_primal"), key=lambda n: rows["fp32"][n]["ms"])
     dom = rows["fp32"][dom_name]
     iter_ms = sum(r["ms"] for r in rows["fp32"].values())
     iter_bytes = sum(r["bytes"] for r in rows["fp32"].values())
@@ -603,6 +871,14 @@ def main():
                 "frac": dom["gbs"] / peak, "traffic": traffic, "kernel": dom_name,
                 "peak_source": peak_src,
                 "bytes_per_launch": dom["bytes"], "ms_per_launch": dom["ms"]}
+    if gather:
+        # the same kernel against the gather ceiling of its side (the minimal
+        # coalesced-load / gather / multiply-add loop over the same nonzeros)
+        side = "K" if dom_name == "spmv_K_dual" else "KT"
+        g = gather["fp32"][side]
+        roofline["gather_ceiling_ms"] = g["ms"]
+        roofline["frac_of_gather_ceiling"] = g["ms"] / dom["ms"]
+        roofline["gathers_per_s"] = lp.nnz / (dom["ms"] * 1e-3)
 
     # end to end through the C ABI with host buffers (H2D of the LP, D2H of x, y)
     e2e = None
@@ -632,13 +908,22 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ref_iters, src = reference_iterations(args.tol)
+        ref_iters, src = reference_iterations(args.tol, lp)
         if ref_iters is None:
-            ref_iters, src = int(i64["iters"]), "iterations of the GPU FP64 run"
-        est, t_iter, sample = oracle_estimate(lp, ref_iters)
-        cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": sample + f"; iteration count from the {src}",
-               "oracle_iters_per_s": 1.0 / t_iter}
+            ref_iters, src = int(i64["iters"]), "GPU FP64 run"
+        ot = OracleTimer(lp)
+        ot.setup()
+        for _ in range(args.cpu_samples):
+            ot.sample()
+        cpu = {"value": ot.estimate(ref_iters), "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": ot.describe(ref_iters, src), "value_is_estimate": True,
+               "oracle_iters_per_s": 1.0 / ot.iter_s(),
+               "oracle_iters_measured": len(ot.t_iter) * ORACLE_SAMPLE_ITERS, **cpu_info()}
+
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and args.workload == "powerlaw":
+        extra = {"dispatch": dispatch_leg(L, args.tol), "batch": batch_leg(L, args.tol),
+                 "adjoint": adjoint_leg(L)}
 
     if rank == 0:
         line = {
@@ -660,9 +945,12 @@ def main():
             "statuses": statuses, "iters_to_tol": iters,
             "pdhg_iters_per_s": iters / (ms / 1e3),
             "setup_s": statistics.mean(i["setup_s"] for i in infos),
+            "fp64_error": err_mixed,
             "fp64_plain": {"time_to_tol_s": fp64_s, "iters": int(i64["iters"]),
                            "status": L.STATUS[i64["status"]],
-                           "spmv_hbm_gbs": rows["fp64"][dom_name]["gbs"]},
+                           "spmv_hbm_gbs": rows["fp64"][dom_name]["gbs"],
+                           "fp64_error": err_fp64},
+            "mixed_speedup_vs_fp64": fp64_s / (ms / 1e3),
             "spmv_hbm_gbs": dom["gbs"],
             "kernels": rows,
             "iteration_gbs": iter_bytes / (iter_ms * 1e-3) / 1e9,
@@ -673,6 +961,7 @@ def main():
             "cpu_baseline": cpu,
             "fishnet": fish,
             "halpern": halp,
+            "workloads": extra,
         }
         print(json.dumps(line), flush=True)
     prob.close()

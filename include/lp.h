@@ -35,15 +35,15 @@
 extern "C" {
 #endif
 
-#define LP_ABI_VERSION 4
+#define LP_ABI_VERSION 5
 
 typedef struct lp_problem_s* lp_handle;
 
 typedef enum {
     LP_OK = 0,
     LP_OPTIMAL = 1,              /* all three relative errors of Section 2.3.2 <= tol */
-    LP_PRIMAL_INFEASIBLE = 2,    /* reserved: certificate of Section 2.4.5 */
-    LP_DUAL_INFEASIBLE = 3,      /* reserved: certificate of Section 2.4.5 */
+    LP_PRIMAL_INFEASIBLE = 2,    /* Algorithm 6 found a primal infeasibility certificate (Section 2.4.5) */
+    LP_DUAL_INFEASIBLE = 3,      /* Algorithm 6 found a dual infeasibility certificate (Section 2.4.5) */
     LP_ITERATION_LIMIT = 4,
     LP_TIME_LIMIT = 5,
     LP_NUMERICAL_ERROR = 6,      /* NaN / Inf met in an iterate or a reduction */
@@ -60,8 +60,12 @@ enum { LP_MEM_HOST = 0, LP_MEM_DEVICE = 1 };
  * LP_PREC_FP64: matrix, iterates and reductions in FP64.
  * LP_PREC_MIXED: matrix, iterates and SpMV accumulation in FP32, every
  *   reduction (KKT terms, step-size terms) in FP64; once the FP32 phase reaches
- *   max(tol, polish_switch_tol) the state moves to FP64 and FP64 iterations
- *   continue to tol (FP64 polish). */
+ *   max(tol, polish_switch_tol) its candidate moves to the FP64 engine, whose
+ *   check re-evaluates the three relative errors of Section 2.3.2 with FP64
+ *   products and FP64 element terms.  LP_OPTIMAL is returned only when they hold
+ *   there; otherwise (and whenever tol < polish_switch_tol) FP64 iterations
+ *   continue from the candidate to tol (FP64 polish).  lp_result.precision_used
+ *   is LP_PREC_FP64 when FP64 iterations ran. */
 enum { LP_PREC_FP64 = 0, LP_PREC_MIXED = 1 };
 
 /* The LP.  Arrays: row_ptr[m+1] (row_ptr[0] = 0, non-decreasing,
@@ -90,7 +94,13 @@ typedef struct {
     int32_t precision;           /* LP_PREC_FP64 (default) or LP_PREC_MIXED */
     int32_t check_every;         /* accepted iterations between KKT checks (default 64) */
     int32_t ruiz_iters;          /* passes of Algorithm 3 (default 10; 0 disables) */
-    int32_t pock_chambolle;      /* 1: one alpha = 1 Pock-Chambolle pass after Ruiz (default 0) */
+    int32_t pock_chambolle;      /* 0 (default): no Pock-Chambolle pass; 1: one pass with
+                                    pc_alpha after Ruiz (rows by 1/sqrt(sum_j |K~_ij|^(2-alpha)),
+                                    columns by 1/sqrt(sum_i |K~_ij|^alpha)); 2 (lp_solve only):
+                                    alpha chosen from {0, 1/2, 1, 2} by trial solves of
+                                    pc_trial_iters iterations each, the one with the smallest
+                                    relative KKT error (Section 2.3.2) at its end wins (ties: the
+                                    earlier); lp_fishnet treats 2 as 1 */
     int32_t adaptive_step;       /* 1: Algorithm 5 (default 1); 0: fixed eta */
     int32_t primal_weight_update;/* 1: Algorithm 4 at restarts (default 1) */
     int32_t restarts;            /* 1: adaptive restarts of Section 2.4.2 (default 1) */
@@ -101,7 +111,8 @@ typedef struct {
     double beta_necessary;       /* 0.8 */
     double beta_artificial;      /* 0.36 */
     double eps_zero;             /* 1e-6 */
-    double polish_switch_tol;    /* LP_PREC_MIXED: FP32 phase target (default 1e-5) */
+    double polish_switch_tol;    /* LP_PREC_MIXED: the FP32 phase runs to max(tol, this)
+                                    (default 1e-5) */
     const double* x0;            /* optional warm start (unscaled primal, length n) or NULL */
     const double* y0;            /* optional warm start (unscaled dual, length m) or NULL */
     double omega0;               /* > 0: initial primal weight instead of ||c~||/||q~|| */
@@ -139,6 +150,17 @@ typedef struct {
                                     0 (default): off */
     double halpern_reflect;      /* rho in [0, 1] (default 1: Halpern on 2T - I); the FP32
                                     phase of LP_PREC_MIXED uses min(rho, 1/2) */
+    double pc_alpha;             /* alpha in [0, 2] of the Pock-Chambolle pass (default 1) */
+    int32_t pc_trial_iters;      /* pock_chambolle = 2: accepted iterations of each trial
+                                    solve (0, the default: 2 check_every) */
+    int32_t reserved_opts2;      /* must be 0 */
+    double* attempt_log;         /* optional host buffer of attempt_cap records of 9 doubles, one
+                                    per step attempt of lp_solve (all phases, in order):
+                                    accepted iterations before the attempt, eta tried, eta_bar
+                                    of Algorithm 5 (NaN for a fixed step), eta', accepted (1/0),
+                                    omega, ||dx||^2, ||dy||^2, dy^T K dx (scaled problem; NaN
+                                    for a fixed step); NULL (default): no log */
+    int64_t attempt_cap;         /* records attempt_log holds */
 } lp_opts;
 
 /* One record per KKT check (the start, every check_every accepted
@@ -182,6 +204,8 @@ typedef struct {
     lp_trace_rec* trace;
     int64_t trace_cap;
     int64_t trace_len;           /* records produced (may exceed trace_cap) */
+    double pc_alpha_used;        /* alpha of the Pock-Chambolle pass of the solve (NaN: none) */
+    int64_t attempt_len;         /* records written to opts->attempt_log (at most attempt_cap) */
 } lp_result;
 
 /* Fills *opts with the defaults listed above.  No CUDA call. */
@@ -198,10 +222,12 @@ lp_status lp_create(const lp_desc* desc, void* cuda_stream, lp_handle* out);
 /* Restarted PDHG (Algorithm 1 with theta = 1; Ruiz scaling, Algorithm 3;
  * step size from Algorithm 2; adaptive restarts, Section 2.4.2; primal weight,
  * Algorithm 4; adaptive steps, Algorithm 5; termination, Section 2.3.2, on the
- * unscaled problem).  The iteration loop runs on the device inside a CUDA graph
- * with a device-side while condition; the host waits once at the end.
- * Returns the solver outcome (LP_OPTIMAL, LP_ITERATION_LIMIT, LP_TIME_LIMIT,
- * LP_NUMERICAL_ERROR), also stored in res->status, or a negative error. */
+ * unscaled problem; infeasibility detection, Algorithm 6, when
+ * opts->infeas_detect).  The iteration loop runs on the device inside a CUDA
+ * graph with a device-side while condition; the host waits once at the end.
+ * Returns the solver outcome (LP_OPTIMAL, LP_PRIMAL_INFEASIBLE,
+ * LP_DUAL_INFEASIBLE, LP_ITERATION_LIMIT, LP_TIME_LIMIT, LP_NUMERICAL_ERROR),
+ * also stored in res->status, or a negative error. */
 lp_status lp_solve(lp_handle h, const lp_opts* opts, lp_result* res);
 
 /* Solves count independent LPs with the same options; results[i] belongs to
@@ -294,13 +320,27 @@ lp_status lp_update_values(lp_handle h, const double* vals, const double* c, con
 lp_status lp_profile_step(lp_handle h, int32_t precision, int32_t reps, double* ms_out,
                           double* bytes_out);
 
+/* Measurement hook: the gather ceiling of the two SpMV products on this
+ * handle's scaled matrices (the products of Algorithm 1).  A minimal kernel
+ * streams the nonzeros of K (then of K^T) with coalesced 16-byte loads of values
+ * and column indices, gathers the vector entry of each nonzero (x of the last
+ * lp_solve of that precision for K, y for K^T; loads that do not allocate in L1)
+ * and multiply-adds it into a per-thread sum: the same request stream as the
+ * SpMV kernels without their row structure and epilogues.  Grid:
+ * blocks_per_sm (1..8) x the SM count, 256 threads.  ms_out (host, 2 doubles)
+ * receives the mean milliseconds per launch over `reps` launches after one
+ * warm-up: [0] K side, [1] K^T side.  Requires an lp_solve of that precision on
+ * the handle first and a problem large enough for the per-thread sums to fit
+ * the handle's scratch (LP_INVALID_ARGUMENT otherwise).  Solver state is kept. */
+lp_status lp_profile_gather(lp_handle h, int32_t precision, int32_t reps, int32_t blocks_per_sm,
+                            double* ms_out);
+
 /* Termination quantities of one primal-dual pair (x, y) of the LP in desc,
  * computed on the device WITHOUT allocating any device memory.  The paper has no
  * counterpart to this entry point; it exists for callers that cannot call
- * cudaMalloc when they check a point: code that is capturing a stream into a CUDA
- * graph, hosts that forbid device allocation after start-up (an allocation can
- * block or synchronise the device), or plugins inside an application that owns
- * all device memory.
+ * cudaMalloc when they check a point: hosts that forbid device allocation after
+ * start-up (an allocation can block or synchronise the device), or plugins
+ * inside an application that owns all device memory.
  * desc: every array in device memory (memory_space = LP_MEM_DEVICE); it is not
  * copied and not validated beforehand, but every row pointer and column index is
  * range-checked on the device (LP_INVALID_ARGUMENT if one is out of range).
@@ -308,15 +348,19 @@ lp_status lp_profile_step(lp_handle h, int32_t precision, int32_t reps, double* 
  * [0] c^T x  [1] q^T y + l^T lambda^+ + u^T lambda^-  [2] primal residual norm
  * [3] dual residual norm  [4] rel_gap  [5] rel_pres  [6] rel_dres  [7] KKT_omega
  * (the quantities of lp_result / lp_trace_rec, unscaled).  cuda_stream: a
- * cudaStream_t or NULL; the call returns after that stream finished its work.
+ * cudaStream_t or NULL; the call copies `out` to the host and returns after that
+ * stream finished its work, so it returns LP_NOT_SUPPORTED, launching nothing,
+ * when the stream is being captured.  An error already pending in the CUDA
+ * runtime when the call starts is returned as LP_CUDA_ERROR and left pending.
  * Scratch: a fixed device array of LP_KKT_NOALLOC_MAX_DOUBLES doubles (8 MiB)
  * compiled into the library, held by every GPU that loads the library until the
  * process exits; problems with m + n + 1800 > LP_KKT_NOALLOC_MAX_DOUBLES are
- * rejected with LP_INVALID_ARGUMENT.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make that first call before
- * any stream capture begins.  All calls share the array and every call
- * overwrites it (what must start at zero is cleared by each call): calls whose
- * work overlaps on the GPU race and must be serialised by the caller. */
+ * rejected with LP_INVALID_ARGUMENT.  Each call looks up the array's device
+ * address (cudaGetSymbolAddress) on the current device; the first call on a
+ * device may also load the library's device code there, so make one call at
+ * start-up.  All calls share the array and every call overwrites it (what must
+ * start at zero is cleared by each call): calls whose work overlaps on the GPU
+ * race and must be serialised by the caller. */
 #define LP_KKT_NOALLOC_MAX_DOUBLES 1048576
 lp_status lp_kkt_noalloc(const lp_desc* desc, const double* x, const double* y, double omega,
                          double* out, void* cuda_stream);

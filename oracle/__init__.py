@@ -55,7 +55,9 @@ class _Opts(C.Structure):
                 ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("omega0", C.c_double), ("eta0", C.c_double),
                 ("infeas_detect", C.c_int32), ("pad", C.c_int32), ("infeas_tol", C.c_double),
-                ("halpern", C.c_int32), ("pad2", C.c_int32), ("reflect", C.c_double)]
+                ("halpern", C.c_int32), ("pad2", C.c_int32), ("reflect", C.c_double),
+                ("pc_alpha", C.c_double), ("pc_trial_iters", C.c_int32), ("pad3", C.c_int32),
+                ("replay", C.c_void_p), ("replay_len", C.c_int64)]
 
 
 class _Info(C.Structure):
@@ -63,7 +65,8 @@ class _Info(C.Structure):
                 ("attempts", C.c_int64), ("restarts", C.c_int64),
                 ("pobj", C.c_double), ("dobj", C.c_double), ("rel_gap", C.c_double),
                 ("rel_pres", C.c_double), ("rel_dres", C.c_double),
-                ("omega", C.c_double), ("eta", C.c_double), ("norm_K", C.c_double)]
+                ("omega", C.c_double), ("eta", C.c_double), ("norm_K", C.c_double),
+                ("pc_alpha", C.c_double)]
 
 
 TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",
@@ -74,7 +77,8 @@ DEFAULTS = dict(tol=1e-4, max_iters=100000, check_every=64, ruiz_iters=10, ruiz_
                 pock_chambolle=0, power_iters=100, adaptive_step=1, primal_weight_update=1,
                 restarts=1, eta_scale=0.9, beta_sufficient=0.2, beta_necessary=0.8,
                 beta_artificial=0.36, eps_zero=1e-6, omega0=0.0, eta0=0.0,
-                infeas_detect=1, infeas_tol=1e-6, halpern=0, reflect=1.0)
+                infeas_detect=1, infeas_tol=1e-6, halpern=0, reflect=1.0, pc_alpha=1.0,
+                pc_trial_iters=0)
 
 
 def _bind(lib):
@@ -84,7 +88,7 @@ def _bind(lib):
         P = C.POINTER
         _lib.orc_spmv.argtypes = [P(_Lp), C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_spmv_t.argtypes = [P(_Lp), C.c_void_p, C.c_void_p, C.c_void_p]
-        _lib.orc_ruiz.argtypes = [P(_Lp), C.c_int32, C.c_double, C.c_int32,
+        _lib.orc_ruiz.argtypes = [P(_Lp), C.c_int32, C.c_double, C.c_int32, C.c_double,
                                   C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_ruiz.restype = C.c_int
         _lib.orc_power_norm.argtypes = [P(_Lp), C.c_void_p, C.c_int32]
@@ -123,6 +127,8 @@ def _bind(lib):
         _lib.orc_step_rule.argtypes = [C.c_double] * 5 + [C.c_int64, P(C.c_double),
                                                            P(C.c_double)]
         _lib.orc_step_rule.restype = C.c_int
+        _lib.orc_pc_tune.argtypes = [P(_Lp), P(_Opts), C.c_void_p]
+        _lib.orc_pc_tune.restype = C.c_double
     return lib
 
 
@@ -200,13 +206,14 @@ def spmv_t(lp, y, vals=None):
     return out
 
 
-def ruiz(lp, iters=10, tol=1e-4, pock_chambolle=False):
-    """Algorithm 3.  Returns (scaled values, R, C, passes) with K~ = diag(R) K diag(C)."""
+def ruiz(lp, iters=10, tol=1e-4, pock_chambolle=False, pc_alpha=1.0):
+    """Algorithm 3 (and the Pock-Chambolle pass with parameter pc_alpha).
+    Returns (scaled values, R, C, passes) with K~ = diag(R) K diag(C)."""
     b = _Bound(lp)
     vs = np.empty(lp.nnz)
     R = np.empty(lp.m)
     Cc = np.empty(lp.n)
-    passes = _load().orc_ruiz(C.byref(b.st), iters, tol, int(pock_chambolle),
+    passes = _load().orc_ruiz(C.byref(b.st), iters, tol, int(pock_chambolle), float(pc_alpha),
                               _ptr(vs), _ptr(R), _ptr(Cc))
     return vs, R, Cc, passes
 
@@ -268,7 +275,7 @@ def halpern_step(lp, x, y, xanc, yanc, tau, sigma, k, rho, vals=None, c=None, q=
     return (xh, yh), (xn, yn), float(r)
 
 
-def _opts(o, x0a=None, y0a=None):
+def _opts(o, x0a=None, y0a=None, replay=None):
     return _Opts(o["tol"], int(o["max_iters"]), int(o["check_every"]), int(o["ruiz_iters"]),
                  o["ruiz_tol"], int(o["pock_chambolle"]), int(o["power_iters"]),
                  int(o["adaptive_step"]), int(o["primal_weight_update"]), int(o["restarts"]),
@@ -276,7 +283,9 @@ def _opts(o, x0a=None, y0a=None):
                  o["beta_artificial"], o["eps_zero"],
                  None if x0a is None else _ptr(x0a), None if y0a is None else _ptr(y0a),
                  o["omega0"], o["eta0"], int(o["infeas_detect"]), 0, o["infeas_tol"],
-                 int(o["halpern"]), 0, float(o["reflect"]))
+                 int(o["halpern"]), 0, float(o["reflect"]), float(o["pc_alpha"]),
+                 int(o["pc_trial_iters"]), 0, None if replay is None else _ptr(replay),
+                 0 if replay is None else int(replay.shape[0]))
 
 
 def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
@@ -303,17 +312,21 @@ def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
 ATTEMPT_FIELDS = ("k", "eta", "eta_bar", "eta_next", "accept", "omega", "dx2", "dy2", "inter")
 
 
-def solve_logged(lp, attempt_cap=100000, trace_cap=100000, x0=None, y0=None, **kw):
+def solve_logged(lp, attempt_cap=100000, trace_cap=100000, x0=None, y0=None, replay=None,
+                 **kw):
     """``solve`` plus one record per step attempt (ATTEMPT_FIELDS: accepted
     iterations before the attempt, the eta tried, Algorithm 5's eta_bar and
     eta', the outcome, omega and the three terms ||dx||^2, ||dy||^2, dy^T K dx on
-    the scaled problem).  Returns (x, y, info, trace, attempts)."""
+    the scaled problem).  replay: attempt records of another run (an array of
+    rows in ATTEMPT_FIELDS order) whose step sizes and outcomes this run takes
+    (eta_bar and eta' are still its own).  Returns (x, y, info, trace, attempts)."""
     o = dict(DEFAULTS)
     o.update(kw)
     b = _Bound(lp)
     x0a = None if x0 is None else _f64(x0)
     y0a = None if y0 is None else _f64(y0)
-    opts = _opts(o, x0a, y0a)
+    rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.float64)
+    opts = _opts(o, x0a, y0a, rep)
     x = np.empty(lp.n)
     y = np.empty(lp.m)
     info = _Info()
@@ -328,6 +341,20 @@ def solve_logged(lp, attempt_cap=100000, trace_cap=100000, x0=None, y0=None, **k
     trace = [dict(zip(TRACE_FIELDS, r.tolist())) for r in tr[: min(tl.value, trace_cap)]]
     attempts = [dict(zip(ATTEMPT_FIELDS, r.tolist())) for r in al[: min(an.value, attempt_cap)]]
     return x, y, d, trace, attempts
+
+
+PC_GRID = (0.0, 0.5, 1.0, 2.0)
+
+
+def pc_tune(lp, **kw):
+    """The Pock-Chambolle alpha that pock_chambolle = 2 picks, and the relative
+    KKT error of each trial (one per alpha of PC_GRID)."""
+    o = dict(DEFAULTS)
+    o.update(kw)
+    b = _Bound(lp)
+    errs = np.empty(len(PC_GRID))
+    a = _load().orc_pc_tune(C.byref(b.st), C.byref(_opts(o)), _ptr(errs))
+    return float(a), errs
 
 
 def primal_weight(omega, dx, dy, eps_zero=1e-6):

@@ -15,7 +15,8 @@
  * Function map (paper sections, algorithms, equations):
  *   orc_spmv / orc_spmv_t     products K x and K^T y
  *   orc_ruiz                  Algorithm 3 (Ruiz), Section 2.4.1 change of variables,
- *                             optional Pock-Chambolle pass (alpha = 1)
+ *                             optional Pock-Chambolle pass (parameter alpha)
+ *   orc_pc_tune               choice of alpha by trial runs (a reading; not in the paper)
  *   orc_power_norm            Algorithm 2 (spectral norm estimate)
  *   orc_proj_lambda           projection onto Lambda (Section 2.2 dual)
  *   orc_kkt                   termination quantities, Eqs. (term1)-(term3) of
@@ -63,7 +64,8 @@ typedef struct {
     int32_t check_every;      /* reading: the paper's "a set number" of iterations */
     int32_t ruiz_iters;       /* N_iter of Algorithm 3 (0 = no scaling) */
     double ruiz_tol;          /* "converged to 1 within tolerance" */
-    int32_t pock_chambolle;   /* reading: one alpha = 1 pass after Ruiz */
+    int32_t pock_chambolle;   /* reading: 1 = one Pock-Chambolle pass (pc_alpha) after Ruiz;
+                                 2 = pick alpha from {0, 1/2, 1, 2} by trial runs (orc_pc_tune) */
     int32_t power_iters;      /* N_iter of Algorithm 2 */
     int32_t adaptive_step;    /* Algorithm 5 on/off */
     int32_t primal_weight_update; /* Algorithm 4 on/off */
@@ -81,6 +83,15 @@ typedef struct {
     int32_t halpern;          /* 1: the restarted Halpern variant (orc_solve_halpern) */
     int32_t pad2;
     double reflect;           /* rho in [0, 1] of the Halpern variant */
+    double pc_alpha;          /* alpha of the Pock-Chambolle pass (pock_chambolle = 1) */
+    int32_t pc_trial_iters;   /* pock_chambolle = 2: iterations of each trial (0: 2 check_every) */
+    int32_t pad3;
+    /* replay (test use): the attempt records of another run (ORC_ATTEMPT_FIELDS
+     * doubles each); attempt a of this run takes its step size ([1]) and its
+     * accept / reject outcome ([4]) from record a, while eta_bar and eta' are
+     * still computed here and logged.  NULL: off. */
+    const double* replay;
+    int64_t replay_len;
 } orc_opts;
 
 typedef struct {
@@ -91,6 +102,7 @@ typedef struct {
     int64_t restarts;
     double pobj, dobj, rel_gap, rel_pres, rel_dres;
     double omega, eta, norm_K;
+    double pc_alpha;          /* alpha of the Pock-Chambolle pass used (NaN: no pass) */
 } orc_info;
 
 #define ORC_ATTEMPT_FIELDS 9
@@ -161,8 +173,17 @@ static double clamp(double v, double lo, double hi)
  * (the same set of passes as testing after each update); an empty row or
  * column keeps factor 1.  Returns the number of passes applied.
  */
+/* |a|^e of a stored value for the Pock-Chambolle sums; |a|^0 is 1 for a
+ * nonzero a and 0 for a stored zero (the sums run over the nonzeros of K). */
+static double pc_pow(double a, double e)
+{
+    a = fabs(a);
+    if (e == 0.0) return a != 0.0 ? 1.0 : 0.0;
+    return pow(a, e);
+}
+
 int orc_ruiz(const orc_lp* lp, int32_t iters, double tol, int32_t pock_chambolle,
-             double* vals_s, double* R, double* C)
+             double pc_alpha, double* vals_s, double* R, double* C)
 {
     const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
     double* rn = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
@@ -196,13 +217,15 @@ int orc_ruiz(const orc_lp* lp, int32_t iters, double tol, int32_t pock_chambolle
         ++passes;
     }
     if (pock_chambolle) {
-        /* reading: alpha = 1, rows by 1/sqrt(sum_j |K~_ij|), columns by 1/sqrt(sum_i |K~_ij|) */
+        /* reading (the pass is not in the paper; Pock and Chambolle, 2011):
+         * rows by 1 / sqrt(sum_j |K~_ij|^(2 - alpha)), columns by
+         * 1 / sqrt(sum_i |K~_ij|^alpha), from the Ruiz-scaled K~ */
         for (int64_t i = 0; i < m; ++i) rn[i] = 0.0;
         for (int64_t j = 0; j < n; ++j) cn[j] = 0.0;
         for (int64_t i = 0; i < m; ++i)
             for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p) {
-                rn[i] += fabs(vals_s[p]);
-                cn[lp->col_idx[p]] += fabs(vals_s[p]);
+                rn[i] += pc_pow(vals_s[p], 2.0 - pc_alpha);
+                cn[lp->col_idx[p]] += pc_pow(vals_s[p], pc_alpha);
             }
         for (int64_t i = 0; i < m; ++i) rn[i] = rn[i] > 0.0 ? 1.0 / sqrt(rn[i]) : 1.0;
         for (int64_t j = 0; j < n; ++j) cn[j] = cn[j] > 0.0 ? 1.0 / sqrt(cn[j]) : 1.0;
@@ -512,10 +535,60 @@ int orc_solve(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
     return orc_solve_logged(lp, o, x_out, y_out, info, trace, trace_cap, trace_len, NULL, 0, NULL);
 }
 
+/*
+ * Choice of the Pock-Chambolle alpha (pock_chambolle = 2).  reading: the paper
+ * has no such pass; the rule is ours.  For each alpha of the grid
+ * {0, 1/2, 1, 2}, in that order, a trial solve with that pass (all other
+ * options as given, infeasibility detection off, no tolerance) runs
+ * pc_trial_iters accepted iterations (0: 2 check_every) from the start point;
+ * its last check's relative KKT error, max(rel_gap, rel_pres, rel_dres) of
+ * Section 2.3.2 on the unscaled problem, is errs[g].  The alpha with the
+ * smallest error wins (ties and NaN: the earlier one).  All trials start from
+ * the same unscaled point, so equal starting errors make the ends comparable.
+ */
+#define ORC_PC_GRID 4
+static const double kPcGrid[ORC_PC_GRID] = {0.0, 0.5, 1.0, 2.0};
+
+double orc_pc_tune(const orc_lp* lp, const orc_opts* o, double* errs)
+{
+    const int64_t trial = o->pc_trial_iters > 0 ? o->pc_trial_iters : 2 * (int64_t)o->check_every;
+    double* x = (double*)malloc(sizeof(double) * (size_t)(lp->n > 0 ? lp->n : 1));
+    double* y = (double*)malloc(sizeof(double) * (size_t)(lp->m > 0 ? lp->m : 1));
+    double best = kPcGrid[0], best_err = INFINITY;
+    for (int g = 0; g < ORC_PC_GRID; ++g) {
+        orc_opts t = *o;
+        t.pock_chambolle = 1;
+        t.pc_alpha = kPcGrid[g];
+        t.max_iters = trial;
+        t.tol = 0.0;
+        t.infeas_detect = 0;
+        orc_info inf;
+        orc_solve_logged(lp, &t, x, y, &inf, NULL, 0, NULL, NULL, 0, NULL);
+        double e = inf.rel_gap;
+        if (inf.rel_pres > e) e = inf.rel_pres;
+        if (inf.rel_dres > e) e = inf.rel_dres;
+        if (errs) errs[g] = e;
+        if (e < best_err) {
+            best_err = e;
+            best = kPcGrid[g];
+        }
+    }
+    free(x);
+    free(y);
+    return best;
+}
+
 int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double* y_out,
                      orc_info* info, orc_trace* trace, int64_t trace_cap, int64_t* trace_len,
                      double* alog, int64_t alog_cap, int64_t* alog_len)
 {
+    if (o->pock_chambolle == 2) {
+        orc_opts t = *o;
+        t.pock_chambolle = 1;
+        t.pc_alpha = orc_pc_tune(lp, o, NULL);
+        return orc_solve_logged(lp, &t, x_out, y_out, info, trace, trace_cap, trace_len, alog,
+                                alog_cap, alog_len);
+    }
     if (o->halpern) return orc_solve_halpern(lp, o, x_out, y_out, info, trace, trace_cap, trace_len);
     int64_t al = 0;   /* attempts logged */
     const int64_t m = lp->m, n = lp->n, nnz = lp->row_ptr[m];
@@ -538,7 +611,7 @@ int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double*
     int64_t tl = 0;
 
     /* 1. preconditioning */
-    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, vs, R, C);
+    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, o->pc_alpha, vs, R, C);
     for (int64_t j = 0; j < n; ++j) {
         cs[j] = C[j] * lp->c[j];
         ls[j] = lp->l[j] / C[j];
@@ -674,6 +747,9 @@ int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double*
         /* 5. one accepted iteration */
         double used = eta;   /* the eta the accepted step was taken with */
         for (;;) {
+            const double* rec = (o->replay && attempts < o->replay_len)
+                                    ? o->replay + ORC_ATTEMPT_FIELDS * attempts : NULL;
+            if (rec) eta = rec[1];   /* replay: the step the other run tried */
             double tau = eta / omega, sigma = eta * omega;
             orc_pdhg_step(lp, vs, cs, qs, ls, us, x, y, tau, sigma, xn, yn);
             ++attempts;
@@ -706,7 +782,7 @@ int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double*
             }
             ++al;
             eta = eta_next;            /* eta' is used by the next attempt either way */
-            if (accept) break;
+            if (rec ? rec[4] != 0.0 : accept) break;
         }
         /* eta-weighted averages of the accepted iterates (Section 2.4.2) */
         for (int64_t j = 0; j < n; ++j) xsum[j] += used * xn[j];
@@ -728,6 +804,7 @@ int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double*
         info->pobj = pobj; info->dobj = dobj;
         info->rel_gap = rel[0]; info->rel_pres = rel[1]; info->rel_dres = rel[2];
         info->omega = omega; info->eta = eta; info->norm_K = normK;
+        info->pc_alpha = o->pock_chambolle ? o->pc_alpha : NAN;
     }
     if (alog_len) *alog_len = al;
     if (trace_len) *trace_len = tl;
@@ -830,7 +907,7 @@ int orc_solve_halpern(const orc_lp* lp, const orc_opts* o, double* x_out, double
     double kc[8], ka[8], kk[8];
     int64_t tl = 0;
 
-    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, vs, R, C);
+    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, o->pc_alpha, vs, R, C);
     for (int64_t j = 0; j < n; ++j) {
         cs[j] = C[j] * lp->c[j];
         ls[j] = lp->l[j] / C[j];
@@ -940,6 +1017,7 @@ int orc_solve_halpern(const orc_lp* lp, const orc_opts* o, double* x_out, double
         info->pobj = pobj; info->dobj = dobj;
         info->rel_gap = rel[0]; info->rel_pres = rel[1]; info->rel_dres = rel[2];
         info->omega = omega; info->eta = eta; info->norm_K = normK;
+        info->pc_alpha = o->pock_chambolle ? o->pc_alpha : NAN;
     }
     if (trace_len) *trace_len = tl;
     free(vs); free(R); free(C); free(cs); free(qs); free(ls); free(us);
@@ -1084,7 +1162,7 @@ int orc_fishnet(const orc_lp* lp, const orc_opts* o, int32_t P, int32_t k_steps,
     double* C = (double*)xalloc(n);
     double *cs = (double*)xalloc(n), *qs = (double*)xalloc(m);
     double *ls = (double*)xalloc(n), *us = (double*)xalloc(n);
-    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, vs, R, C);
+    orc_ruiz(lp, o->ruiz_iters, o->ruiz_tol, o->pock_chambolle, o->pc_alpha, vs, R, C);
     for (int64_t j = 0; j < n; ++j) {
         cs[j] = C[j] * lp->c[j];
         ls[j] = lp->l[j] / C[j];

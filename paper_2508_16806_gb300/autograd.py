@@ -4,9 +4,10 @@
 returns x_K, the primal iterate after K fixed-step PDHG iterations (Algorithm 1,
 theta = 1, start x = proj_X(0), y = 0) of the LP held by ``problem`` with its cost
 c, right-hand side q and nonzero values vals replaced by the given tensors.
-Backward calls the CUDA library's hand-written adjoint (lp_grad) for
-dL/dc, dL/dq and dL/dvals; step sizes are constants (eta, omega given, or
-derived once from the LP when None).
+Backward puts the forward's values back on the handle (another forward on the
+same problem may have replaced them) and calls the CUDA library's hand-written
+adjoint (lp_grad) for dL/dc, dL/dq and dL/dvals; step sizes are constants (eta,
+omega given, or derived from the LP of that forward when None).
 """
 from __future__ import annotations
 
@@ -47,6 +48,9 @@ class UnrolledPDHG(torch.autograd.Function):
             raise L.LpError(s, "lp_unroll")
         ctx.problem, ctx.K, ctx.ckpt, ctx.opts = problem, int(K), int(ckpt), o
         ctx.dtypes = (c.dtype, q.dtype, vals.dtype)
+        # the values this forward ran on: lp_grad recomputes the unrolled forward
+        # from the handle's current values, which a later forward may have replaced
+        ctx.values = (c64, q64, v64)
         return xK
 
     @staticmethod
@@ -56,7 +60,12 @@ class UnrolledPDHG(torch.autograd.Function):
         dc = torch.empty(p.n, dtype=torch.float64, device="cuda")
         dq = torch.empty(p.m, dtype=torch.float64, device="cuda")
         dv = torch.empty(max(p.nnz, 1), dtype=torch.float64, device="cuda")
+        c64, q64, v64 = ctx.values
         torch.cuda.current_stream().synchronize()
+        s = L.lp_update_values(p.handle, v64.data_ptr(), c64.data_ptr(), q64.data_ptr(), None,
+                               None, L.LP_MEM_DEVICE)
+        if s != 0:
+            raise L.LpError(s, "lp_update_values")
         s = L.lp_grad(p.handle, ctx.opts, ctx.K, ctx.ckpt, g.data_ptr(), dc.data_ptr(),
                       dq.data_ptr(), dv.data_ptr(), None, L.LP_MEM_DEVICE)
         if s != 0:

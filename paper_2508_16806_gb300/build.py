@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(CSRC, "libpdhg.so")
 SOURCES = ["setup.cu", "solver.cu", "capi.cu", "grad.cu", "noalloc.cu", "batch.cu", "fishnet.cu",
-           "tune.cu"]
+           "tune.cu", "probe.cu"]
 HEADERS = ["common.cuh", "spmv.cuh", "control.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -334,9 +334,17 @@ kb_primal(const Ctrl* __restrict__ ctrl, const int32_t* __restrict__ lp_col, T* 
 __device__ __forceinline__ double warp_range_sum(const double* part, int a, int b)
 {
     const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int i = a + lane; i < b; i += 32) s += __ldcg(part + i);
-    return warp_sum(s);   // lane 0
+    // four independent loads in flight per lane, fixed order
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = a + lane;
+    for (; i + 3 * 32 < b; i += 4 * 32) {
+        s0 += __ldcg(part + i);
+        s1 += __ldcg(part + i + 32);
+        s2 += __ldcg(part + i + 64);
+        s3 += __ldcg(part + i + 96);
+    }
+    for (; i < b; i += 32) s0 += __ldcg(part + i);
+    return warp_sum((s0 + s1) + (s2 + s3));   // lane 0
 }
 
 // maximum of part[a..b) (0 when empty) by one warp; the result is valid in lane 0
@@ -852,7 +860,7 @@ lp_status batch_scale(BatchHandle* bh, const lp_opts* o, double* normK_dev)
     }
     if (o->pock_chambolle) {
         k_pc_sums<<<grid_n(m + n, 256, 65535), 256, 0, st>>>(m, n, h->rp, h->trp, h->tperm, E.val,
-                                                             rn, cn);
+                                                             o->pc_alpha, rn, cn);
         k_ruiz_factors<<<grid_n(m, 256, 65535), 256, 0, st>>>(m, rn, h->R);
         k_ruiz_factors<<<grid_n(n, 256, 65535), 256, 0, st>>>(n, cn, h->C);
         k_scale_vals<<<grid_n(nnz, 256, 8192), 256, 0, st>>>(nnz, h->krow, h->ci, rn, cn, E.val);
@@ -1294,6 +1302,9 @@ lp_status lp_batch_solve(lp_batch b, const lp_opts* o, lp_result* rs)
         o->power_iters < 0 || !(o->eta_scale > 0.0) || !(o->time_limit_s > 0.0))
         return LP_INVALID_ARGUMENT;
     if (o->halpern) return LP_NOT_SUPPORTED;   // the batched loop runs averaged PDHG restarts
+    if (o->pock_chambolle == 2) return LP_NOT_SUPPORTED;   // alpha trials: lp_solve only
+    if (o->pock_chambolle < 0 || o->pock_chambolle > 2 || !(o->pc_alpha >= 0.0 && o->pc_alpha <= 2.0))
+        return LP_INVALID_ARGUMENT;
     for (int k = 0; k < b->b.meta.B; ++k)
         if (rs[k].memory_space != LP_MEM_HOST && rs[k].memory_space != LP_MEM_DEVICE)
             return LP_INVALID_ARGUMENT;

@@ -48,8 +48,15 @@ lp_status check_opts(const lp_opts* o)
     if (o->halpern != 0 && o->halpern != 1) return LP_INVALID_ARGUMENT;
     if (o->halpern && !(o->halpern_reflect >= 0.0 && o->halpern_reflect <= 1.0))
         return LP_INVALID_ARGUMENT;
+    if (o->pock_chambolle < 0 || o->pock_chambolle > 2) return LP_INVALID_ARGUMENT;
+    if (!(o->pc_alpha >= 0.0 && o->pc_alpha <= 2.0) || o->pc_trial_iters < 0)
+        return LP_INVALID_ARGUMENT;
+    if (o->attempt_cap < 0 || (o->attempt_cap > 0 && !o->attempt_log)) return LP_INVALID_ARGUMENT;
     return LP_OK;
 }
+
+// The grid of Pock-Chambolle parameters that pock_chambolle = 2 tries.
+constexpr double kPcGrid[4] = {0.0, 0.5, 1.0, 2.0};
 
 void fill_result(lp_result* r, const Ctrl& c)
 {
@@ -103,6 +110,8 @@ void lp_opts_default(lp_opts* o)
     o->autotune = 0;
     o->halpern = 0;
     o->halpern_reflect = 1.0;
+    o->pc_alpha = 1.0;
+    o->pc_trial_iters = 0;
 }
 
 const char* lp_status_string(lp_status s)
@@ -202,7 +211,57 @@ static lp_status prepare_fp64(Handle* h, const lp_opts* o, double* normK, double
     return LP_OK;
 }
 
+static lp_status solve_core(Handle* h, const lp_opts* o, lp_result* r);
+
+// lp_solve: with pock_chambolle = 2, one trial solve per alpha of kPcGrid (the
+// caller's options with that pass, pc_trial_iters accepted iterations, no
+// tolerance, no infeasibility detection, no outputs), then the solve with the
+// alpha whose trial ended with the smallest max(rel_gap, rel_pres, rel_dres);
+// ties and NaN go to the earlier alpha.  The trials' time is added to setup_s.
 static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
+{
+    LP_TRY(check_opts(o));
+    if (!r) return LP_INVALID_ARGUMENT;
+    if (o->pock_chambolle != 2) {
+        lp_status s = solve_core(h, o, r);
+        r->pc_alpha_used = o->pock_chambolle ? o->pc_alpha : NAN;
+        return s;
+    }
+    const double t0 = now_s();
+    const long long launches0 = h->launches;
+    double best = kPcGrid[0], best_err = INFINITY;
+    for (double a : kPcGrid) {
+        lp_opts t = *o;
+        t.pock_chambolle = 1;
+        t.pc_alpha = a;
+        t.max_iters = o->pc_trial_iters > 0 ? o->pc_trial_iters : 2 * (int64_t)o->check_every;
+        t.tol = 0.0;
+        t.infeas_detect = 0;
+        t.attempt_log = nullptr;
+        t.attempt_cap = 0;
+        lp_result rt;
+        std::memset(&rt, 0, sizeof(rt));
+        rt.memory_space = LP_MEM_HOST;
+        const lp_status st = solve_core(h, &t, &rt);
+        if (st < 0) return st;
+        const double e = std::max(rt.rel_gap, std::max(rt.rel_pres, rt.rel_dres));
+        if (e < best_err) {
+            best_err = e;
+            best = a;
+        }
+    }
+    const double t_trials = now_s() - t0;
+    lp_opts t = *o;
+    t.pock_chambolle = 1;
+    t.pc_alpha = best;
+    const lp_status s = solve_core(h, &t, r);
+    r->setup_s += t_trials;
+    r->kernel_launches = h->launches - launches0;
+    r->pc_alpha_used = best;
+    return s;
+}
+
+static lp_status solve_core(Handle* h, const lp_opts* o, lp_result* r)
 {
     LP_TRY(check_opts(o));
     if (!r) return LP_INVALID_ARGUMENT;
@@ -224,6 +283,15 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
     Ctrl c;
     std::memset(&c, 0, sizeof(c));
     r->trace_len = 0;
+    r->attempt_len = 0;
+    // the attempt log runs through the phases of this solve (run_solve reads it)
+    struct AlogScope {
+        Handle* h;
+        ~AlogScope() { h->alog_host = nullptr; h->alog_cap_host = 0; h->alog_off = 0; }
+    } alog_scope{h};
+    h->alog_host = o->attempt_cap > 0 ? o->attempt_log : nullptr;
+    h->alog_cap_host = h->alog_host ? o->attempt_cap : 0;
+    h->alog_off = 0;
     if (o->precision == LP_PREC_MIXED) {
         lp_opts o32 = *o;
         o32.tol = std::max(o->tol, o->polish_switch_tol);
@@ -236,7 +304,14 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
         r->trace_len = c.trace_len;
         r->precision_used = LP_PREC_MIXED;
         r->fp64_iters = 0;
-        const bool polish = c.status == LP_OPTIMAL && o->tol < o32.tol;
+        // An FP32 phase that stopped optimal hands its candidate to the FP64 engine
+        // in every case: the FP64 start check re-evaluates the three relative
+        // errors of Section 2.3.2 with FP64 products and FP64 element terms (the
+        // FP32 phase judged them on FP32 products), and LP_OPTIMAL is returned
+        // only when they hold there.  When tol is below the hand-over tolerance, or
+        // the FP32 judgement does not survive the FP64 one, FP64 iterations continue
+        // from the candidate to tol (the FP64 polish).
+        const bool polish = c.status == LP_OPTIMAL;
         if (!polish) {
             fill_result(r, c);
             LP_TRY(extract_solution<float>(h, r->x, r->y, r->memory_space));
@@ -247,6 +322,7 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
             lp_opts o64 = *o;
             o64.time_limit_s = std::max(1e-3, o->time_limit_s - (now_s() - t1));
             const long long k32 = c.k;
+            h->alog_off = std::min<long long>(c.alog_len, h->alog_cap_host);
             Ctrl c2;
             LP_TRY(run_solve<double>(h, &o64, c.eta, c.omega, h->wbuf, h->wbuf + h->n, nullptr,
                                      nullptr, LP_MEM_HOST, c.k, c.attempts, c.restarts, r->trace,
@@ -255,7 +331,9 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
             r->trace_len = c.trace_len + c2.trace_len;
             fill_result(r, c2);
             r->fp64_iters = c2.k - k32;
-            r->precision_used = LP_PREC_FP64;
+            // FP64 is the precision of the last phase only if FP64 iterations ran
+            // (a confirmation by the FP64 check alone keeps the FP32 result)
+            r->precision_used = r->fp64_iters > 0 ? LP_PREC_FP64 : LP_PREC_MIXED;
             LP_TRY(extract_solution<double>(h, r->x, r->y, r->memory_space));
         }
     } else {
@@ -269,6 +347,7 @@ static lp_status solve_impl(Handle* h, const lp_opts* o, lp_result* r)
     }
     r->solve_s = now_s() - t1;
     r->kernel_launches = h->launches - launches0;
+    r->attempt_len = std::min<long long>(r->attempts, h->alog_cap_host);
     return r->status;
 }
 

@@ -21,6 +21,7 @@ constexpr int kCtlNT = 512;       // threads of a control (single-block) kernel
 // KKT-check reductions: row side 11 sums + 2 maxima, column side 15 sums + 1 maximum
 constexpr int kRowSums = 11, kRowMax = 2, kRowQ = kRowSums + kRowMax;
 constexpr int kColSums = 15, kColMax = 1, kColQ = kColSums + kColMax;
+constexpr int kAttemptFields = 9;   // doubles per record of the attempt log
 
 // status codes shared with the ABI
 constexpr int kRunning = -100;
@@ -69,7 +70,19 @@ struct Ctrl {
     int infeas;          // Algorithm 6 at every check
     int halpern;         // restarted Halpern iterations instead of averaged PDHG restarts
     int rejects;         // consecutive rejected attempts (a guard against a stuck loop)
-    unsigned int tick;   // finished blocks of the current K^T launch (last one runs the step control)
+    // what the K^T launch of a fused PDHG attempt does after the decision taken
+    // at the end of the K launch: 0 nothing, 1 K^T y' and the next x' (accepted),
+    // 2 K^T y' only (accepted, a check or the end follows), 3 the next x' from the
+    // kept K^T y (rejected: no product)
+    int t_mode;
+    int npx;             // number of ||x' - x||^2 partials at px (the K^T launch grid)
+    const double* px;    // those partials (written by k_primal or the K^T launch)
+    // optional log of every step attempt (kAttemptFields doubles per record;
+    // nullptr: off): accepted iterations before it, eta tried, eta_bar, eta',
+    // accepted, omega, ||dx||^2, ||dy||^2, dy^T K dx (scaled problem)
+    double* alog;
+    long long alog_cap, alog_len;
+    unsigned int tick;   // finished blocks of the launch that takes the step decision (its last block does)
     long long bodies;    // loop-body executions (for the launch count)
     long long t_done_ns; // device clock when the loop finished for this LP
     // the step scalars, formed in FP64 once per change of eta, omega, pend_w, W or
@@ -148,12 +161,15 @@ struct Engine {
     T* Rt = nullptr; T* Ct = nullptr; T* Rinv = nullptr; T* Cinv = nullptr;
     // reduction partials
     double* partD = nullptr;   // [2][gK] Algorithm 5 partials of the K x' launch (largest grid)
-    double* partT = nullptr;   // [kEWGrid] ||x' - x||^2 partials of k_primal
+    double* partT = nullptr;   // [kEWGrid] ||x' - x||^2 partials (k_primal, or the K^T launch's
+                               // fused primal step), one per block of the K^T launch grid
     double* partR = nullptr;   // [kRowQ][kEWGrid]
     double* partC = nullptr;   // [kColQ][kEWGrid]
     Ctrl* ctrl = nullptr;
     lp_trace_rec* trace = nullptr;  // device trace ring
     long long trace_cap = 0;
+    double* alog = nullptr;         // device attempt log (kAttemptFields per record)
+    long long alog_cap = 0;
     // loop graph
     cudaGraphExec_t exec = nullptr;
     int graph_check_every = -1;
@@ -193,6 +209,10 @@ struct Handle {
     Engine<double> e64;
     Engine<float> e32;
     long long launches = 0;      // kernels launched by the host (graph bodies counted apart)
+    // attempt log of the current lp_solve (host buffer of the caller, records
+    // already written by an earlier phase)
+    double* alog_host = nullptr;
+    long long alog_cap_host = 0, alog_off = 0;
     int built_precision_mask = 0;
 };
 
@@ -369,7 +389,8 @@ __global__ void k_ruiz_factors(int64_t count, double* nrm, double* acc);
 __global__ void k_scale_vals(int64_t nnz, const int32_t* krow, const int32_t* ci, const double* r,
                              const double* s, double* v);
 __global__ void k_pc_sums(int64_t m, int64_t n, const int64_t* rp, const int64_t* trp,
-                          const int32_t* tperm, const double* v, double* rs, double* cs);
+                          const int32_t* tperm, const double* v, double alpha, double* rs,
+                          double* cs);
 __global__ void k_scale_vectors(int64_t m, int64_t n, const double* R, const double* C,
                                 const double* c0, const double* q0, const double* l0,
                                 const double* u0, double* c, double* q, double* l, double* u);

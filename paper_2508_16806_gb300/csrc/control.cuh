@@ -124,7 +124,8 @@ __device__ __forceinline__ bool infeas_active(const Ctrl& c)
 // Algorithm 5 decision (or the plain swap of a fixed step), by one thread.
 // The paper's k is read as the 1-based index of the iteration being taken.
 // Halpern iterations (fixed step) also record the fixed-point residual.
-__device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, double dx2, double inter)
+__device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, double dx2, double inter,
+                                            double* eta_bar_out = nullptr)
 {
     const double eta = ctrl->eta, omega = ctrl->omega;
     bool accept = true;
@@ -132,6 +133,7 @@ __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, d
     if (adapt) {
         const double movement = omega * dx2 + dy2 / omega;
         const double eta_bar = inter != 0.0 ? movement / (2.0 * fabs(inter)) : INFINITY;
+        if (eta_bar_out) *eta_bar_out = eta_bar;
         const double kp1 = (double)(ctrl->k + 1) + 1.0;
         const double e1 = (1.0 - pow(kp1, -0.3)) * eta_bar;
         const double e2 = (1.0 + pow(kp1, -0.6)) * eta;
@@ -172,7 +174,9 @@ __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, d
     }
     ctrl->eta = eta_next;
     refresh_scalars(*ctrl);
-    if (ctrl->k % ctrl->check_every == 0 || ctrl->k >= ctrl->max_iters) {
+    // a check follows an accepted iteration that completes a check period (or
+    // reaches max_iters); a rejected attempt never checks (the iterate did not move)
+    if (accept && (ctrl->k % ctrl->check_every == 0 || ctrl->k >= ctrl->max_iters)) {
         ctrl->want_check = 1;
         ctrl->skip = 1;
     }

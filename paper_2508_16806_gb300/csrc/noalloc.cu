@@ -2,12 +2,11 @@
 // without allocating any device memory.
 //
 // Who needs this: code that cannot call cudaMalloc at the moment it wants to
-// check a candidate solution.  Examples are a caller in the middle of capturing
-// a stream into a CUDA graph (allocation calls are not allowed while a capture
-// is open), a host that forbids device allocation after start-up because an
-// allocation can block or synchronise the whole device (real-time control loops,
-// serving processes with strict latency budgets), and a plugin that runs inside
-// an application that has already handed all device memory to its own pool.
+// check a candidate solution.  Examples are a host that forbids device
+// allocation after start-up because an allocation can block or synchronise the
+// whole device (real-time control loops, serving processes with strict latency
+// budgets), and a plugin that runs inside an application that has already handed
+// all device memory to its own pool.
 //
 // How: all scratch lives in one fixed array in the library's device image
 // (g_na_scratch below, LP_KKT_NOALLOC_MAX_DOUBLES doubles = 8 MiB).  Every GPU
@@ -17,10 +16,11 @@
 // behind; the accumulators that must start at zero are cleared by each call.
 // Two calls whose work overlaps on the GPU (different streams, or different
 // host threads) race on the array and give wrong results: serialise them.
+// The call waits for its stream before it returns (it copies eight doubles to
+// the host), so it refuses a stream that is being captured.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -33,31 +33,20 @@ constexpr long long kNaMax = LP_KKT_NOALLOC_MAX_DOUBLES;
 
 static __device__ __align__(256) double g_na_scratch[LP_KKT_NOALLOC_MAX_DOUBLES];
 
-// Device address of g_na_scratch per device, looked up once per device with
-// that device current (in host code the symbol itself is only a host-side
-// stand-in, not a device address).
-constexpr int kMaxDevices = 64;
-std::mutex g_na_mutex;
-double* g_na_ptr[kMaxDevices] = {nullptr};
-
+// Device address of g_na_scratch on the current device.  In host code the
+// symbol itself is only a host-side stand-in, not a device address, so it is
+// looked up with the device current, on every call: the lookup is cheap once
+// the module is loaded, and a cached address could outlive its context (after
+// cudaDeviceReset or a re-created primary context the module, and the array,
+// are loaded anew).
 lp_status scratch_for_current_device(double** out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
         (void)cudaGetLastError();
         return LP_CUDA_ERROR;
     }
-    if (dev < 0 || dev >= kMaxDevices) return LP_NOT_SUPPORTED;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
-            (void)cudaGetLastError();
-            return LP_CUDA_ERROR;
-        }
-        g_na_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_na_ptr[dev];
+    *out = static_cast<double*>(p);
     return LP_OK;
 }
 
@@ -156,26 +145,45 @@ extern "C" lp_status lp_kkt_noalloc(const lp_desc* d, const double* x, const dou
     // layout: K x [m] | K^T y [n] | partials [kNaQ * kNaGrid] | sums [kNaQ] | flag [1]
     const long long need = d->m + d->n + (long long)kNaQ * kNaGrid + kNaQ + 1;
     if (need > kNaMax) return LP_INVALID_ARGUMENT;   // the problem exceeds the fixed scratch
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // the call ends with a copy to the host and a stream synchronisation, which
+    // would invalidate a capture in progress: refuse before touching the stream
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LP_NOT_SUPPORTED;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return LP_NOT_SUPPORTED;
+    // an error left pending by earlier, unrelated work is the caller's: report it
+    // without clearing it, before this call launches anything
+    if (cudaPeekAtLastError() != cudaSuccess) return LP_CUDA_ERROR;
     double* base = nullptr;
     lp_status s = scratch_for_current_device(&base);
     if (s != LP_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     double* kx = base;
     double* kty = base + d->m;
     double* part = kty + d->n;
     double* sums = part + (size_t)kNaQ * kNaGrid;
     unsigned int* bad = reinterpret_cast<unsigned int*>(sums + kNaQ);
     const int64_t m = d->m, n = d->n;
-    // K^T y accumulates with atomics and the flag with atomicOr: both start at 0
+    // K^T y accumulates with atomics and the flag with atomicOr: both start at 0.
+    // Each launch is checked right after it, so only this call's failures map to
+    // LP_CUDA_ERROR.
+    bool launched = true;
     k_na_zero<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(kty, n);
+    launched = launched && cudaGetLastError() == cudaSuccess;
     k_na_zero<<<1, 32, 0, st>>>(sums + kNaQ, 1);
+    launched = launched && cudaGetLastError() == cudaSuccess;
     k_na_products<<<(int)std::min<int64_t>((m * 32 + 255) / 256, 65535), 256, 0, st>>>(
         m, n, d->nnz, d->row_ptr, d->col_idx, d->vals, x, y, kx, kty, bad);
+    launched = launched && cudaGetLastError() == cudaSuccess;
     k_na_terms<<<kNaGrid, kNaNT, 0, st>>>(m, n, d->sense, d->c, d->q, d->l, d->u, x, y, kx, kty,
                                           part);
+    launched = launched && cudaGetLastError() == cudaSuccess;
     k_na_final<<<1, kNaNT, 0, st>>>(part, sums);
+    launched = launched && cudaGetLastError() == cudaSuccess;
     double h[kNaQ + 1];
-    if (cudaGetLastError() != cudaSuccess ||
+    if (!launched ||
         cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         (void)cudaGetLastError();

@@ -290,20 +290,37 @@ __global__ void k_scale_vals(int64_t nnz, const int32_t* krow, const int32_t* ci
         v[p] = v[p] * r[krow[p]] * s[ci[p]];
 }
 
-// Pock-Chambolle (alpha = 1): sequential per-row and per-column |.| sums in
-// row order (rows: CSR order; columns: K^T order, ascending rows).
+// |a|^e for the Pock-Chambolle sums: |a|^0 = 1 for a stored nonzero (0 for a
+// stored zero); the exponents of alpha in {0, 1/2, 1, 2} by products and square
+// roots, others by pow.
+__device__ __forceinline__ double pc_pow(double a, double e)
+{
+    a = fabs(a);
+    if (e == 0.0) return a != 0.0 ? 1.0 : 0.0;
+    if (e == 1.0) return a;
+    if (e == 2.0) return a * a;
+    if (e == 0.5) return sqrt(a);
+    if (e == 1.5) return a * sqrt(a);
+    return pow(a, e);
+}
+
+// Pock-Chambolle pass (parameter alpha): sequential per-row sums of
+// |v|^(2 - alpha) and per-column sums of |v|^alpha in row order (rows: CSR
+// order; columns: K^T order, ascending rows).
 __global__ void k_pc_sums(int64_t m, int64_t n, const int64_t* rp, const int64_t* trp,
-                          const int32_t* tperm, const double* v, double* rs, double* cs)
+                          const int32_t* tperm, const double* v, double alpha, double* rs,
+                          double* cs)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m + n;
          t += (int64_t)gridDim.x * blockDim.x) {
         double a = 0.0;
         if (t < m) {
-            for (int64_t p = rp[t]; p < rp[t + 1]; ++p) a += fabs(v[p]);
+            const double e = 2.0 - alpha;
+            for (int64_t p = rp[t]; p < rp[t + 1]; ++p) a += pc_pow(v[p], e);
             rs[t] = a;
         } else {
             const int64_t j = t - m;
-            for (int64_t p = trp[j]; p < trp[j + 1]; ++p) a += fabs(v[tperm[p]]);
+            for (int64_t p = trp[j]; p < trp[j + 1]; ++p) a += pc_pow(v[tperm[p]], alpha);
             cs[j] = a;
         }
     }
@@ -588,7 +605,8 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
         LP_CUDA_TRY(cudaGetLastError());
     }
     if (o->pock_chambolle) {
-        k_pc_sums<<<grid_for(m + n), 256, 0, st>>>(m, n, h->rp, h->trp, h->tperm, E.val, rn, cn);
+        k_pc_sums<<<grid_for(m + n), 256, 0, st>>>(m, n, h->rp, h->trp, h->tperm, E.val,
+                                                   o->pc_alpha, rn, cn);
         ++h->launches;
         k_ruiz_factors<<<grid_for(m), 256, 0, st>>>(m, rn, h->R);
         ++h->launches;

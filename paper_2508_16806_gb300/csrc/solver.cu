@@ -1,13 +1,21 @@
 // The restarted PDHG iteration on the device.
 //
 // One step attempt (Algorithm 1 with theta = 1, step sizes tau = eta / omega,
-// sigma = eta * omega, Section 2.3.1) is three launches:
-//   k_primal      x' = clamp(x - tau (c - K^T y), l, u)        (K^T y kept from the last step)
-//   k_spmv<Dual>  K x', then y' = proj_Y(y + sigma (q - (2 K x' - K x)))  (K x kept)
-//   k_spmv<PrT>   K^T y' and the Algorithm 5 terms ||dx||^2, dx . (K^T y' - K^T y); its
-//                 last block takes the accept / reject decision (Algorithm 5) and swaps
-//                 the double buffers
-// Every check_every accepted iterations the check launches run: averages
+// sigma = eta * omega, Section 2.3.1) is two launches; the candidate x' of the
+// attempt was formed by the launch before:
+//   k_spmv<Dual>        K x', then y' = proj_Y(y + sigma (q - (2 K x' - K x))) (K x kept),
+//                       ||y' - y||^2 and (y' - y)^T K (x' - x); its last block adds
+//                       ||x' - x||^2 (from the launch that formed x') and takes the
+//                       Algorithm 5 accept / reject decision, swaps the double buffers
+//                       and sets eta'
+//   k_spmv<PrimalStep>  accepted: K^T y', then per column the next candidate
+//                       x'' = clamp(x' - tau' (c - K^T y'), l, u) with its ||x'' - x'||^2
+//                       partials and the eta-weighted sum of the accepted x'; rejected:
+//                       no product, x'' = clamp(x - tau' (c - K^T y), l, u) from the kept
+//                       K^T y
+// After a check (which may restart and change omega) k_primal forms the first
+// candidate of the next period.  Every check_every accepted iterations the check
+// launches run: averages
 // (Section 2.4.2), their products, FP64 KKT reductions, the candidate, the
 // termination test on the unscaled problem (Section 2.3.2), the three restart
 // criteria and the primal-weight update (Algorithm 4).  The whole loop is a CUDA
@@ -37,23 +45,32 @@ namespace pdhg {
 
 // ------------------------------------------------------------------ step kernels
 
-// x' = clamp(x - tau (c - K^T y), l, u); the pending averaged iterate is added to
-// the x sums on the way, and (adaptive step) each block's partial of ||x' - x||^2
-// goes to part[blockIdx.x].  16-byte vector loads, scalar tail.
+// x' = clamp(x - tau (c - K^T y), l, u): the first candidate after a check
+// (in the loop body's check, after the restart decision, and at the start),
+// and, where the primal step is not fused into the K^T launch, the candidate of
+// every next attempt; the accepted iterates reach the eta-weighted sums in the
+// K^T launch.  Block partials of ||x' - x||^2 go to part[blockIdx.x]; the
+// grid is the K^T launch's, so that the step decision always sums the same
+// number of partials.  16-byte vector loads, scalar tail.
 template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0,
          const T* __restrict__ kty1, const T* __restrict__ c, const T* __restrict__ l,
-         const T* __restrict__ u, T* xs, int64_t n, double* part)
+         const T* __restrict__ u, int64_t n, double* part, int after_step)
 {
-    if (ctrl->skip) return;
+    // after_step = 0: after a check (and at the start); 1: after the K^T launch
+    // of an attempt when the primal step is not fused into it (its mode 1 or 3)
+    if (after_step) {
+        const int mode = ctrl->t_mode;
+        if (mode != 1 && mode != 3) return;
+    } else if (!ctrl->want_check || ctrl->done) {
+        return;
+    }
     T dx2 = T(0);
     using VT = VecTraits<T>;
     constexpr int VEC = VT::N;
     const int cur = ctrl->cur;
-    const StepScalars<T>& sc = step_scalars<T>(*ctrl);
-    const T tau = sc.tau;
-    const T pw = sc.pw;
+    const T tau = step_scalars<T>(*ctrl).tau;
     const T* x = cur ? x1 : x0;
     T* xn = cur ? x0 : x1;
     const T* kty = cur ? kty1 : kty0;
@@ -65,13 +82,6 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
         VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(c + t * VEC)), cj);
         VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(l + t * VEC)), lj);
         VT::unpack(__ldg(reinterpret_cast<const typename VT::V*>(u + t * VEC)), uj);
-        if (pw != T(0)) {
-            T sj[VEC];
-            VT::unpack(*reinterpret_cast<const typename VT::V*>(xs + t * VEC), sj);
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) sj[k] += pw * xj[k];
-            *reinterpret_cast<typename VT::V*>(xs + t * VEC) = VT::pack(sj);
-        }
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
             T v = xj[k] - tau * (cj[k] - kj[k]);
@@ -85,7 +95,6 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
     for (int64_t j = nv * VEC + (int64_t)blockIdx.x * kEW + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * kEW) {
         const T xj = x[j];
-        if (pw != T(0)) xs[j] += pw * xj;
         T v = xj - tau * (c[j] - kty[j]);
         const T lo = l[j], hi = u[j];
         if (v < lo) v = lo;
@@ -93,10 +102,8 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
         xn[j] = v;
         dx2 += (v - xj) * (v - xj);
     }
-    if (ctrl->adaptive) {
-        const double t[1] = {(double)dx2};
-        block_partials<1, kEW>(t, part, gridDim.x);
-    }
+    const double t[1] = {(double)dx2};
+    block_partials<1, kEW>(t, part, gridDim.x);
 }
 
 // Halpern iteration, primal half: x^ = clamp(x - tau (c - K^T y), l, u) (the
@@ -164,17 +171,92 @@ k_primal_halpern(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restric
     block_partials<1, kEW>(t, part, gridDim.x);
 }
 
-// K x' SpMV + dual step: y' = proj_Y(y + sigma (q - (2 K x' - K x)))
+// Thread 0 of the deciding block: step_decide, then (fused PDHG attempts) the
+// mode of the K^T launch that follows.  Kept out of line so that its FP64
+// arithmetic does not add to the register pressure of the SpMV kernels that
+// call it once per launch.
+__device__ __noinline__ void decide_thread0(Ctrl* ctrl, bool sums, int adapt, double dy2,
+                                            double dx2, double inter, bool fused)
+{
+    ctrl->tick = 0;
+    const long long k0 = ctrl->k;
+    const double eta = ctrl->eta, omega = ctrl->omega;
+    double eta_bar = NAN;
+    if (sums) step_decide(ctrl, adapt, dy2, dx2, inter, &eta_bar);
+    else step_decide(ctrl, adapt, 0.0, 0.0, 0.0);
+    if (ctrl->alog && ctrl->alog_len < ctrl->alog_cap) {
+        double* r = ctrl->alog + kAttemptFields * ctrl->alog_len;
+        r[0] = (double)k0; r[1] = eta; r[2] = eta_bar; r[3] = ctrl->eta;
+        r[4] = ctrl->k != k0 ? 1.0 : 0.0; r[5] = omega;
+        r[6] = sums ? dx2 : NAN; r[7] = sums ? dy2 : NAN; r[8] = sums ? inter : NAN;
+    }
+    ctrl->alog_len += 1;
+    if (fused) {
+        int mode = 0;
+        if (!ctrl->done) {
+            if (ctrl->k != k0) mode = ctrl->want_check ? 2 : 1;
+            else mode = 3;
+        }
+        ctrl->t_mode = mode;
+    }
+}
+
+// The step decision of an attempt, taken by the last block of the launch that
+// completes the attempt's reductions (no block waits for another: the last
+// block is the one whose ticket completes the count).  Warps 0..2 sum, in a
+// fixed order, ||y' - y||^2 (partD[0, nD)), the interaction (partD[nD, 2 nD))
+// and ||x' - x||^2 (partX[0, nX)); thread 0 runs step_decide.  With `fused`
+// it also tells the K^T launch what to do next (Ctrl::t_mode).  Out of line:
+// inlined into the K-side SpMV it raised that kernel's register spills from 10
+// to 34 bytes per thread (FP32).
+template <int NT>
+__device__ __noinline__ void last_block_decide(Ctrl* ctrl, const double* partD, int nD,
+                                                  const double* partX, int nX, bool sums,
+                                                  int adapt, bool fused)
+{
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctrl->tick, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double tot[3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (sums && warp < 3) {
+        const double* src = warp == 0 ? partD : warp == 1 ? partD + nD : partX;
+        const int cnt = warp == 2 ? nX : nD;
+        // eight independent loads in flight per lane (a single running sum would
+        // wait one L2 round trip per 32 partials: about 10 us on a 608-block
+        // grid, on the critical path of every attempt); fixed order
+        double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int i = lane;
+        for (; i + 7 * 32 < cnt; i += 8 * 32) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] += __ldcg(src + i + 32 * u);
+        }
+        for (; i < cnt; i += 32) a[0] += __ldcg(src + i);
+        double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+        v = warp_sum(v);
+        if (lane == 0) tot[warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) decide_thread0(ctrl, sums, adapt, tot[0], tot[2], tot[1], fused);
+}
+
+// K x' SpMV + dual step: y' = proj_Y(y + sigma (q - (2 K x' - K x))); the
+// pending weight of the current y (the last accepted iterate) goes to the y sums
+// on the way.  The last block takes the attempt's Algorithm 5 decision.
 template <typename T>
 struct EpiDual {
     PDHG_SINGLE_LP_TASK_HOOKS
-    const Ctrl* ctrl;
+    Ctrl* ctrl;
     const T* xs0; const T* xs1;     // X[0], X[1]
     T* y0; T* y1; T* kx0; T* kx1;
     T* ys;
     const T* q;
     const uint8_t* sense;
-    double* part;
+    double* part;                   // [2][gridDim.x] partials of this launch
     int cur; T sigma; T pw; int adapt;
     struct Pre { T y = 0, kx = 0, q = 0, ys = 0; uint8_t ge = 0; };
     // per-lane sums in T, reduced in FP64: ||y' - y||^2 and the Algorithm 5
@@ -183,7 +265,11 @@ struct EpiDual {
     // after begin(), the *0 members point at the current half and the *1 members
     // at the other one (x' and the new y, K x' are written there)
     __device__ bool begin() {
-        if (ctrl->skip) return false;
+        if (ctrl->skip) {
+            // a slot after a pending check or the end: its K^T launch does nothing
+            if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->t_mode = 0;
+            return false;
+        }
         cur = ctrl->cur;
         if (cur) {
             const T* t = xs0; xs0 = xs1; xs1 = t;
@@ -220,6 +306,98 @@ struct EpiDual {
         if (adapt) {
             const double t[2] = {(double)a.dy2, (double)a.inter};
             block_partials<2, kSpmvNT>(t, part, gridDim.x);
+        }
+        // ||x' - x||^2 partials: Ctrl::px[0, npx) (kept in the control block, not in
+        // this epilogue, whose members live in registers through the whole SpMV)
+        last_block_decide<kSpmvNT>(ctrl, part, gridDim.x, ctrl->px, ctrl->npx, adapt != 0, adapt,
+                                   true);
+    }
+};
+
+// K^T launch of a PDHG attempt, after the decision (Ctrl::t_mode).
+//  1, 2 (accepted; cur already points at (x', y')): K^T y' -> KTY[cur]; per column
+//       the accepted x'_j enters the eta-weighted sum (weight pw = the eta the step
+//       was taken with); mode 1 also forms the next candidate
+//       x''_j = clamp(x'_j - tau' (c_j - (K^T y')_j), l_j, u_j) -> X[cur ^ 1] with the
+//       ||x'' - x'||^2 block partials (tau' from the new eta').
+//  3 (rejected): no product; every block runs the elementwise retry
+//       x'' = clamp(x - tau' (c - K^T y), l, u) from the kept K^T y, and returns.
+//  Without F (the primal step not fused), modes 1 and 2 only store K^T y' and
+//  add x' to the sums, mode 3 does nothing here, and k_primal follows.
+template <typename T, bool F>
+struct EpiPrimalStep {
+    PDHG_SINGLE_LP_TASK_HOOKS
+    const Ctrl* ctrl;
+    T* xs0; T* xs1;                 // X[0], X[1]
+    const T* ys0; const T* ys1;     // Y[0], Y[1]
+    T* kty0; T* kty1;               // KTY[0], KTY[1]
+    const T* c; const T* l; const T* u;
+    T* xsum;
+    double* part;                   // [gridDim.x] ||x'' - x'||^2 partials
+    int64_t n;
+    int mode; T tau; T pw; int adapt;
+    struct Pre { T x = 0, c = 0, l = 0, u = 0, s = 0; };
+    struct Acc { T dx2 = T(0); };
+    // after begin(): xs0 / ys0 / kty0 are the current half (x', y', K^T y'),
+    // xs1 the other half (the next candidate goes there)
+    __device__ bool begin() {
+        mode = ctrl->t_mode;
+        if (mode == 0) return false;
+        if (ctrl->cur) {
+            T* t = xs0; xs0 = xs1; xs1 = t;
+            const T* v = ys0; ys0 = ys1; ys1 = v;
+            t = kty0; kty0 = kty1; kty1 = t;
+        }
+        const StepScalars<T>& sc = step_scalars<T>(*ctrl);
+        tau = sc.tau;
+        pw = sc.pw;
+        adapt = ctrl->adaptive;
+        if (!F && mode == 1) mode = 2;
+        if (mode != 3) return true;
+        if (!F) return false;
+        // rejected attempt: the retry's candidate from the kept K^T y
+        T dx2 = T(0);
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            const T xj = xs0[j];
+            T v = xj - tau * (c[j] - kty0[j]);
+            const T lo = l[j], hi = u[j];
+            if (v < lo) v = lo;
+            if (v > hi) v = hi;
+            xs1[j] = v;
+            dx2 += (v - xj) * (v - xj);
+        }
+        const double t[1] = {(double)dx2};
+        block_partials<1, kSpmvNT>(t, part, gridDim.x);
+        return false;
+    }
+    __device__ const T* xin() const { return ys0; }   // y'
+    __device__ Pre load(int j) const {
+        Pre p;
+        p.x = xs0[j];
+        if (pw != T(0)) p.s = xsum[j];
+        if (mode == 1) {
+            p.c = c[j];
+            p.l = l[j];
+            p.u = u[j];
+        }
+        return p;
+    }
+    __device__ void row(int j, T ktyn, const Pre& p, Acc& a) const {
+        kty0[j] = ktyn;
+        if (pw != T(0)) xsum[j] = p.s + pw * p.x;
+        if (mode == 1) {
+            T v = p.x - tau * (p.c - ktyn);
+            if (v < p.l) v = p.l;
+            if (v > p.u) v = p.u;
+            xs1[j] = v;
+            a.dx2 += (v - p.x) * (v - p.x);
+        }
+    }
+    __device__ void finish(Acc& a) const {
+        if (mode == 1 && adapt) {
+            const double t[1] = {(double)a.dx2};
+            block_partials<1, kSpmvNT>(t, part, gridDim.x);
         }
     }
 };
@@ -286,11 +464,11 @@ struct EpiHalpernDual {
     }
 };
 
-// K^T y' SpMV; the last block to finish sums the Algorithm 5 partials of the
-// attempt (||x' - x||^2 from k_primal, ||y' - y||^2 and the interaction from the
-// K x' launch; fixed order; the same terms of a Halpern iteration) and takes
-// the step decision, so the attempt needs no separate control launch.  No block waits for another: the last block is
-// the one whose ticket completes the count.
+// K^T y+ SpMV of a Halpern iteration; the last block sums the iteration's
+// partials (||x^ - x||^2 from k_primal_halpern, ||y^ - y||^2 and the interaction
+// from the K x^ launch; fixed order), records the fixed-point residual and
+// advances the iteration (step_decide), so the iteration needs no separate
+// control launch.
 template <typename T>
 struct EpiPrimalT {
     PDHG_SINGLE_LP_TASK_HOOKS
@@ -321,38 +499,14 @@ struct EpiPrimalT {
     __device__ Pre load(int) const { return Pre{}; }
     __device__ void row(int j, T ktyn, const Pre&, Acc&) const { kty1[j] = ktyn; }
     __device__ void finish(Acc&) const {
-        __shared__ int last;
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) last = atomicAdd(&ctrl->tick, 1u) == gridDim.x - 1;
-        __syncthreads();
-        if (!last) return;
-        __threadfence();
-        // warps 0..2 sum the three partial arrays side by side (fixed order:
-        // lane-strided sums, then the warp's tree)
-        __shared__ double tot[3];
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const bool sums = adapt || halp;
-        if (sums && warp < 3) {
-            const double* src = warp == 0 ? partD : warp == 1 ? partD + nD : partP;
-            const int cnt = warp == 2 ? nP : nD;
-            double v = 0.0;
-            for (int i = lane; i < cnt; i += 32) v += __ldcg(src + i);
-            v = warp_sum(v);
-            if (lane == 0) tot[warp] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            ctrl->tick = 0;
-            if (sums) step_decide(ctrl, adapt, tot[0], tot[2], tot[1]);
-            else step_decide(ctrl, adapt, 0.0, 0.0, 0.0);
-        }
+        last_block_decide<kSpmvNT>(ctrl, partD, nD, partP, nP, adapt || halp, adapt, false);
     }
 };
 
 // ------------------------------------------------------------------ check kernels
 
-// Adds the pending iterate to the sums and materialises the averages.  An
+// Adds the pending y of the last accepted iterate to the y sums (its x was
+// added by the K^T launch of its attempt) and materialises the averages.  An
 // average of points of X (resp. Y) lies in X (resp. Y); the projection applied
 // here only removes the rounding of the running sums (it matters for FP32 sums).
 // Halpern iterations have no averages: only the start check copies z to XA, YA.
@@ -383,9 +537,7 @@ k_check_prep(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* y
     for (int64_t t = (int64_t)blockIdx.x * kEW + threadIdx.x; t < n + m;
          t += (int64_t)gridDim.x * kEW) {
         if (t < n) {
-            T s = xs[t];
-            if (pw != T(0)) { s += pw * x[t]; xs[t] = s; }
-            T a = s * winv;
+            T a = xs[t] * winv;
             if (a < l[t]) a = l[t];
             if (a > u[t]) a = u[t];
             xa[t] = a;
@@ -543,6 +695,7 @@ __global__ void k_set_cond(Ctrl* ctrl, cudaGraphConditionalHandle handle, int us
 {
     if (in_body) ctrl->bodies += 1;
     ctrl->want_check = 0;
+    ctrl->t_mode = 0;
     ctrl->restart = 0;
     ctrl->skip = ctrl->done;
     if (use_handle) cudaGraphSetConditional(handle, ctrl->done ? 0u : 1u);
@@ -627,11 +780,29 @@ static int primal_grid(int64_t n)
     return g < PDHG_PRIMAL_GRID ? g : PDHG_PRIMAL_GRID;
 }
 
+// Whether the primal step of a PDHG attempt runs in the K^T launch's epilogue.
+// FP32: yes (on the 1M x 2M power-law LP the K^T launch with the fused step
+// takes 109 us against 114 + 16 us for the product and a separate primal
+// kernel).  FP64: no; its five prefetched operands per row (two rows per lane)
+// spill registers in the SpMV, and the fused launch took 247 us against
+// 183 + 33 us for the product and k_primal after it.
+#ifndef PDHG_FUSE_PRIMAL_F32
+#define PDHG_FUSE_PRIMAL_F32 1
+#endif
+#ifndef PDHG_FUSE_PRIMAL_F64
+#define PDHG_FUSE_PRIMAL_F64 0
+#endif
+template <typename T> struct FusePrimal { static constexpr bool value = PDHG_FUSE_PRIMAL_F32 != 0; };
+template <> struct FusePrimal<double> { static constexpr bool value = PDHG_FUSE_PRIMAL_F64 != 0; };
+
+// a candidate x' from X[cur], KTY[cur]: after a check (and at the start), or
+// after an unfused K^T launch; the K^T launch's grid, so that the ||x' - x||^2
+// partials always number E.gT
 template <typename T>
-static void launch_primal(Handle* h, Engine<T>& E, cudaStream_t st)
+static void launch_primal(Handle* h, Engine<T>& E, cudaStream_t st, int after_step = 0)
 {
-    k_primal<T><<<primal_grid<T>(h->n), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1],
-                                                       E.c, E.l, E.u, E.XS, h->n, E.partT);
+    k_primal<T><<<E.gT, kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c, E.l, E.u,
+                                      h->n, E.partT, after_step);
 }
 
 template <typename T>
@@ -642,6 +813,18 @@ static void launch_dual(Handle* h, Engine<T>& E, cudaStream_t st)
     launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed);
 }
 
+template <typename T>
+static void launch_primal_step(Handle* h, Engine<T>& E, cudaStream_t st, bool with_primal = true)
+{
+    constexpr bool F = FusePrimal<T>::value;
+    EpiPrimalStep<T, F> ep{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KTY[0], E.KTY[1], E.c, E.l,
+                           E.u, E.XS, E.partT, h->n};
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval,
+                   h->dev_err, h->m, ep);
+    if (!F && with_primal) launch_primal<T>(h, E, st, 1);
+}
+
+// K^T launch of a Halpern iteration (its last block advances the iteration)
 template <typename T>
 static void launch_primal_t(Handle* h, Engine<T>& E, cudaStream_t st)
 {
@@ -667,23 +850,30 @@ static void launch_dual_halpern(Handle* h, Engine<T>& E, cudaStream_t st)
                    h->dev_err, h->n, ed);
 }
 
-// one step attempt: 3 launches
+// one step attempt: 2 launches (PDHG) or 3 (a Halpern iteration)
 template <typename T>
 static void launch_attempt(Handle* h, Engine<T>& E, cudaStream_t st, bool halpern)
 {
     if (halpern) {
         launch_primal_halpern<T>(h, E, st);
         launch_dual_halpern<T>(h, E, st);
+        launch_primal_t<T>(h, E, st);
     } else {
-        launch_primal<T>(h, E, st);
         launch_dual<T>(h, E, st);
+        launch_primal_step<T>(h, E, st);
     }
-    launch_primal_t<T>(h, E, st);
 }
 
+// launches of one attempt and of one check
+template <typename T>
+inline int attempt_launches(bool halpern) { return halpern ? 3 : (FusePrimal<T>::value ? 2 : 3); }
+inline int check_launches(bool halpern) { return halpern ? 9 : 10; }
+
+// The check (every kernel gated on Ctrl::want_check); PDHG loops end it with
+// k_primal, the first candidate of the next period.
 template <typename T>
 static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphConditionalHandle hd,
-                         int use_handle, int in_body)
+                         int use_handle, int in_body, bool halpern)
 {
     const int64_t m = h->m, n = h->n;
     k_check_prep<T><<<ew_grid(n + m), kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.XS,
@@ -703,6 +893,7 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
     k_restart_apply<T><<<ew_grid(n + m), kEW, 0, st>>>(
         E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.KTY[0], E.KTY[1], E.XA, E.YA,
         E.KXA, E.KTYA, E.XANC, E.YANC, E.KXANC, E.XS, E.YS, n, m);
+    if (!halpern) launch_primal<T>(h, E, st);
     k_set_cond<<<1, 1, 0, st>>>(E.ctrl, hd, use_handle, in_body);
 }
 
@@ -748,7 +939,7 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
         LP_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal));
         for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st, halpern != 0);
-        launch_check<T>(h, E, st, hd, 1, 1);
+        launch_check<T>(h, E, st, hd, 1, 1, halpern != 0);
         cudaGraph_t captured = nullptr;
         LP_CUDA_TRY(cudaStreamEndCapture(st, &captured));
         LP_CUDA_TRY(cudaGraphInstantiate(&E.exec, graph, 0));
@@ -757,7 +948,7 @@ static lp_status build_graph(Handle* h, Engine<T>& E, int check_every, int slots
         cudaGraphDestroy(graph);
         LP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         for (int s = 0; s < slots; ++s) launch_attempt<T>(h, E, st, halpern != 0);
-        launch_check<T>(h, E, st, hd, 0, 1);
+        launch_check<T>(h, E, st, hd, 0, 1, halpern != 0);
         cudaGraph_t g2 = nullptr;
         LP_CUDA_TRY(cudaStreamEndCapture(st, &g2));
         LP_CUDA_TRY(cudaGraphInstantiate(&E.body_exec, g2, 0));
@@ -784,6 +975,7 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     LP_CUDA_TRY((spmv_prepare<T, EpiStore<T>>()));
     LP_CUDA_TRY((spmv_prepare<T, EpiDual<T>>()));
     LP_CUDA_TRY((spmv_prepare<T, EpiPrimalT<T>>()));
+    LP_CUDA_TRY((spmv_prepare<T, EpiPrimalStep<T, FusePrimal<T>::value>>()));
     LP_CUDA_TRY((spmv_prepare<T, EpiHalpernDual<T>>()));
     LP_TRY(engine_factors<T>(h));
     if (o->autotune) LP_TRY(tune_engine<T>(h));
@@ -821,8 +1013,17 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
         E.trace_cap = cap;
     }
 
+    // device attempt log (when the caller asked for one)
+    long long acap = h->alog_host ? std::max<long long>(0, h->alog_cap_host - h->alog_off) : 0;
+    if (acap > E.alog_cap) {
+        LP_TRY(dev_alloc_n(h, &E.alog, (size_t)acap * kAttemptFields));
+        E.alog_cap = acap;
+    }
+
     Ctrl c;
     std::memset(&c, 0, sizeof(c));
+    c.alog = acap > 0 ? E.alog : nullptr;
+    c.alog_cap = acap;
     c.eta = eta0;
     c.omega = omega0;
     c.kkt_prev = INFINITY;
@@ -854,6 +1055,8 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     c.infeas = o->infeas_detect && !halpern ? 1 : 0;
     c.infeas_tol = o->infeas_tol;
     c.check_every = o->check_every;
+    c.px = E.partT;
+    c.npx = E.gT;
     refresh_scalars(c);
     {
         // the time origin is the device clock read now
@@ -867,9 +1070,10 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     LP_CUDA_TRY(cudaMemcpyAsync(E.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
 
     // the start-point check (KKT of z^0, anchor)
-    launch_check<T>(h, E, st, cudaGraphConditionalHandle{}, 0, 0);
+    launch_check<T>(h, E, st, cudaGraphConditionalHandle{}, 0, 0, halpern != 0);
     LP_CUDA_TRY(cudaGetLastError());
-    h->launches += 3 + 1 + 9;   // start state, its two products, the clock read, the start check
+    // start state, its two products, the clock read, the start check
+    h->launches += 3 + 1 + check_launches(halpern != 0);
 
     const int slots = o->check_every + (c.adaptive ? 4 : 0);
     LP_TRY(build_graph<T>(h, E, o->check_every, slots, o->loop_mode == 1 ? 1 : 0, halpern));
@@ -886,13 +1090,22 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
             LP_CUDA_TRY(cudaGraphLaunch(E.body_exec, st));
         }
     }
-    // loop bodies ran on the device: each is `slots` attempts of 3 launches + 9 check launches
-    h->launches += out->bodies * (long long)(slots * 3 + 9);
+    // loop bodies ran on the device: each is `slots` attempts and one check
+    h->launches += out->bodies * (long long)(slots * attempt_launches<T>(halpern != 0) +
+                                             check_launches(halpern != 0));
     {
         int derr = 0;
         LP_CUDA_TRY(cudaMemcpyAsync(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         LP_CUDA_TRY(cudaStreamSynchronize(st));
         if (derr) return LP_DEVICE_TIMEOUT;
+    }
+    if (acap > 0) {
+        const long long got = std::min<long long>(out->alog_len, acap);
+        if (got > 0)
+            LP_CUDA_TRY(cudaMemcpyAsync(h->alog_host + kAttemptFields * h->alog_off, E.alog,
+                                        sizeof(double) * kAttemptFields * got,
+                                        cudaMemcpyDeviceToHost, st));
+        LP_CUDA_TRY(cudaStreamSynchronize(st));
     }
     if (trace_host && cap > 0) {
         const long long got = std::min<long long>(out->trace_len, cap);
@@ -965,22 +1178,36 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes)
     c.check_every = 1 << 30;
     c.time_limit_ns = 1e18;
     c.tick = 0;
+    c.alog = nullptr;
     LP_CUDA_TRY(cudaMemcpyAsync(E.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
     cudaEvent_t ev[4];
     for (auto& e : ev) LP_CUDA_TRY(cudaEventCreate(&e));
     double acc[3] = {0, 0, 0};
     const bool halp = E.graph_halpern == 1;   // the loop of the last lp_solve
+    if (!halp) {
+        // the candidate x' of the first timed attempt (the check gate of k_primal)
+        c.want_check = 1;
+        LP_CUDA_TRY(cudaMemcpyAsync(E.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+        launch_primal<T>(h, E, st);
+        c.want_check = 0;
+        LP_CUDA_TRY(cudaMemcpyAsync(E.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+        h->launches += 1;
+    }
+    // ev[0..3] bracket three launches: Halpern: primal, K side, K^T side; PDHG:
+    // K side (with the decision), K^T side, then the unfused primal step (if any)
+    constexpr bool F = FusePrimal<T>::value;
     for (int r = 0; r < reps + 2; ++r) {
         cudaEventRecord(ev[0], st);
         if (halp) launch_primal_halpern<T>(h, E, st);
-        else launch_primal<T>(h, E, st);
+        else launch_dual<T>(h, E, st);
         cudaEventRecord(ev[1], st);
         if (halp) launch_dual_halpern<T>(h, E, st);
-        else launch_dual<T>(h, E, st);
+        else launch_primal_step<T>(h, E, st, false);
         cudaEventRecord(ev[2], st);
-        launch_primal_t<T>(h, E, st);
+        if (halp) launch_primal_t<T>(h, E, st);
+        else if (!F) launch_primal<T>(h, E, st, 1);
         cudaEventRecord(ev[3], st);
-        h->launches += 3;
+        h->launches += halp ? 3 : attempt_launches<T>(false);
         LP_CUDA_TRY(cudaGetLastError());
         LP_CUDA_TRY(cudaEventSynchronize(ev[3]));
         if (r >= 2) {
@@ -991,22 +1218,32 @@ lp_status profile_step(Handle* h, int reps, double* ms, double* bytes)
             }
         }
     }
+    if (!halp) {
+        // order as for Halpern: [0] primal, [1] K side, [2] K^T side
+        const double a0 = acc[0], a1 = acc[1], a2 = acc[2];
+        acc[0] = a2;
+        acc[1] = a0;
+        acc[2] = a1;
+    }
     for (auto& e : ev) cudaEventDestroy(e);
     for (int k = 0; k < 3; ++k) ms[k] = acc[k] / reps;
     ms[3] = 0.0;
+    const bool fused = !halp && F;
     if (bytes) {
         const double s = sizeof(T);
-        // primal: read x, c, l, u, K^T y, x-sum; write x', x-sum
-        // (Halpern: read x, c, l, u, K^T y, x-anchor; write x^, x+: the same count)
-        bytes[0] = (double)n * 8 * s;
+        // Halpern primal: read x, c, l, u, K^T y, x-anchor; write x^, x+; the
+        // unfused PDHG primal step: read x, K^T y, c, l, u; write x'
+        bytes[0] = halp ? (double)n * 8 * s : (fused ? 0.0 : (double)n * 6 * s);
         // K x' + dual: values + indices + row pointers (int64) + x' (each element
         // gathered at least once) + y, q, K x, y-sum, sense read; y', K x', y-sum written
         // (Halpern: y, q, K x, y-anchor, K x-anchor, sense read; y+, K x+ written)
         bytes[1] = (double)nnz * (s + 4) + (double)(m + 1) * 8 + (double)n * s +
                    (double)m * (7 * s + 1);
-        // K^T y' + step terms: values + indices + row pointers + y'; K^T y' written;
-        // x, x', K^T y read
-        bytes[2] = (double)nnz * (s + 4) + (double)(n + 1) * 8 + (double)m * s + (double)n * s;
+        // K^T y' (values + indices + row pointers + y' gathered; K^T y' written);
+        // PDHG adds the fused primal step: x', c, l, u, x-sum read; x'', x-sum written
+        // (unfused: x', x-sum read and x-sum written)
+        bytes[2] = (double)nnz * (s + 4) + (double)(n + 1) * 8 + (double)m * s + (double)n * s +
+                   (halp ? 0.0 : (fused ? (double)n * 7 * s : (double)n * 3 * s));
         bytes[3] = 0.0;
     }
     return LP_OK;

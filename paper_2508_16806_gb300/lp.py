@@ -27,7 +27,7 @@ STATUS = {0: "LP_OK", 1: "LP_OPTIMAL", 2: "LP_PRIMAL_INFEASIBLE", 3: "LP_DUAL_IN
           -1: "LP_INVALID_ARGUMENT", -2: "LP_CUDA_ERROR", -3: "LP_OUT_OF_MEMORY",
           -4: "LP_DEVICE_TIMEOUT", -5: "LP_NOT_SUPPORTED"}
 LP_OPTIMAL, LP_ITERATION_LIMIT, LP_TIME_LIMIT, LP_NUMERICAL_ERROR = 1, 4, 5, 6
-LP_INVALID_ARGUMENT = -1
+LP_INVALID_ARGUMENT, LP_NOT_SUPPORTED = -1, -5
 
 
 class LpDesc(C.Structure):
@@ -53,8 +53,13 @@ class LpOpts(C.Structure):
                 ("warm_memory_space", C.c_int32), ("loop_mode", C.c_int32),
                 ("infeas_detect", C.c_int32), ("reserved_opts", C.c_int32),
                 ("infeas_tol", C.c_double), ("autotune", C.c_int32),
-                ("halpern", C.c_int32), ("halpern_reflect", C.c_double)]
+                ("halpern", C.c_int32), ("halpern_reflect", C.c_double),
+                ("pc_alpha", C.c_double), ("pc_trial_iters", C.c_int32),
+                ("reserved_opts2", C.c_int32), ("attempt_log", C.c_void_p),
+                ("attempt_cap", C.c_int64)]
 
+
+ATTEMPT_FIELDS = ("k", "eta", "eta_bar", "eta_next", "accept", "omega", "dx2", "dy2", "inter")
 
 TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",
                 "kkt_cur", "kkt_avg", "rel_gap", "rel_pres", "rel_dres", "kkt_cand")
@@ -75,11 +80,13 @@ class LpResult(C.Structure):
                 ("kernel_launches", C.c_int64),
                 ("x", C.c_void_p), ("y", C.c_void_p),
                 ("memory_space", C.c_int32), ("reserved", C.c_int32),
-                ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("trace_len", C.c_int64)]
+                ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("trace_len", C.c_int64),
+                ("pc_alpha_used", C.c_double), ("attempt_len", C.c_int64)]
 
 
 EXPORTS = ("lp_opts_default", "lp_create", "lp_solve", "lp_solve_batch", "lp_grad",
-           "lp_unroll", "lp_update_values", "lp_profile_step", "lp_destroy", "lp_status_string",
+           "lp_unroll", "lp_update_values", "lp_profile_step", "lp_profile_gather", "lp_destroy",
+           "lp_status_string",
            "lp_abi_version", "lp_kkt_noalloc", "lp_batch_create", "lp_batch_solve",
            "lp_batch_destroy", "lp_fishnet", "lp_fishnet_draws")
 
@@ -115,6 +122,8 @@ def load(build_if_missing: bool = True):
     lib.lp_grad.restype = C.c_int
     lib.lp_profile_step.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
     lib.lp_profile_step.restype = C.c_int
+    lib.lp_profile_gather.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
+    lib.lp_profile_gather.restype = C.c_int
     lib.lp_destroy.argtypes = [C.c_void_p]
     lib.lp_destroy.restype = None
     lib.lp_status_string.argtypes = [C.c_int]
@@ -200,6 +209,15 @@ def lp_fishnet_draws(P: int) -> int:
 def lp_update_values(h, vals=None, c=None, q=None, l=None, u=None,
                      memory_space: int = LP_MEM_DEVICE) -> int:
     return load().lp_update_values(h, vals, c, q, l, u, memory_space)
+
+
+def lp_profile_gather(h, precision: int, reps: int, blocks_per_sm: int = 4):
+    """Milliseconds per launch of the minimal gather loop over K and over K^T."""
+    ms = (C.c_double * 2)()
+    s = load().lp_profile_gather(h, precision, reps, blocks_per_sm, C.cast(ms, C.c_void_p))
+    if s != 0:
+        raise LpError(s, "lp_profile_gather")
+    return list(ms)
 
 
 def lp_profile_step(h, precision: int, reps: int):
@@ -308,12 +326,20 @@ class Problem:
         except Exception:
             pass
 
-    def solve(self, trace_cap: int = 0, out_device: bool = False, x0=None, y0=None, **opts):
+    def solve(self, trace_cap: int = 0, out_device: bool = False, x0=None, y0=None,
+              attempt_cap: int = 0, **opts):
         """Returns (x, y, info, trace).  x, y are numpy (or torch CUDA tensors
-        with out_device=True); info is a dict of the lp_result scalars."""
+        with out_device=True); info is a dict of the lp_result scalars.  With
+        attempt_cap > 0, info["attempt_log"] lists up to that many step attempts
+        (dicts of ATTEMPT_FIELDS)."""
         torch = _torch()
         o = lp_opts_default(**opts)
         keep = []
+        alog = None
+        if attempt_cap > 0:
+            alog = np.zeros((attempt_cap, len(ATTEMPT_FIELDS)))
+            o.attempt_log = alog.ctypes.data
+            o.attempt_cap = attempt_cap
         if x0 is not None or y0 is not None:
             wx = np.ascontiguousarray(x0, np.float64) if x0 is not None else None
             wy = np.ascontiguousarray(y0, np.float64) if y0 is not None else None
@@ -342,6 +368,9 @@ class Problem:
             raise LpError(s, "lp_solve")
         info = {f: getattr(res, f) for f, _ in LpResult._fields_
                 if f not in ("x", "y", "trace", "reserved", "memory_space", "trace_cap")}
+        if alog is not None:
+            info["attempt_log"] = [dict(zip(ATTEMPT_FIELDS, r.tolist()))
+                                   for r in alog[: res.attempt_len]]
         trace = []
         if tr is not None:
             for r in tr[: min(res.trace_len, trace_cap)]:
@@ -367,6 +396,10 @@ class Problem:
 
     def profile_step(self, precision: int = LP_PREC_FP64, reps: int = 20):
         return lp_profile_step(self.handle, precision, reps)
+
+    def profile_gather(self, precision: int = LP_PREC_MIXED, reps: int = 20,
+                       blocks_per_sm: int = 4):
+        return lp_profile_gather(self.handle, precision, reps, blocks_per_sm)
 
 
 class Batch:

@@ -42,7 +42,7 @@ def test_host_only_calls_without_gpu():
     assert o.halpern == 0 and o.halpern_reflect == 1.0
     assert L.lp_status_string(1) == "LP_OPTIMAL"
     assert L.lp_status_string(-1) == "LP_INVALID_ARGUMENT"
-    assert L.load().lp_abi_version() == 4
+    assert L.load().lp_abi_version() == 5
 
 
 def test_binding_mirrors_struct_sizes():
@@ -54,9 +54,10 @@ def test_binding_mirrors_struct_sizes():
 #include <stddef.h>
 #include "lp.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(lp_desc), sizeof(lp_opts), sizeof(lp_result),
-         sizeof(lp_trace_rec), offsetof(lp_result, x), offsetof(lp_opts, x0),
-         offsetof(lp_opts, halpern_reflect));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lp_desc), sizeof(lp_opts),
+         sizeof(lp_result), sizeof(lp_trace_rec), offsetof(lp_result, x), offsetof(lp_opts, x0),
+         offsetof(lp_opts, halpern_reflect), offsetof(lp_opts, pc_alpha),
+         offsetof(lp_result, pc_alpha_used));
   return 0;
 }
 '''
@@ -68,5 +69,6 @@ int main(void) {
         got = [int(t) for t in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(L.LpDesc), ctypes.sizeof(L.LpOpts), ctypes.sizeof(L.LpResult),
             ctypes.sizeof(L.LpTraceRec), L.LpResult.x.offset, L.LpOpts.x0.offset,
-            L.LpOpts.halpern_reflect.offset]
+            L.LpOpts.halpern_reflect.offset, L.LpOpts.pc_alpha.offset,
+            L.LpResult.pc_alpha_used.offset]
     assert got == want

@@ -151,6 +151,45 @@ def test_autograd_function(L, oracle_mod):
     assert rel(v.grad.cpu().numpy(), ov) < 1e-10
 
 
+def test_autograd_two_forwards_then_backward_of_first(L, oracle_mod):
+    """Two forwards on one Problem with different values, then backward of the
+    first: the gradient is that of the first LP (its values are put back on the
+    handle), with step sizes derived from the first LP (eta, omega = None)."""
+    import dataclasses
+    import torch
+    from paper_2508_16806_gb300.autograd import UnrolledPDHG
+    lp, xt = synth.adjoint_lp(50, 100, 8, seed=12)
+    rng = np.random.default_rng(99)
+    lpb = synth.LP(**{f.name: getattr(lp, f.name) for f in dataclasses.fields(lp)})
+    lpb.c = lp.c + rng.normal(0, 0.5, lp.n)
+    lpb.vals = lp.vals * rng.uniform(0.5, 1.5, lp.nnz)
+    prob = L.Problem(lp)
+    dev = dict(device="cuda", dtype=torch.float64)
+    ca = torch.tensor(lp.c, requires_grad=True, **dev)
+    qa = torch.tensor(lp.q, requires_grad=True, **dev)
+    va = torch.tensor(lp.vals, requires_grad=True, **dev)
+    xa = UnrolledPDHG.apply(ca, qa, va, prob, 80, 20, L.LP_PREC_FP64, None, None)
+    cb = torch.tensor(lpb.c, requires_grad=True, **dev)
+    qb = torch.tensor(lpb.q, requires_grad=True, **dev)
+    vb = torch.tensor(lpb.vals, requires_grad=True, **dev)
+    xb = UnrolledPDHG.apply(cb, qb, vb, prob, 80, 20, L.LP_PREC_FP64, None, None)
+    loss_a = ((xa - torch.tensor(xt, **dev)) ** 2).sum()
+    loss_a.backward()
+    # the first LP's own step sizes: eta_scale / ||K||_2 (Algorithm 2 on the
+    # unscaled K, as lp_grad takes them) and ||c|| / ||q||
+    eta = 0.9 / oracle_mod.power_norm(lp, 100)
+    omega = np.linalg.norm(lp.c) / np.linalg.norm(lp.q)
+    tau, sigma = eta / omega, eta * omega
+    xs, _ = oracle_mod.unrolled_forward(lp, tau, sigma, 80)
+    assert rel(xa.detach().cpu().numpy(), xs[-1]) < 1e-8
+    oc, oq, ov = oracle_mod.unrolled_adjoint(lp, tau, sigma, 80, 2.0 * (xs[-1] - xt))
+    assert rel(ca.grad.cpu().numpy(), oc) < 1e-8
+    assert rel(qa.grad.cpu().numpy(), oq) < 1e-8
+    assert rel(va.grad.cpu().numpy(), ov) < 1e-8
+    assert xb.shape == xa.shape and cb.grad is None
+    prob.close()
+
+
 def test_fp32_gradient_close_to_fp64(L, oracle_mod):
     """The FP32 adjoint (FP64 accumulation of dc, dq, dvals) stays close to the
     FP64 one on an m = 5000 instance; the error is reported in the assertion."""

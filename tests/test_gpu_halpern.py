@@ -104,16 +104,24 @@ def test_mixed_halpern_solves(L, oracle_mod, name, tol):
 
 def test_fp32_phase_caps_reflection(L):
     """The FP32 phase of LP_PREC_MIXED runs with min(rho, 1/2): rho = 1 and
-    rho = 1/2 give the same FP32 run, and it reaches the hand-over tolerance."""
+    rho = 1/2 give the same FP32 run (the same check records up to its last
+    check), and it reaches the hand-over tolerance; the FP64 check then decides
+    whether FP64 iterations follow."""
     lp = PROBS["ragged"]
     prob = L.Problem(lp)
     a = prob.solve(tol=1e-5, max_iters=400000, precision=L.LP_PREC_MIXED, halpern=1,
-                   halpern_reflect=1.0)
+                   halpern_reflect=1.0, trace_cap=100000)
     b = prob.solve(tol=1e-5, max_iters=400000, precision=L.LP_PREC_MIXED, halpern=1,
-                   halpern_reflect=0.5)
-    assert a[2]["status"] == L.LP_OPTIMAL and a[2]["precision_used"] == L.LP_PREC_MIXED
-    assert a[2]["iters"] == b[2]["iters"]
-    np.testing.assert_array_equal(a[0], b[0])
+                   halpern_reflect=0.5, trace_cap=100000)
+    assert a[2]["status"] == b[2]["status"] == L.LP_OPTIMAL
+    k32 = a[2]["iters"] - a[2]["fp64_iters"]
+    assert k32 == b[2]["iters"] - b[2]["fp64_iters"]
+    # records of the FP32 phase: up to its last check, at k32 (the FP64 start
+    # check that follows has the same k)
+    n32 = next(i for i, r in enumerate(a[3]) if r["k"] == k32) + 1
+    assert a[3][:n32] == b[3][:n32]
+    assert a[3][n32 - 1]["k"] == k32 and max(a[3][n32 - 1][f] for f in
+                                            ("rel_gap", "rel_pres", "rel_dres")) <= 1e-5
 
 
 def test_halpern_profile_step(L):
@@ -144,19 +152,25 @@ def test_halpern_then_pdhg_on_one_handle(L, oracle_mod):
 
 
 def test_halpern_stop_between_checks_returns_last_candidate(L, oracle_mod):
-    """A loop stopped between two checks (by the time limit, after about two
-    thousand iterations) returns the candidate of the last check: its x and y
-    belong together, so the oracle's FP64 termination quantities of the returned
-    pair are the ones that check reported."""
+    """A loop stopped by the time limit returns the candidate of the last check:
+    its x and y belong together, so the oracle's FP64 termination quantities of
+    the returned pair are the ones that check recorded.  Several limits are
+    tried; whatever iteration each run stops at, the pair must match the last
+    trace record, and at least one run must stop between two checks (iterations
+    not a multiple of check_every), the case the candidate buffers exist for."""
     lp = PROBS["powerlaw"]
     prob = L.Problem(lp)
-    x, y, info, tr = prob.solve(tol=1e-14, max_iters=10**9, time_limit_s=0.05, halpern=1,
-                                trace_cap=100000)
-    assert info["status"] == L.LP_TIME_LIMIT
-    assert len(tr) > 3
-    k = oracle_mod.kkt(lp, x, y)
-    for f in ("rel_gap", "rel_pres", "rel_dres"):
-        assert k[f] == pytest.approx(info[f], rel=1e-6, abs=1e-12), (f, k[f], info[f])
+    between = 0
+    for limit in (0.02, 0.05, 0.11, 0.23):
+        x, y, info, tr = prob.solve(tol=1e-14, max_iters=10**9, time_limit_s=limit, halpern=1,
+                                    trace_cap=100000)
+        assert info["status"] == L.LP_TIME_LIMIT
+        k = oracle_mod.kkt(lp, x, y)
+        for f in ("rel_gap", "rel_pres", "rel_dres"):
+            assert tr[-1][f] == info[f]
+            assert k[f] == pytest.approx(info[f], rel=1e-6, abs=1e-12), (limit, f, k[f], info[f])
+        between += int(info["iters"] % 64 != 0)
+    assert between >= 1
 
 
 def test_halpern_options_validated(L):

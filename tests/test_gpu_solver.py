@@ -130,6 +130,37 @@ def test_fp64_adaptive_iterates_track_oracle(L, oracle_mod, name, iters):
     _check_trace(tr, tro)
 
 
+@pytest.mark.parametrize("name", ["lp200x400", "ragged", "shuffled", "powerlaw"])
+def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
+    """Parity of the adaptive path (Algorithm 5) over 1000 iterations by replay:
+    the oracle takes the GPU run's step sizes and accept / reject outcomes from
+    its attempt log and computes everything else itself.  Its iterates then
+    track the GPU's to 1e-10, its own eta_bar agrees with the GPU's at every
+    attempt, every GPU outcome is the one its eta_bar gives (unless eta sits
+    within 1e-8 of eta_bar), and its own eta' from Algorithm 5 is the GPU's."""
+    lp = PROBS[name]
+    prob = L.Problem(lp)
+    x, y, info, tr = prob.solve(tol=1e-13, max_iters=1000, trace_cap=4096, attempt_cap=5000)
+    log = info["attempt_log"]
+    assert info["attempt_len"] == info["attempts"] == len(log) > 1000
+    rows = np.array([[a[f] for f in L.ATTEMPT_FIELDS] for a in log])
+    xo, yo, io, tro, att = oracle_mod.solve_logged(lp, tol=1e-13, max_iters=1000,
+                                                   trace_cap=4096, replay=rows)
+    assert io["iters"] == info["iters"] == 1000 and io["attempts"] == info["attempts"]
+    assert rel(x, xo) <= 1e-10, rel(x, xo)
+    assert rel(y, yo) <= 1e-10, rel(y, yo)
+    _check_trace(tr, tro)
+    rejected = 0
+    for g, o in zip(log, att):
+        assert g["k"] == o["k"] and g["eta"] == o["eta"]
+        assert g["eta_bar"] == pytest.approx(o["eta_bar"], rel=1e-8), (g, o)
+        if abs(g["eta"] - o["eta_bar"]) > 1e-8 * o["eta_bar"]:
+            assert bool(g["accept"]) == (g["eta"] <= o["eta_bar"]), (g, o)
+        assert g["eta_next"] == pytest.approx(o["eta_next"], rel=1e-8), (g, o)
+        rejected += int(not g["accept"])
+    print(name, "rejected attempts", rejected)
+
+
 # ---------------------------------------------------------------- to tolerance
 
 @pytest.mark.parametrize("tol", [1e-4, 1e-8])

@@ -389,3 +389,52 @@ def test_adaptive_step_amplifies_rounding(oracle_mod):
         out[adaptive] = np.linalg.norm(xa - xb) / np.linalg.norm(xa)
     assert out[0] < 1e-13
     assert out[1] > 1e-7
+
+
+# ---------------------------------------------------------------- Pock-Chambolle
+
+def test_pock_chambolle_hand_values(oracle_mod):
+    """The Pock-Chambolle pass for alpha in {0, 1/2, 1, 2} on a hand-worked 2 x 2
+    matrix (tests/golden/pock_chambolle_hand.json): factors and scaled values."""
+    d = _load("pock_chambolle_hand.json")
+    K = np.array(d["K"], dtype=float)
+    lp = synth.from_dense(K, [1, 1], [1.0, 1.0], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0])
+    for case in d["cases"]:
+        vs, R, Cc, passes = oracle_mod.ruiz(lp, 0, 1e-4, pock_chambolle=True,
+                                            pc_alpha=case["alpha"])
+        assert passes == 0
+        np.testing.assert_allclose(R, case["R"], rtol=1e-14, err_msg=case["_work"])
+        np.testing.assert_allclose(Cc, case["C"], rtol=1e-14, err_msg=case["_work"])
+        want = (np.array(case["R"])[:, None] * K * np.array(case["C"])[None, :])[K != 0]
+        np.testing.assert_allclose(vs, want, rtol=1e-14)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.5, 1.0, 2.0])
+def test_pock_chambolle_leaves_the_optimum_unchanged(oracle_mod, alpha):
+    """Section 2.4.1 change of variables with the Pock-Chambolle pass after Ruiz:
+    the unscaled objective at 1e-8 is the planted one for every alpha."""
+    lp = synth.small_dense_lp()
+    x, y, info, _ = oracle_mod.solve(lp, tol=1e-8, pock_chambolle=1, pc_alpha=alpha,
+                                     max_iters=200000)
+    assert info["status"] == 1 and info["pc_alpha"] == alpha
+    assert float(lp.c @ x) == pytest.approx(lp.f_star, rel=1e-6)
+
+
+@pytest.mark.parametrize("name", ["small_dense", "ragged"])
+def test_pock_chambolle_choice(oracle_mod, name):
+    """pock_chambolle = 2: each trial error is that of a separate solve with that
+    alpha, the stated number of iterations, no tolerance and no infeasibility
+    detection; the chosen alpha has the smallest; the tuned solve is the solve
+    with the chosen alpha, bit for bit."""
+    lp = {"small_dense": synth.small_dense_lp, "ragged": synth.ragged_lp}[name]()
+    alpha, errs = oracle_mod.pc_tune(lp, check_every=32)
+    for a, e in zip(oracle_mod.PC_GRID, errs):
+        _, _, info, _ = oracle_mod.solve(lp, pock_chambolle=1, pc_alpha=a, max_iters=64, tol=0.0,
+                                         infeas_detect=0, check_every=32)
+        assert e == max(info["rel_gap"], info["rel_pres"], info["rel_dres"])
+    assert alpha == oracle_mod.PC_GRID[int(np.argmin(errs))]
+    xa, ya, ia, _ = oracle_mod.solve(lp, pock_chambolle=2, check_every=32)
+    xb, yb, ib, _ = oracle_mod.solve(lp, pock_chambolle=1, pc_alpha=alpha, check_every=32)
+    assert ia["pc_alpha"] == alpha
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(ya, yb)

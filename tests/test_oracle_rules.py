@@ -239,3 +239,16 @@ def test_planted_mistake_fails_a_pin(oracle_mod, tmp_path, mutant):
 
 def test_unmodified_oracle_passes_all_pins(oracle_mod):
     assert run_all_pins(oracle_mod) == []
+
+
+def test_replay_of_own_log_reproduces_the_run(oracle_mod):
+    """The replay mode (used to extend GPU parity of the adaptive path): taking
+    the step sizes and outcomes of a run's own attempt log reproduces that run
+    bit for bit, and the replayed run's own eta_bar and eta' equal the logged ones."""
+    lp = synth.ragged_lp()
+    x, y, info, tr, att = oracle_mod.solve_logged(lp, tol=1e-9, max_iters=700)
+    rows = np.array([[a[f] for f in oracle_mod.ATTEMPT_FIELDS] for a in att])
+    x2, y2, i2, tr2, att2 = oracle_mod.solve_logged(lp, tol=1e-9, max_iters=700, replay=rows)
+    np.testing.assert_array_equal(x, x2)
+    np.testing.assert_array_equal(y, y2)
+    assert att == att2 and tr == tr2 and i2["attempts"] == info["attempts"]
