@@ -107,9 +107,10 @@ def gather_ceiling(prob, prec, lp, reps=20):
     """lp_profile_gather: the minimal gather loop over the nonzeros of K and of
     K^T (milliseconds per launch, CUDA events on the solver's stream) and the
     rate of gathers it reaches, for 4 and 8 resident blocks per SM."""
-    out = {}
-    for bps in (4, 8):
+    out = {"by_blocks_per_sm": {}}
+    for bps in (2, 4, 6, 8):
         ms = prob.profile_gather(prec, reps=reps, blocks_per_sm=bps)
+        out["by_blocks_per_sm"][bps] = ms
         for side, t in zip(("K", "KT"), ms):
             cur = out.get(side)
             if cur is None or t < cur["ms"]:
@@ -406,9 +407,14 @@ class OracleTimer:
 def cpu_info():
     out = {"nproc": os.cpu_count()}
     try:
+        keys = {}
         for ln in open("/proc/cpuinfo"):
-            if ln.lower().startswith(("model name", "cpu part", "cpu implementer")):
-                out.setdefault("cpu", ln.split(":", 1)[1].strip())
+            k, _, v = ln.partition(":")
+            k = k.strip().lower()
+            if k in ("model name", "cpu implementer", "cpu part") and k not in keys:
+                keys[k] = v.strip()
+        out["cpu"] = keys.get("model name") or (
+            f"implementer {keys.get('cpu implementer')} part {keys.get('cpu part')}")
         out["machine"] = os.uname().machine
     except Exception:
         pass

@@ -82,6 +82,12 @@ struct Ctrl {
     // accepted, omega, ||dx||^2, ||dy||^2, dy^T K dx (scaled problem)
     double* alog;
     long long alog_cap, alog_len;
+    // the Algorithm 5 factors 1 - (k + 2)^-0.3 and 1 + (k + 2)^-0.6 for
+    // k = ftab_k0 .. ftab_k0 + ftab_len - 1 (ftab[i], ftab[ftab_len + i]), filled by
+    // each check for the period that follows (nullptr: computed in place)
+    const double* ftab;
+    long long ftab_k0;
+    int ftab_len;
     unsigned int tick;   // finished blocks of the launch that takes the step decision (its last block does)
     long long bodies;    // loop-body executions (for the launch count)
     long long t_done_ns; // device clock when the loop finished for this LP
@@ -170,6 +176,8 @@ struct Engine {
     long long trace_cap = 0;
     double* alog = nullptr;         // device attempt log (kAttemptFields per record)
     long long alog_cap = 0;
+    double* ftab = nullptr;         // Algorithm 5 factors of a check period [2][ftab_cap]
+    int ftab_cap = 0;
     // loop graph
     cudaGraphExec_t exec = nullptr;
     int graph_check_every = -1;

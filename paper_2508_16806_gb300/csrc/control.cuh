@@ -134,9 +134,20 @@ __device__ __forceinline__ void step_decide(Ctrl* ctrl, int adapt, double dy2, d
         const double movement = omega * dx2 + dy2 / omega;
         const double eta_bar = inter != 0.0 ? movement / (2.0 * fabs(inter)) : INFINITY;
         if (eta_bar_out) *eta_bar_out = eta_bar;
-        const double kp1 = (double)(ctrl->k + 1) + 1.0;
-        const double e1 = (1.0 - pow(kp1, -0.3)) * eta_bar;
-        const double e2 = (1.0 + pow(kp1, -0.6)) * eta;
+        // (k + 1) of the paper with its k 1-based: accepted iterations + 2; the two
+        // factors come from the period's table when the check filled one
+        const long long ti = ctrl->k - ctrl->ftab_k0;
+        double f3, f6;
+        if (ctrl->ftab && ti >= 0 && ti < ctrl->ftab_len) {
+            f3 = ctrl->ftab[ti];
+            f6 = ctrl->ftab[ctrl->ftab_len + ti];
+        } else {
+            const double kp1 = (double)(ctrl->k + 1) + 1.0;
+            f3 = 1.0 - pow(kp1, -0.3);
+            f6 = 1.0 + pow(kp1, -0.6);
+        }
+        const double e1 = f3 * eta_bar;
+        const double e2 = f6 * eta;
         eta_next = e1 < e2 ? e1 : e2;
         accept = eta <= eta_bar;
         if (!isfinite(movement) || isnan(inter)) {

@@ -619,9 +619,23 @@ k_check_cols(const Ctrl* __restrict__ ctrl, const T* x0, const T* x1, const T* k
 // restart criteria (Section 2.4.2) and Algorithm 4.
 __global__ void __launch_bounds__(kCtlNT)
 k_check_ctrl(Ctrl* ctrl, const double* partR, const double* partC, int nparts,
-             lp_trace_rec* trace)
+             lp_trace_rec* trace, double* ftab)
 {
     if (!ctrl->want_check) return;
+    // Algorithm 5's two factors for the attempts of the coming period (k does not
+    // change in a check): computed here by all threads at once instead of by the
+    // single deciding thread at the end of every K launch, where the two FP64
+    // powers sat on each attempt's critical path
+    if (ftab && ctrl->adaptive) {
+        const int len = ctrl->ftab_len;
+        const long long k0 = ctrl->k;
+        for (int i = threadIdx.x; i < len; i += kCtlNT) {
+            const double kp1 = (double)(k0 + i + 1) + 1.0;
+            ftab[i] = 1.0 - pow(kp1, -0.3);
+            ftab[len + i] = 1.0 + pow(kp1, -0.6);
+        }
+        if (threadIdx.x == 0) ctrl->ftab_k0 = k0;
+    }
     // one warp per reduced quantity (fixed order: lane-strided sums, then the
     // warp's tree); the Algorithm 6 terms only when the check runs it
     __shared__ double red[kRowQ + kColQ];
@@ -810,7 +824,8 @@ static void launch_dual(Handle* h, Engine<T>& E, cudaStream_t st)
 {
     EpiDual<T> ed{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS, E.q, h->sense,
                   E.partD};
-    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed,
+                   true);
 }
 
 template <typename T>
@@ -820,7 +835,7 @@ static void launch_primal_step(Handle* h, Engine<T>& E, cudaStream_t st, bool wi
     EpiPrimalStep<T, F> ep{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KTY[0], E.KTY[1], E.c, E.l,
                            E.u, E.XS, E.partT, h->n};
     launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval,
-                   h->dev_err, h->m, ep);
+                   h->dev_err, h->m, ep, true);
     if (!F && with_primal) launch_primal<T>(h, E, st, 1);
 }
 
@@ -889,7 +904,7 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
     k_check_cols<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.XA,
                                              E.KTYA, E.XANC, E.c, E.l, E.u, E.Ct, E.Cinv, n,
                                              E.partC);
-    k_check_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partR, E.partC, kEWGrid, E.trace);
+    k_check_ctrl<<<1, kCtlNT, 0, st>>>(E.ctrl, E.partR, E.partC, kEWGrid, E.trace, E.ftab);
     k_restart_apply<T><<<ew_grid(n + m), kEW, 0, st>>>(
         E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.KTY[0], E.KTY[1], E.XA, E.YA,
         E.KXA, E.KTYA, E.XANC, E.YANC, E.KXANC, E.XS, E.YS, n, m);
@@ -1020,8 +1035,18 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
         E.alog_cap = acap;
     }
 
+    if (o->check_every > E.ftab_cap) {
+        if (E.ftab) dev_free(h, E.ftab);
+        E.ftab = nullptr;
+        LP_TRY(dev_alloc_n(h, &E.ftab, 2 * (size_t)o->check_every));
+        E.ftab_cap = o->check_every;
+    }
+
     Ctrl c;
     std::memset(&c, 0, sizeof(c));
+    c.ftab = E.ftab;
+    c.ftab_len = o->check_every;
+    c.ftab_k0 = -((long long)1 << 62);   // no period filled yet
     c.alog = acap > 0 ? E.alog : nullptr;
     c.alog_cap = acap;
     c.eta = eta0;

@@ -294,6 +294,12 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
     constexpr int VA = 16 / (int)sizeof(T);
     constexpr unsigned long long kWaitNs = 50ull * 1000 * 1000;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // Programmatic dependent launch: a launch made with launch_spmv(..., pdl =
+    // true) may start while the previous kernel of the stream finishes; it
+    // waits here, before reading anything that kernel wrote.  Both
+    // instructions are no-ops for ordinary launches.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
     if (!epi.begin()) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStage<T>& W = reinterpret_cast<WarpStage<T>*>(smem_raw)[warp];
@@ -524,14 +530,40 @@ inline cudaError_t spmv_prepare()
 // resident there); larger vectors are gathered without L1 allocation.
 constexpr int64_t kL1GatherBytes = 96 * 1024;
 
+// pdl: launch with programmatic stream serialisation (the kernel may start
+// before the previous kernel of the stream has finished; it waits for it at its
+// top), so that its launch and block start-up overlap the previous kernel's tail.
+#ifndef PDHG_PDL
+#define PDHG_PDL 0
+#endif
 template <typename T, class Epi>
 inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
                         const int64_t* task_nz, int ntasks, const int32_t* wbeg,
                         const int32_t* perm, const int64_t* rp, const int32_t* ci, const T* val,
-                        int* err, int64_t x_len, const Epi& epi)
+                        int* err, int64_t x_len, const Epi& epi, bool pdl = false)
 {
     const size_t sm = spmv_smem_bytes<T>();
-    if (x_len * (int64_t)sizeof(T) <= kL1GatherBytes)
+    const bool l1 = x_len * (int64_t)sizeof(T) <= kL1GatherBytes;
+    if (pdl && PDHG_PDL) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(kSpmvNT);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (l1)
+            (void)cudaLaunchKernelEx(&cfg, k_spmv<T, Epi, true>, task_row, task_nz, ntasks, wbeg,
+                                     perm, rp, ci, val, err, epi);
+        else
+            (void)cudaLaunchKernelEx(&cfg, k_spmv<T, Epi, false>, task_row, task_nz, ntasks,
+                                     wbeg, perm, rp, ci, val, err, epi);
+        return;
+    }
+    if (l1)
         k_spmv<T, Epi, true><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg, perm, rp,
                                                         ci, val, err, epi);
     else
