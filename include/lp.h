@@ -243,8 +243,14 @@ lp_status lp_solve_batch(const lp_handle* hs, int32_t count, const lp_opts* opts
  * eta_0, omega_0, step sizes, restarts, primal weights and termination stay per LP
  * exactly as in lp_solve; an LP that finishes stops consuming work.  The loop runs
  * in one CUDA graph (device-side while condition) until every LP is done.
- * LP_PREC_MIXED runs FP32 iterations with FP64 reductions to opts->tol (no FP64
- * polish phase); traces and warm starts are not supported (ignored). */
+ * LP_PREC_MIXED runs FP32 iterations with FP64 reductions to
+ * max(tol, polish_switch_tol); the LPs that phase declares optimal then go to an
+ * FP64 phase from their candidates, whose first check re-evaluates the relative
+ * errors in FP64: LP_OPTIMAL stands only if they hold there, otherwise (and below
+ * the hand-over tolerance) FP64 iterations continue to tol, as in lp_solve.
+ * Traces, warm starts and Pock-Chambolle trials (pock_chambolle = 2) are not
+ * supported (traces and warm starts are ignored; the trials return
+ * LP_NOT_SUPPORTED). */
 typedef struct lp_batch_s* lp_batch;
 lp_status lp_batch_create(const lp_handle* hs, int32_t count, void* cuda_stream, lp_batch* out);
 lp_status lp_batch_solve(lp_batch b, const lp_opts* opts, lp_result* results);

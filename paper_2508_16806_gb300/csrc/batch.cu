@@ -553,10 +553,14 @@ __global__ void kb_set_cond(Ctrl* ctrl, int B, cudaGraphConditionalHandle handle
 // ---------------------------------------------------------------- setup kernels
 
 // per-LP step sizes and weights from the per-LP sums; control blocks initialised
+// prev (nullptr, or the control blocks of an FP32 phase): an LP that phase
+// declared optimal continues from its step size, primal weight and counters
+// (its first check is the FP64 confirmation); any other LP keeps its outcome and
+// takes no part (done; its result is the warm start, X[0] / Y[0]).
 __global__ void kb_init_ctrl(Ctrl* ctrl, int B, const double* normK, const double* cs2,
                              const double* qs2, const double* qn, const double* cn, Ctrl tmpl,
                              double eta_scale, double eta0, double omega0, double eps_zero,
-                             unsigned long long t0)
+                             unsigned long long t0, const Ctrl* prev)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < B; k += gridDim.x * blockDim.x) {
         Ctrl c = tmpl;
@@ -567,6 +571,24 @@ __global__ void kb_init_ctrl(Ctrl* ctrl, int B, const double* normK, const doubl
         c.qnorm = qn[k];
         c.cnorm = cn[k];
         c.t0_ns = (long long)t0;
+        if (prev) {
+            const Ctrl& p = prev[k];
+            if (p.status == LP_OPTIMAL) {
+                c.eta = p.eta;
+                c.omega = p.omega;
+                c.k = p.k;
+                c.attempts = p.attempts;
+                c.restarts = p.restarts;
+                c.t0_ns = p.t0_ns;
+            } else {
+                c = p;
+                c.done = 1;
+                c.skip = 1;
+                c.want_check = 0;
+                c.cur = 0;
+                c.cand_avg = 0;
+            }
+        }
         refresh_scalars(c);
         ctrl[k] = c;
     }
@@ -600,14 +622,17 @@ __global__ void kb_pow_scale(double* b, const int32_t* lp_col, const double* nb,
     }
 }
 
+// Start point x = proj_X(0), y = 0, or the unscaled warm start w (n + m
+// values: x then y) moved to scaled space and projected.
 template <typename T>
 __global__ void kb_init_state(T* x, T* y, T* xanc, T* yanc, T* xs, T* ys, const T* l, const T* u,
-                              int64_t n, int64_t m)
+                              int64_t n, int64_t m, const double* w, const double* R,
+                              const double* C, const uint8_t* sense)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n + m;
          t += (int64_t)gridDim.x * blockDim.x) {
         if (t < n) {
-            T v = T(0);
+            T v = w ? (T)(w[t] / C[t]) : T(0);
             if (v < l[t]) v = l[t];
             if (v > u[t]) v = u[t];
             x[t] = v;
@@ -615,8 +640,10 @@ __global__ void kb_init_state(T* x, T* y, T* xanc, T* yanc, T* xs, T* ys, const 
             xs[t] = T(0);
         } else {
             const int64_t i = t - n;
-            y[i] = T(0);
-            yanc[i] = T(0);
+            T v = w ? (T)(w[t] / R[i]) : T(0);
+            if (w && sense[i] && v < T(0)) v = T(0);
+            y[i] = v;
+            yanc[i] = v;
             ys[i] = T(0);
         }
     }
@@ -993,8 +1020,15 @@ __global__ void kb_cast_vec(const double* src, T* dst, int64_t count)
         dst[t] = (T)src[t];
 }
 
+// One batched solve in precision T.  prev / warm (both or neither): the control
+// blocks and the unscaled candidates (n + m, device) of an FP32 phase, for the
+// FP64 confirmation and polish of the LPs it declared optimal.  ctrl_out /
+// xo_out (optional): this phase's control blocks and its unscaled candidates
+// (the caller then owns xo_out, a dev_alloc of the handle).
 template <typename T>
-lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
+lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs,
+                        const std::vector<Ctrl>* prev = nullptr, const double* warm = nullptr,
+                        std::vector<Ctrl>* ctrl_out = nullptr, double** xo_out = nullptr)
 {
     Handle* h = &bh->h;
     const int B = bh->meta.B;
@@ -1059,14 +1093,21 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
     unsigned long long t0 = 0;
     LP_CUDA_TRY(cudaMemcpyAsync(&t0, tns, sizeof(t0), cudaMemcpyDeviceToHost, st));
     LP_CUDA_TRY(cudaStreamSynchronize(st));
+    Ctrl* dprev = nullptr;
+    if (prev) {
+        LP_TRY(dev_alloc_n(h, &dprev, (size_t)B));
+        LP_CUDA_TRY(cudaMemcpyAsync(dprev, prev->data(), sizeof(Ctrl) * B, cudaMemcpyHostToDevice,
+                                    st));
+    }
     kb_init_ctrl<<<grid_n(B, 256, 4096), 256, 0, st>>>(bh->ctrl, B, normK, cs2, qs2, bh->meta.qn,
                                                        bh->meta.cn, tmpl, o->eta_scale, o->eta0,
-                                                       o->omega0, o->eps_zero, t0);
+                                                       o->omega0, o->eps_zero, t0, dprev);
     LP_TRY(engine_factors<T>(h));
     if (o->autotune) LP_TRY(tune_batch<T>(bh));
     // start point and its products
     kb_init_state<T><<<grid_n(n + m, 256, 8192), 256, 0, st>>>(E.X[0], E.Y[0], E.XANC, E.YANC,
-                                                               E.XS, E.YS, E.l, E.u, n, m);
+                                                               E.XS, E.YS, E.l, E.u, n, m, warm,
+                                                               h->R, h->C, h->sense);
     BatchSched<T>& S = sched_of<T>(bh);
     {
         EpiBStore<T> e1{E.X[0], E.KX[0], nullptr, S.lpK, nullptr, nullptr};
@@ -1121,6 +1162,12 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
         r->attempts = c.attempts;
         r->restarts = c.restarts;
         r->fp64_iters = sizeof(T) == 8 ? c.k : 0;
+        if (prev) {
+            // after an FP32 phase: FP64 iterations only where the FP64 check sent
+            // the LP on (a confirmation alone keeps the FP32 result)
+            r->fp64_iters = c.k - (*prev)[(size_t)k].k;
+            r->precision_used = r->fp64_iters > 0 ? LP_PREC_FP64 : LP_PREC_MIXED;
+        }
         r->pobj = c.pobj;
         r->dobj = c.dobj;
         r->rel_gap = c.rel_gap;
@@ -1137,14 +1184,52 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs)
     for (int k = 0; k < B; ++k) rs[k].norm_K = nk[(size_t)k];
     const long long lz = h->launches - launches0;
     for (int k = 0; k < B; ++k) rs[k].kernel_launches = k == 0 ? lz : 0;
-    for (void* p : {(void*)xo, (void*)offc, (void*)offr})
+    if (ctrl_out) *ctrl_out = hc;
+    if (xo_out) *xo_out = xo;
+    for (void* p : {(void*)(xo_out ? nullptr : xo), (void*)offc, (void*)offr, (void*)dprev}) {
+        if (!p) continue;
         for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
             if (it->p == p) {
                 cudaFree(p);
                 h->allocs.erase(it);
                 break;
             }
+    }
     return LP_OK;
+}
+
+// LP_PREC_MIXED: the FP32 phase to max(tol, polish_switch_tol), then, for the
+// LPs it declared optimal, an FP64 phase from their candidates: its first check
+// re-evaluates the relative errors with FP64 products (the FP32 phase judged
+// them on FP32 products) and LP_OPTIMAL stands only if they hold; otherwise, or
+// below the hand-over tolerance, FP64 iterations continue to tol.
+lp_status batch_solve_mixed(BatchHandle* bh, const lp_opts* o, lp_result* rs)
+{
+    lp_opts o32 = *o;
+    o32.tol = std::max(o->tol, o->polish_switch_tol);
+    std::vector<Ctrl> c32;
+    double* xo = nullptr;
+    lp_status s = batch_solve_t<float>(bh, &o32, rs, nullptr, nullptr, &c32, &xo);
+    if (s != LP_OK) return s;
+    bool any = false;
+    for (const Ctrl& c : c32) any = any || c.status == LP_OPTIMAL;
+    const long long launches32 = rs[0].kernel_launches;
+    if (any) {
+        const int B = bh->meta.B;
+        std::vector<double> setup32((size_t)B);
+        for (int k = 0; k < B; ++k) setup32[(size_t)k] = rs[k].setup_s;
+        s = batch_solve_t<double>(bh, o, rs, &c32, xo, nullptr, nullptr);
+        for (int k = 0; k < B; ++k) rs[k].setup_s += setup32[(size_t)k];
+        rs[0].kernel_launches += launches32;
+    }
+    Handle* h = &bh->h;
+    for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+        if (it->p == xo) {
+            cudaFree(xo);
+            h->allocs.erase(it);
+            break;
+        }
+    return s;
 }
 
 }  // namespace
@@ -1310,7 +1395,7 @@ lp_status lp_batch_solve(lp_batch b, const lp_opts* o, lp_result* rs)
             return LP_INVALID_ARGUMENT;
     lp_status s;
     if (o->precision == LP_PREC_FP64) s = pdhg::batch_solve_t<double>(&b->b, o, rs);
-    else if (o->precision == LP_PREC_MIXED) s = pdhg::batch_solve_t<float>(&b->b, o, rs);
+    else if (o->precision == LP_PREC_MIXED) s = pdhg::batch_solve_mixed(&b->b, o, rs);
     else return LP_INVALID_ARGUMENT;
     if (s < 0) {
         cudaStreamSynchronize(b->b.h.stream);

@@ -69,7 +69,7 @@ def test_batch_512_mixed_to_1e4(L, oracle_mod):
     for k in rng.choice(len(lps), 8, replace=False):
         x, y, info = out[k]
         kk = oracle_mod.kkt(lps[k], x, y)
-        assert max(kk["rel_gap"], kk["rel_pres"], kk["rel_dres"]) <= 1.5e-4
+        assert max(kk["rel_gap"], kk["rel_pres"], kk["rel_dres"]) <= 1e-4 * (1 + 1e-6)
 
 
 def test_powerlaw_1Mx2M_halpern_mixed_to_1e4(L, oracle_mod):
