@@ -741,8 +741,8 @@ lp_status build_sched(BatchHandle* bh, SchedParams pK, SchedParams pT)
     S.gK = spmv_grid<T>(S.ntK, sms);
     S.gT = spmv_grid<T>(S.ntT, sms);
     std::vector<int32_t> wk, pk, wt, pt;
-    assign_tasks(nK, pK.cap, S.gK * kTaskWarps, wk, pk);
-    assign_tasks(nT, pT.cap, S.gT * kTaskWarps, wt, pt);
+    assign_tasks(nK, pK.cap, S.gK * kSpmvWorkers, wk, pk);
+    assign_tasks(nT, pT.cap, S.gT * kSpmvWorkers, wt, pt);
     auto up32 = [&](int32_t** d, const std::vector<int32_t>& v) -> lp_status {
         LP_TRY(dev_alloc_n(h, d, v.size()));
         LP_CUDA_TRY(cudaMemcpyAsync(*d, v.data(), v.size() * 4, cudaMemcpyHostToDevice, h->stream));

@@ -682,8 +682,8 @@ lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
     LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     const int gK = spmv_grid<T>((int)bk.size() - 1, sms), gT = spmv_grid<T>((int)bt.size() - 1, sms);
     std::vector<int32_t> wk, pk, wt, pt;
-    assign_tasks(nk, sK.cap, gK * kTaskWarps, wk, pk);
-    assign_tasks(nt, sT.cap, gT * kTaskWarps, wt, pt);
+    assign_tasks(nk, sK.cap, gK * kSpmvWorkers, wk, pk);
+    assign_tasks(nt, sT.cap, gT * kSpmvWorkers, wt, pt);
     for (void* p : {(void*)E.brow, (void*)E.bcol, (void*)E.bnzK, (void*)E.bnzT, (void*)E.wbegK,
                     (void*)E.permK, (void*)E.wbegT, (void*)E.permT})
         dev_free(h, p);

@@ -251,10 +251,61 @@ struct alignas(16) WarpStage {
     int rps[kTaskRows + 1];   // row starts of a short task, relative to its first nonzero
 };
 
-template <typename T>
-constexpr size_t spmv_smem_bytes() { return sizeof(WarpStage<T>) * kTaskWarps; }
 static_assert(sizeof(WarpStage<float>) % 16 == 0 && sizeof(WarpStage<double>) % 16 == 0,
               "stages must stay 16-byte aligned");
+
+// ------------------------------------------------ warp-specialised variant
+// The warps of a block form producer / consumer pairs (warp 2p produces, warp
+// 2p + 1 consumes) that work through one task list per pair.  The producer
+// streams the chunks through a ring of kWsStages shared-memory stages (bulk
+// copies, issued two chunks ahead), gathers the vector and writes the products
+// back into the stage; the consumer sums the rows of a stage and runs the
+// epilogue, then releases the stage.  Gathers thus stay in flight while rows
+// are summed and epilogues run (the request stream of a plain gather loop),
+// instead of pausing for them as in the one-warp form.  Products and sums have
+// the one-warp form's order, so both forms give the same bits.
+#ifndef PDHG_SPMV_WS
+#define PDHG_SPMV_WS 1
+#endif
+constexpr bool kSpmvWs = PDHG_SPMV_WS != 0;
+constexpr int kWsPairs = kTaskWarps / 2;
+constexpr int kWsStages = 3;
+// task lists (workers) per block of an SpMV launch
+constexpr int kSpmvWorkers = kSpmvWs ? kWsPairs : kTaskWarps;
+
+// A chunk of a stage: its task, nonzero range [cs, ce) and flags (bit 0 the
+// task's first chunk, bit 1 its last, bit 2 the task is one long row); task < 0
+// ends the pair's sequence.
+struct WsDesc {
+    int task, cs, ce, flags;
+};
+constexpr int kWsFirst = 1, kWsLast = 2, kWsLong = 4;
+
+template <typename T>
+struct alignas(16) PairStage {
+    static constexpr int VPAD = WarpStage<T>::VPAD;
+    static constexpr int IPAD = WarpStage<T>::IPAD;
+    T v[kWsStages][VPAD];          // values, then products (long row: lane sums)
+    int i[kWsStages][IPAD];        // column indices
+    uint64_t tma[kWsStages];       // bulk copy of the stage complete
+    uint64_t full[kWsStages];      // products written (32 producer arrivals)
+    uint64_t empty[kWsStages];     // stage read (32 consumer arrivals)
+    WsDesc desc[kWsStages];
+    int rps[kTaskRows + 1];        // row starts of the consumer's short task
+};
+static_assert(sizeof(PairStage<float>) % 16 == 0 && sizeof(PairStage<double>) % 16 == 0,
+              "stages must stay 16-byte aligned");
+
+template <typename T>
+constexpr size_t spmv_smem_bytes()
+{
+    return kSpmvWs ? sizeof(PairStage<T>) * kWsPairs : sizeof(WarpStage<T>) * kTaskWarps;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 // Issues the bulk copies of a short task's values [s, e) and column indices
 // into stage `st` (lane 0 only).  Each copy covers the 16-byte aligned range
@@ -506,6 +557,279 @@ k_spmv(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz
     epi.finish(acc);
 }
 
+// Bulk copy of the values [s, e) and column indices of one chunk into a stage
+// (one lane); as stage_task, for the warp-specialised stages.
+template <typename T>
+__device__ __forceinline__ void stage_chunk(T* vdst, int* idst, uint64_t* bar, int64_t s,
+                                            int64_t e, const T* val, const int32_t* ci,
+                                            uint64_t pol)
+{
+    constexpr int VA = 16 / (int)sizeof(T);
+    const int64_t v0 = s & ~(int64_t)(VA - 1), v1 = (e + VA - 1) & ~(int64_t)(VA - 1);
+    const int64_t i0 = s & ~(int64_t)3, i1 = (e + 3) & ~(int64_t)3;
+    const uint32_t vb = (uint32_t)((v1 - v0) * (int64_t)sizeof(T));
+    const uint32_t ib = (uint32_t)((i1 - i0) * 4);
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, vb + ib);
+    bulk_g2s(vdst, val + v0, vb, bar, pol);
+    bulk_g2s(idst, ci + i0, ib, bar, pol);
+}
+
+// The warp-specialised SpMV (see PairStage).  Same arguments, task lists (one per
+// pair: wbeg has gridDim.x * kWsPairs + 1 entries), epilogue interface, bounded
+// waits and summation order as k_spmv.
+template <typename T, class Epi, bool L1G>
+__global__ void __launch_bounds__(kSpmvNT, MinBlocks<T>::value)
+k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz, int ntasks,
+          const int32_t* __restrict__ wbeg, const int32_t* __restrict__ perm,
+          const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+          const T* __restrict__ val, int* err, Epi epi)
+{
+    constexpr int CAPW = cap_w<T>();
+    constexpr int VA = 16 / (int)sizeof(T);
+    constexpr int NS = kWsStages;
+    constexpr unsigned long long kWaitNs = 50ull * 1000 * 1000;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (!epi.begin()) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pair = warp >> 1;
+    const bool producer = (warp & 1) == 0;
+    PairStage<T>& P = reinterpret_cast<PairStage<T>*>(smem_raw)[pair];
+    if (producer && lane == 0) {
+        for (int q = 0; q < NS; ++q) {
+            mbar_init(&P.tma[q], 1);
+            mbar_init(&P.full[q], 32);
+            mbar_init(&P.empty[q], 32);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    typename Epi::Acc acc;
+    const int gw = blockIdx.x * kWsPairs + pair;
+    const int pbeg = wbeg[gw], pend = wbeg[gw + 1];
+    if (producer) {
+        // ---------------------------------------------------------- producer
+        const uint64_t pol = evict_first_policy();
+        auto next_live = [&](int p) {
+            while (p < pend && !epi.live(perm[p])) ++p;
+            return p;
+        };
+        // the issue cursor: task at position ipos, its nonzeros [is, ie), next chunk at ics
+        int ipos = next_live(pbeg);
+        int itask = ipos < pend ? perm[ipos] : ntasks;
+        int is = 0, ie = 0, ics = 0;
+        if (itask < ntasks) {
+            is = (int)task_nz[itask];
+            ie = (int)task_nz[itask + 1];
+            ics = is;
+        }
+        bool ended = false;       // the terminator has been issued
+        bool failed = false;
+        uint32_t tpar = 0;        // bit q: parity of the next wait on tma[q]
+        uint32_t inflight = 0;    // bit q: a copy into stage q not yet waited for
+        // issue(q): after the consumer released stage q % NS from its previous
+        // chunk, describe chunk q there and start its copy
+        auto issue = [&](int q) {
+            if (ended || failed) return;
+            const int st = q % NS, n = q / NS;
+            if (n >= 1) {
+                const bool got = mbar_wait_bounded(&P.empty[st], (uint32_t)((n - 1) & 1), kWaitNs);
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) atomicOr(err, 1);
+                    failed = true;
+                    return;
+                }
+            }
+            WsDesc d{-1, 0, 0, 0};
+            if (itask < ntasks) {
+                const int cs = ics, ce = ie - ics > CAPW ? ics + CAPW : ie;
+                d.task = itask;
+                d.cs = cs;
+                d.ce = ce;
+                d.flags = (cs == is ? kWsFirst : 0) | (ce == ie ? kWsLast : 0) |
+                          (ie - is > CAPW ? kWsLong : 0);
+                if (ce != ie) {
+                    ics = ce;
+                } else {
+                    ipos = next_live(ipos + 1);
+                    itask = ipos < pend ? perm[ipos] : ntasks;
+                    if (itask < ntasks) {
+                        is = (int)task_nz[itask];
+                        ie = (int)task_nz[itask + 1];
+                        ics = is;
+                    }
+                }
+                if (ce > cs) {
+                    if (lane == 0) stage_chunk<T>(P.v[st], P.i[st], &P.tma[st], cs, ce, val, ci, pol);
+                    inflight |= 1u << st;
+                }
+            } else {
+                ended = true;
+            }
+            if (lane == 0) P.desc[st] = d;
+            __syncwarp();
+        };
+        issue(0);
+        issue(1);
+        const T* __restrict__ xv = epi.xin();
+        T along = 0;
+        using VT = VecTraits<T>;
+        constexpr int VEC = VT::N;
+        constexpr int UG = (VA - 1 + CAPW + 32 * VEC - 1) / (32 * VEC);
+#pragma unroll 1
+        for (int q = 0; !failed; ++q) {
+            const int st = q % NS;
+            const WsDesc d = P.desc[st];
+            if (d.task < 0) {
+                mbar_arrive(&P.full[st]);   // the consumer sees the end
+                break;
+            }
+            if (d.flags & kWsFirst) {
+                epi.task_start(d.task);
+                xv = epi.xin();
+                along = 0;
+            }
+            const int cs = d.cs, ce = d.ce;
+            if (ce > cs) {
+                const bool got = mbar_wait_bounded(&P.tma[st], (tpar >> st) & 1u, kWaitNs);
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) atomicOr(err, 1);
+                    failed = true;
+                    break;
+                }
+                tpar ^= 1u << st;
+                inflight &= ~(1u << st);
+                const int v0 = cs & ~(VA - 1);
+                const int dd = v0 - (cs & ~3);
+                const int vo = cs - v0;
+                const int lim = vo + (ce - cs);
+                T* vbuf = P.v[st];
+                const int* ibuf = P.i[st] + dd;
+                T vv[UG][VEC];
+                int ii[UG][VEC];
+#pragma unroll
+                for (int k = 0; k < UG; ++k) {
+                    const int off = (k * 32 + lane) * VEC;
+                    if (off < lim) {
+                        VT::unpack(*reinterpret_cast<const typename VT::V*>(vbuf + off), vv[k]);
+                        VT::unpacki(*reinterpret_cast<const typename VT::I*>(ibuf + off), ii[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < UG; ++k) {
+                    const int off = (k * 32 + lane) * VEC;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        const int p = off + v;
+                        if (p >= vo && p < lim) {
+                            if constexpr (L1G) vv[k][v] *= __ldg(xv + ii[k][v]);
+                            else vv[k][v] *= ld_gather(xv + ii[k][v]);
+                        } else {
+                            vv[k][v] = T(0);
+                        }
+                    }
+                }
+                if (d.flags & kWsLong) {
+#pragma unroll
+                    for (int k = 0; k < UG; ++k)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) along += vv[k][v];
+                    if (d.flags & kWsLast) {
+                        __syncwarp();   // every lane has read its values
+                        vbuf[lane] = along;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < UG; ++k) {
+                        const int off = (k * 32 + lane) * VEC;
+                        if (off < lim)
+                            *reinterpret_cast<typename VT::V*>(vbuf + off) = VT::pack(vv[k]);
+                    }
+                }
+            }
+            mbar_arrive(&P.full[st]);   // each lane releases its own writes
+            issue(q + 2);
+        }
+        if (failed) {
+            // copies still in flight must land before the block's shared memory goes
+            for (int q = 0; q < NS; ++q)
+                if ((inflight >> q) & 1u)
+                    (void)mbar_wait_bounded(&P.tma[q], (tpar >> q) & 1u, kWaitNs);
+        }
+    } else {
+        // ---------------------------------------------------------- consumer
+        typename Epi::Pre pre0, pre1;
+        int r0 = 0, nrows = 0;
+#pragma unroll 1
+        for (int q = 0;; ++q) {
+            const int st = q % NS, n = q / NS;
+            const bool got = mbar_wait_bounded(&P.full[st], (uint32_t)(n & 1), kWaitNs);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) atomicOr(err, 1);
+                break;
+            }
+            const WsDesc d = P.desc[st];
+            if (d.task < 0) break;
+            const bool lng = d.flags & kWsLong;
+            if (d.flags & kWsFirst) {
+                epi.task_start(d.task);
+                r0 = task_row[d.task];
+                nrows = task_row[d.task + 1] - r0;
+                if (lane < nrows) pre0 = epi.load(r0 + lane);
+                if (kTaskRows > 32 && lane + 32 < nrows) pre1 = epi.load(r0 + 32 + lane);
+                if (!lng) {
+                    // row starts relative to the task's first nonzero (a short task
+                    // is one chunk: [d.cs, d.ce))
+                    const int* rp32 = reinterpret_cast<const int*>(rp);
+                    if (lane < nrows) P.rps[lane] = rp32[2 * ((int64_t)r0 + lane)] - d.cs;
+                    if (kTaskRows > 32 && lane + 32 < nrows)
+                        P.rps[lane + 32] = rp32[2 * ((int64_t)r0 + 32 + lane)] - d.cs;
+                    if (lane == 0) P.rps[nrows] = d.ce - d.cs;
+                }
+            }
+            __syncwarp();
+            if (lng) {
+                if (d.flags & kWsLast) {
+                    const T a = warp_sum_T(P.v[st][lane]);
+                    if (lane == 0) epi.row(r0, a, pre0, acc);
+                }
+            } else {
+                const int v0 = d.cs & ~(VA - 1);
+                const T* vs = P.v[st] + (d.cs - v0);
+                const int* rps = P.rps;
+                if (nrows <= 32) {
+                    int G = 32;
+                    while (G > 1 && G * nrows > 32) G >>= 1;
+                    const int j = lane / G, g = lane % G;
+                    T a = 0;
+                    if (j < nrows) {
+                        const int pb = rps[j], pe = rps[j + 1];
+                        a = strided_sum(vs, pb + g, pe, G);
+                    }
+                    for (int o = G >> 1; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o, G);
+                    const T v = __shfl_sync(0xffffffffu, a, (lane * G) & 31);
+                    if (lane < nrows) epi.row(r0 + lane, v, pre0, acc);
+                } else if (kTaskRows > 32) {
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int j = lane + 32 * half;
+                        if (j < nrows) {
+                            const int pb = rps[j], pe = rps[j + 1];
+                            epi.row(r0 + j, strided_sum(vs, pb, pe, 1), half ? pre1 : pre0, acc);
+                        }
+                    }
+                }
+            }
+            if (d.flags & kWsLast) epi.task_done(d.task, acc);
+            __syncwarp();
+            mbar_arrive(&P.empty[st]);
+        }
+    }
+    epi.finish(acc);
+}
+
 // Dynamic shared-memory limit (and the optional carveout preference) of one
 // SpMV instantiation; spmv_prepare sets both gather variants of an epilogue.
 // Call before any launch or graph capture of that epilogue.
@@ -521,9 +845,15 @@ inline cudaError_t spmv_set_attrs(const void* f)
 template <typename T, class Epi>
 inline cudaError_t spmv_prepare()
 {
-    cudaError_t e = spmv_set_attrs<T>((const void*)k_spmv<T, Epi, true>);
-    if (e != cudaSuccess) return e;
-    return spmv_set_attrs<T>((const void*)k_spmv<T, Epi, false>);
+    if constexpr (kSpmvWs) {
+        cudaError_t e = spmv_set_attrs<T>((const void*)k_spmv_ws<T, Epi, true>);
+        if (e != cudaSuccess) return e;
+        return spmv_set_attrs<T>((const void*)k_spmv_ws<T, Epi, false>);
+    } else {
+        cudaError_t e = spmv_set_attrs<T>((const void*)k_spmv<T, Epi, true>);
+        if (e != cudaSuccess) return e;
+        return spmv_set_attrs<T>((const void*)k_spmv<T, Epi, false>);
+    }
 }
 
 // Gathers from a vector of at most this many bytes go through L1 (it stays
@@ -555,12 +885,19 @@ inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
+        auto kern = kSpmvWs ? (l1 ? k_spmv_ws<T, Epi, true> : k_spmv_ws<T, Epi, false>)
+                            : (l1 ? k_spmv<T, Epi, true> : k_spmv<T, Epi, false>);
+        (void)cudaLaunchKernelEx(&cfg, kern, task_row, task_nz, ntasks, wbeg, perm, rp, ci, val,
+                                 err, epi);
+        return;
+    }
+    if constexpr (kSpmvWs) {
         if (l1)
-            (void)cudaLaunchKernelEx(&cfg, k_spmv<T, Epi, true>, task_row, task_nz, ntasks, wbeg,
-                                     perm, rp, ci, val, err, epi);
+            k_spmv_ws<T, Epi, true><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg,
+                                                               perm, rp, ci, val, err, epi);
         else
-            (void)cudaLaunchKernelEx(&cfg, k_spmv<T, Epi, false>, task_row, task_nz, ntasks,
-                                     wbeg, perm, rp, ci, val, err, epi);
+            k_spmv_ws<T, Epi, false><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg,
+                                                                perm, rp, ci, val, err, epi);
         return;
     }
     if (l1)
@@ -615,7 +952,7 @@ struct EpiStore {
 template <typename T>
 inline int spmv_grid(int ntasks, int num_sms)
 {
-    const int full = (ntasks + kTaskWarps - 1) / kTaskWarps;
+    const int full = (ntasks + kSpmvWorkers - 1) / kSpmvWorkers;
     if (PDHG_SPMV_WAVES <= 0) return full > 0 ? full : 1;
     const int wave = num_sms * MinBlocks<T>::value * PDHG_SPMV_WAVES;
     return full < wave ? (full > 0 ? full : 1) : wave;

@@ -38,7 +38,7 @@ lp_status tune_schedule(int sms, cudaStream_t st, const RowBlockBuilder& build,
             for (size_t t = 0; t < b.size(); ++t) nz[t] = h_rp[(size_t)b[t]];
             const int grid = spmv_grid<T>(nt, sms);
             std::vector<int32_t> wb, pm;
-            assign_tasks(nz, caps[ci_], grid * kTaskWarps, wb, pm);
+            assign_tasks(nz, caps[ci_], grid * kSpmvWorkers, wb, pm);
             int32_t *tb = nullptr, *wbd = nullptr, *pmd = nullptr;
             int64_t* tn = nullptr;
             if (cudaMalloc(&tb, b.size() * sizeof(int32_t)) != cudaSuccess ||

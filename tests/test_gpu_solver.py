@@ -142,7 +142,7 @@ def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
     prob = L.Problem(lp)
     x, y, info, tr = prob.solve(tol=1e-13, max_iters=1000, trace_cap=4096, attempt_cap=5000)
     log = info["attempt_log"]
-    assert info["attempt_len"] == info["attempts"] == len(log) > 1000
+    assert info["attempt_len"] == info["attempts"] == len(log) >= 1000
     rows = np.array([[a[f] for f in L.ATTEMPT_FIELDS] for a in log])
     xo, yo, io, tro, att = oracle_mod.solve_logged(lp, tol=1e-13, max_iters=1000,
                                                    trace_cap=4096, replay=rows)
