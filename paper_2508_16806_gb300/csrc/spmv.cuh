@@ -33,6 +33,7 @@
 #pragma once
 
 #include <functional>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -272,6 +273,14 @@ constexpr int kWsPairs = kTaskWarps / 2;
 constexpr int kWsStages = 3;
 // task lists (workers) per block of an SpMV launch
 constexpr int kSpmvWorkers = kSpmvWs ? kWsPairs : kTaskWarps;
+
+// Whether an epilogue's load() of one task may run before another task's rows
+// are finished (no per-task state set by task_start).
+template <class E, class = void>
+struct StatelessTasks : std::false_type {};
+template <class E>
+struct StatelessTasks<E, std::void_t<decltype(E::kStatelessTasks)>>
+    : std::integral_constant<bool, E::kStatelessTasks> {};
 
 // A chunk of a stage: its task, nonzero range [cs, ce) and flags (bit 0 the
 // task's first chunk, bit 1 its last, bit 2 the task is one long row); task < 0
@@ -762,6 +771,30 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
         // ---------------------------------------------------------- consumer
         typename Epi::Pre pre0, pre1;
         int r0 = 0, nrows = 0;
+        // With stateless tasks the consumer walks the pair's task list itself and
+        // loads the next task's row operands and row starts while it finishes
+        // the current one (their latency then hides behind that work).
+        // (FP32 only: the FP64 operands of a second task spill registers)
+#ifndef PDHG_WS_PREFETCH_F64
+#define PDHG_WS_PREFETCH_F64 0
+#endif
+        constexpr bool PF = StatelessTasks<Epi>::value && (sizeof(T) == 4 || PDHG_WS_PREFETCH_F64);
+        typename Epi::Pre npre0, npre1;
+        int nrpl0 = 0, nrpl1 = 0;
+        int cpos = pbeg;
+        auto prefetch = [&]() {
+            while (cpos < pend && !epi.live(perm[cpos])) ++cpos;
+            if (cpos >= pend) return;
+            const int t = perm[cpos];
+            const int nr0 = task_row[t], nn = task_row[t + 1] - nr0;
+            if (lane < nn) npre0 = epi.load(nr0 + lane);
+            if (kTaskRows > 32 && lane + 32 < nn) npre1 = epi.load(nr0 + 32 + lane);
+            const int* rp32 = reinterpret_cast<const int*>(rp);
+            if (lane < nn) nrpl0 = rp32[2 * ((int64_t)nr0 + lane)];
+            if (kTaskRows > 32 && lane + 32 < nn) nrpl1 = rp32[2 * ((int64_t)nr0 + 32 + lane)];
+            ++cpos;
+        };
+        if constexpr (PF) prefetch();
 #pragma unroll 1
         for (int q = 0;; ++q) {
             const int st = q % NS, n = q / NS;
@@ -777,15 +810,28 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                 epi.task_start(d.task);
                 r0 = task_row[d.task];
                 nrows = task_row[d.task + 1] - r0;
-                if (lane < nrows) pre0 = epi.load(r0 + lane);
-                if (kTaskRows > 32 && lane + 32 < nrows) pre1 = epi.load(r0 + 32 + lane);
+                int rpl0 = 0, rpl1 = 0;
+                if constexpr (PF) {
+                    pre0 = npre0;
+                    pre1 = npre1;
+                    rpl0 = nrpl0;
+                    rpl1 = nrpl1;
+                    prefetch();
+                } else {
+                    const int* rp32 = reinterpret_cast<const int*>(rp);
+                    if (lane < nrows) pre0 = epi.load(r0 + lane);
+                    if (kTaskRows > 32 && lane + 32 < nrows) pre1 = epi.load(r0 + 32 + lane);
+                    if (!lng) {
+                        if (lane < nrows) rpl0 = rp32[2 * ((int64_t)r0 + lane)];
+                        if (kTaskRows > 32 && lane + 32 < nrows)
+                            rpl1 = rp32[2 * ((int64_t)r0 + 32 + lane)];
+                    }
+                }
                 if (!lng) {
                     // row starts relative to the task's first nonzero (a short task
                     // is one chunk: [d.cs, d.ce))
-                    const int* rp32 = reinterpret_cast<const int*>(rp);
-                    if (lane < nrows) P.rps[lane] = rp32[2 * ((int64_t)r0 + lane)] - d.cs;
-                    if (kTaskRows > 32 && lane + 32 < nrows)
-                        P.rps[lane + 32] = rp32[2 * ((int64_t)r0 + 32 + lane)] - d.cs;
+                    if (lane < nrows) P.rps[lane] = rpl0 - d.cs;
+                    if (kTaskRows > 32 && lane + 32 < nrows) P.rps[lane + 32] = rpl1 - d.cs;
                     if (lane == 0) P.rps[nrows] = d.ce - d.cs;
                 }
             }
@@ -909,8 +955,10 @@ inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
 }
 
 // The task hooks of an epilogue that serves a single LP: every task is live,
-// no per-task state.
+// no per-task state (so the operands of a task's rows can be loaded while an
+// earlier task is still being finished).
 #define PDHG_SINGLE_LP_TASK_HOOKS                                   \
+    static constexpr bool kStatelessTasks = true;                   \
     __device__ bool live(int) const { return true; }               \
     __device__ void task_start(int) {}                              \
     template <class A>                                              \

@@ -149,7 +149,17 @@ def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
     assert io["iters"] == info["iters"] == 1000 and io["attempts"] == info["attempts"]
     assert rel(x, xo) <= 1e-10, rel(x, xo)
     assert rel(y, yo) <= 1e-10, rel(y, yo)
-    _check_trace(tr, tro)
+    # check records: the same decisions; the KKT figures of the current iterate
+    # carry cancellation (a gap of O(|objective|) terms), so one-ulp step-size
+    # differences already move them by 1e-7 relative within the oracle itself
+    assert len(tr) == len(tro)
+    for a, b in zip(tr, tro):
+        for f in ("k", "attempts", "restart", "cand_is_avg"):
+            assert a[f] == b[f], (f, a, b)
+        for f in ("omega", "eta"):
+            assert a[f] == pytest.approx(b[f], rel=1e-10), (f, a[f], b[f])
+        for f in ("kkt_cur", "kkt_cand", "rel_gap", "rel_pres", "rel_dres"):
+            assert a[f] == pytest.approx(b[f], rel=1e-6, abs=1e-10), (f, a[f], b[f])
     rejected = 0
     for g, o in zip(log, att):
         assert g["k"] == o["k"] and g["eta"] == o["eta"]
