@@ -163,10 +163,11 @@ def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
     rejected = 0
     for g, o in zip(log, att):
         assert g["k"] == o["k"] and g["eta"] == o["eta"]
-        # eta_bar divides by the interaction dy^T K dx, a difference of larger
-        # terms: far above eta (where it cannot decide anything) it is compared
-        # loosely
-        tol_eb = 1e-8 if o["eta_bar"] < 10 * g["eta"] else 1e-4
+        # eta_bar divides by the interaction dy^T K dx, a sum of terms of both
+        # signs whose summation order differs between the two runs: well above
+        # eta (where eta' = (1 + (k+1)^-0.6) eta does not depend on it and the
+        # step is accepted either way) it is compared loosely
+        tol_eb = 1e-8 if o["eta_bar"] < 2 * g["eta"] else 1e-5
         assert g["eta_bar"] == pytest.approx(o["eta_bar"], rel=tol_eb), (g, o)
         if abs(g["eta"] - o["eta_bar"]) > 1e-8 * o["eta_bar"]:
             assert bool(g["accept"]) == (g["eta"] <= o["eta_bar"]), (g, o)
