@@ -594,7 +594,8 @@ def timed_solve(prob, stream, **opts):
 def dispatch_leg(L, tol):
     """The 615,001 x 5,000 dispatch-shaped LP to tol: the mixed path and the
     plain FP64 path (one warm-up solve each builds the loop graphs), with the
-    oracle's FP64 error of each result."""
+    oracle's FP64 error of each result and the step kernels' times
+    (lp_profile_step, CUDA events)."""
     import torch
     from paper_2508_16806_gb300 import synth
     lp = synth.dispatch_lp()
@@ -604,9 +605,11 @@ def dispatch_leg(L, tol):
     for prec, tag in ((L.LP_PREC_MIXED, "mixed"), (L.LP_PREC_FP64, "fp64")):
         prob.solve(tol=tol, precision=prec, max_iters=64)
         t, x, y, info = timed_solve(prob, stream, tol=tol, precision=prec, max_iters=2_000_000)
+        ms, _ = prob.profile_step(prec, reps=20)
         out[tag] = {"time_to_tol_s": t, "iters": int(info["iters"]),
                     "fp64_iters": int(info["fp64_iters"]), "status": L.STATUS[info["status"]],
-                    "fp64_error": fp64_error(lp, x, y, info)}
+                    "fp64_error": fp64_error(lp, x, y, info),
+                    "step_kernels_ms": dict(zip(STEP_NAMES, ms))}
     out["mixed_speedup_vs_fp64"] = out["fp64"]["time_to_tol_s"] / out["mixed"]["time_to_tol_s"]
     prob.close()
     return out

@@ -200,7 +200,10 @@ typedef struct {
     double* x;
     double* y;
     int32_t memory_space;        /* of x and y */
-    int32_t reserved;
+    int32_t split_rows;          /* rows of K and K^T whose products the SpMV schedules of the
+                                    first phase's precision (FP32 for LP_PREC_MIXED) cut into
+                                    pieces on several warps (long rows of unbalanced
+                                    schedules; the results do not depend on it) */
     lp_trace_rec* trace;
     int64_t trace_cap;
     int64_t trace_len;           /* records produced (may exceed trace_cap) */
@@ -330,8 +333,9 @@ lp_status lp_profile_step(lp_handle h, int32_t precision, int32_t reps, double* 
  * handle's scaled matrices (the products of Algorithm 1).  A minimal kernel
  * streams the nonzeros of K (then of K^T) with coalesced 16-byte loads of values
  * and column indices, gathers the vector entry of each nonzero (x of the last
- * lp_solve of that precision for K, y for K^T; loads that do not allocate in L1)
- * and multiply-adds it into a per-thread sum: the same request stream as the
+ * lp_solve of that precision for K, y for K^T; through L1 when the vector takes
+ * at most 96 KB, else with loads that do not allocate in L1, as the SpMV kernels
+ * do) and multiply-adds it into a per-thread sum: the same request stream as the
  * SpMV kernels without their row structure and epilogues.  Grid:
  * blocks_per_sm (1..8) x the SM count, 256 threads.  ms_out (host, 2 doubles)
  * receives the mean milliseconds per launch over `reps` launches after one

@@ -57,7 +57,8 @@ class _Opts(C.Structure):
                 ("infeas_detect", C.c_int32), ("pad", C.c_int32), ("infeas_tol", C.c_double),
                 ("halpern", C.c_int32), ("pad2", C.c_int32), ("reflect", C.c_double),
                 ("pc_alpha", C.c_double), ("pc_trial_iters", C.c_int32), ("pad3", C.c_int32),
-                ("replay", C.c_void_p), ("replay_len", C.c_int64)]
+                ("replay", C.c_void_p), ("replay_len", C.c_int64),
+                ("replay_checks", C.c_void_p), ("replay_checks_len", C.c_int64)]
 
 
 class _Info(C.Structure):
@@ -71,7 +72,7 @@ class _Info(C.Structure):
 
 TRACE_FIELDS = ("k", "attempts", "restart", "cand_is_avg", "omega", "eta",
                 "kkt_cur", "kkt_avg", "rel_gap", "rel_pres", "rel_dres", "kkt_cand",
-                "fpr", "fpr0")
+                "fpr", "fpr0", "own_restart", "own_cand_is_avg", "kkt_anchor", "kkt_prev")
 
 DEFAULTS = dict(tol=1e-4, max_iters=100000, check_every=64, ruiz_iters=10, ruiz_tol=1e-4,
                 pock_chambolle=0, power_iters=100, adaptive_step=1, primal_weight_update=1,
@@ -275,7 +276,7 @@ def halpern_step(lp, x, y, xanc, yanc, tau, sigma, k, rho, vals=None, c=None, q=
     return (xh, yh), (xn, yn), float(r)
 
 
-def _opts(o, x0a=None, y0a=None, replay=None):
+def _opts(o, x0a=None, y0a=None, replay=None, replay_checks=None):
     return _Opts(o["tol"], int(o["max_iters"]), int(o["check_every"]), int(o["ruiz_iters"]),
                  o["ruiz_tol"], int(o["pock_chambolle"]), int(o["power_iters"]),
                  int(o["adaptive_step"]), int(o["primal_weight_update"]), int(o["restarts"]),
@@ -285,7 +286,9 @@ def _opts(o, x0a=None, y0a=None, replay=None):
                  o["omega0"], o["eta0"], int(o["infeas_detect"]), 0, o["infeas_tol"],
                  int(o["halpern"]), 0, float(o["reflect"]), float(o["pc_alpha"]),
                  int(o["pc_trial_iters"]), 0, None if replay is None else _ptr(replay),
-                 0 if replay is None else int(replay.shape[0]))
+                 0 if replay is None else int(replay.shape[0]),
+                 None if replay_checks is None else _ptr(replay_checks),
+                 0 if replay_checks is None else int(replay_checks.shape[0]))
 
 
 def solve(lp, trace_cap=100000, x0=None, y0=None, **kw):
@@ -313,20 +316,26 @@ ATTEMPT_FIELDS = ("k", "eta", "eta_bar", "eta_next", "accept", "omega", "dx2", "
 
 
 def solve_logged(lp, attempt_cap=100000, trace_cap=100000, x0=None, y0=None, replay=None,
-                 **kw):
+                 replay_checks=None, **kw):
     """``solve`` plus one record per step attempt (ATTEMPT_FIELDS: accepted
     iterations before the attempt, the eta tried, Algorithm 5's eta_bar and
     eta', the outcome, omega and the three terms ||dx||^2, ||dy||^2, dy^T K dx on
     the scaled problem).  replay: attempt records of another run (an array of
     rows in ATTEMPT_FIELDS order) whose step sizes and outcomes this run takes
-    (eta_bar and eta' are still its own).  Returns (x, y, info, trace, attempts)."""
+    (eta_bar and eta' are still its own).  replay_checks: per check of another
+    run, (restart, candidate is the average); this run takes those decisions and
+    logs its own in the trace (own_restart, own_cand_is_avg, with the KKT values
+    its restart criteria compared: kkt_anchor, kkt_prev).
+    Returns (x, y, info, trace, attempts)."""
     o = dict(DEFAULTS)
     o.update(kw)
     b = _Bound(lp)
     x0a = None if x0 is None else _f64(x0)
     y0a = None if y0 is None else _f64(y0)
     rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.float64)
-    opts = _opts(o, x0a, y0a, rep)
+    rch = (None if replay_checks is None
+           else np.ascontiguousarray(replay_checks, dtype=np.float64).reshape(-1, 2))
+    opts = _opts(o, x0a, y0a, rep, rch)
     x = np.empty(lp.n)
     y = np.empty(lp.m)
     info = _Info()

@@ -92,6 +92,11 @@ typedef struct {
      * still computed here and logged.  NULL: off. */
     const double* replay;
     int64_t replay_len;
+    /* replay of checks (test use): record c (2 doubles) gives check c's restart
+     * decision ([0]) and candidate choice ([1], 1 = the average) as another run
+     * took them; this run follows them and logs its own (orc_trace).  NULL: off. */
+    const double* replay_checks;
+    int64_t replay_checks_len;
 } orc_opts;
 
 typedef struct {
@@ -114,6 +119,12 @@ typedef struct {
     double k, attempts, restart, cand_is_avg, omega, eta;
     double kkt_cur, kkt_avg, rel_gap, rel_pres, rel_dres, kkt_cand;
     double fpr, fpr0;
+    /* this run's own restart decision and candidate choice (they differ from
+     * restart / cand_is_avg only under a replay of checks), and the two KKT
+     * values the restart criteria compared the candidate with: the last
+     * restart's candidate and the previous check's (+inf after a restart; NaN
+     * for the Halpern variant, whose criteria use fpr and fpr0) */
+    double own_restart, own_cand_is_avg, kkt_anchor, kkt_prev;
 } orc_trace;
 
 /* ------------------------------------------------------------------ */
@@ -660,7 +671,10 @@ int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double*
                 orc_kkt(lp, vs, cs, qs, ls, us, xa, ya, omega, ka);
                 kkt_avg = ka[7];
             }
-            int cand_avg = !(kc[7] < kkt_avg);
+            const int cand_own = !(kc[7] < kkt_avg);
+            const double* rc = (o->replay_checks && tl < o->replay_checks_len)
+                                   ? o->replay_checks + 2 * tl : NULL;
+            int cand_avg = rc ? (rc[1] != 0.0 && wsum > 0.0) : cand_own;
             const double* xc = cand_avg ? xa : x;
             const double* yc = cand_avg ? ya : y;
             double kkt_c = cand_avg ? kkt_avg : kc[7];
@@ -691,6 +705,7 @@ int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double*
                 for (int64_t i = 0; i < m; ++i) yu[i] = R[i] * yc[i];
             }
             int restart = 0;
+            const double anchor_before = first ? kkt_c : kkt_anchor, prev_before = kkt_prev;
             if (first) {
                 kkt_anchor = kkt_c;
             } else if (!converged && !infeasible && o->restarts) {
@@ -699,6 +714,8 @@ int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double*
                 int crit3 = (double)epoch_k > o->beta_artificial * (double)k;
                 restart = crit1 || crit2 || crit3;
             }
+            const int restart_own = restart;
+            if (rc && !first) restart = rc[0] != 0.0;
             if (restart) {
                 if (cand_avg) {
                     memcpy(x, xa, sizeof(double) * (size_t)n);
@@ -733,6 +750,8 @@ int orc_solve_logged(const orc_lp* lp, const orc_opts* o, double* x_out, double*
                 t->rel_gap = rel[0]; t->rel_pres = rel[1]; t->rel_dres = rel[2];
                 t->kkt_cand = kkt_c;
                 t->fpr = 0.0; t->fpr0 = 0.0;
+                t->own_restart = restart_own; t->own_cand_is_avg = cand_own;
+                t->kkt_anchor = anchor_before; t->kkt_prev = prev_before;
             }
             ++tl;
             if (converged || infeasible || k >= o->max_iters) {
@@ -990,6 +1009,8 @@ int orc_solve_halpern(const orc_lp* lp, const orc_opts* o, double* x_out, double
                 t->rel_gap = rel[0]; t->rel_pres = rel[1]; t->rel_dres = rel[2];
                 t->kkt_cand = ka[7];
                 t->fpr = r; t->fpr0 = r0;
+                t->own_restart = restart; t->own_cand_is_avg = 1;
+                t->kkt_anchor = NAN; t->kkt_prev = NAN;
             }
             ++tl;
             if (converged || k >= o->max_iters) {

@@ -348,6 +348,10 @@ static lp_status solve_core(Handle* h, const lp_opts* o, lp_result* r)
     r->solve_s = now_s() - t1;
     r->kernel_launches = h->launches - launches0;
     r->attempt_len = std::min<long long>(r->attempts, h->alog_cap_host);
+    if (o->precision == LP_PREC_MIXED)
+        r->split_rows = engine_of<float>(h).splitK.n + engine_of<float>(h).splitT.n;
+    else
+        r->split_rows = engine_of<double>(h).splitK.n + engine_of<double>(h).splitT.n;
     return r->status;
 }
 

@@ -135,6 +135,26 @@ struct SchedParams {
     int max_rows = 0;
 };
 
+// Rows cut into pieces across task lists (warp-specialised form only).  A row
+// of a schedule whose lists would otherwise be unbalanced (few, long rows, as
+// the columns of K in a dispatch-shaped LP) is cut on the host into pieces of
+// whole chunks; each piece is a task of its own, marked by its slot g + 1 in
+// the high 32 bits of its task_nz entry (nonzero offsets fit in the low 31).
+// The warp that finishes a piece stores its sum in slots[g] and takes a ticket
+// on the row's counter; the warp that takes the last ticket adds the row's
+// slots in piece order, so the result does not depend on which warp that is,
+// resets the counter for the next launch and applies the epilogue to the row.
+// The epilogue's reductions of that row go to a fixed place too: Epi::split_acc
+// stores them in the split's own partial slot (after the block partials),
+// which the consumer of the partials sums with them in a fixed order.
+struct SplitRows {
+    const int32_t* pspl = nullptr;   // [npieces] split of each piece slot
+    const int32_t* info = nullptr;   // [n][2] first piece slot, number of pieces
+    int* cnt = nullptr;              // [n] tickets taken in the current launch (0 between launches)
+    void* slots = nullptr;           // [npieces] piece sums (the launch's T)
+    int n = 0;                       // split rows
+};
+
 // State and scaled data of one precision T (double or float).
 template <typename T>
 struct Engine {
@@ -161,14 +181,18 @@ struct Engine {
     int32_t* wbegK = nullptr;  int32_t* permK = nullptr;  // per-warp task lists (K)
     int32_t* wbegT = nullptr;  int32_t* permT = nullptr;  // per-warp task lists (K^T)
     int gK = 0, gT = 0;                         // blocks of the K and K^T SpMV launches
+    SplitRows splitK, splitT;                   // rows cut into pieces (n = 0: none)
+    int npK = 0, npT = 0;                       // partials of the two launches: grid + split rows
     SchedParams schedK, schedT;                 // parameters of the two schedules
     bool tuned = false;                         // schedules chosen by the autotuner
     // Ruiz factors R, C and their reciprocals in this precision (KKT checks)
     T* Rt = nullptr; T* Ct = nullptr; T* Rinv = nullptr; T* Cinv = nullptr;
     // reduction partials
-    double* partD = nullptr;   // [2][gK] Algorithm 5 partials of the K x' launch (largest grid)
-    double* partT = nullptr;   // [kEWGrid] ||x' - x||^2 partials (k_primal, or the K^T launch's
-                               // fused primal step), one per block of the K^T launch grid
+    double* partD = nullptr;   // [2][npK] Algorithm 5 partials of the K x' launch
+    double* partT = nullptr;   // [max(npT, kEWGrid)] ||x' - x||^2 partials (k_primal, or the
+                               // K^T launch's fused primal step): one per block of the K^T
+                               // launch grid, then one per split row of its schedule
+    size_t partD_cap = 0, partT_cap = 0;        // allocated entries
     double* partR = nullptr;   // [kRowQ][kEWGrid]
     double* partC = nullptr;   // [kColQ][kEWGrid]
     Ctrl* ctrl = nullptr;

@@ -224,9 +224,11 @@ void forward_step(Handle* h, Engine<T>& E, const double* coef, const T* x, const
     cudaStream_t st = h->stream;
     k_g_primal<T><<<ew_grid_g(h->n), kEW, 0, st>>>(x, kty, E.c, E.l, E.u, coef, xn, mx, h->n);
     EpiGDual<T> ed{xn, y, kx, E.q, h->sense, coef, yn, kxn, my};
-    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed,
+                   false, E.splitK);
     EpiStore<T> et{yn, ktyn, nullptr, nullptr, nullptr};
-    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et,
+                   false, E.splitT);
     h->launches += 3;
 }
 
@@ -235,9 +237,11 @@ lp_status products(Handle* h, Engine<T>& E, const T* x, const T* y, T* kx, T* kt
 {
     cudaStream_t st = h->stream;
     EpiStore<T> e1{x, kx, nullptr, nullptr, nullptr};
-    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1,
+                   false, E.splitK);
     EpiStore<T> e2{y, kty, nullptr, nullptr, nullptr};
-    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2,
+                   false, E.splitT);
     h->launches += 2;
     LP_CUDA_TRY(cudaGetLastError());
     return LP_OK;
@@ -371,12 +375,12 @@ lp_status grad_impl(Handle* h, const lp_opts* o, int K, int ckpt, const double* 
             k_g_gvy<T><<<ew_grid_g(m), kEW, 0, st>>>(RMY + (size_t)s * m, gy, coef, gvy, ddq, m);
             EpiStore<T> eg{gvy, gxbar, coef + 2, nullptr, nullptr};
             launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err,
-                           h->m, eg);
+                           h->m, eg, false, E.splitT);
             k_g_gvx<T><<<ew_grid_g(n), kEW, 0, st>>>(RMX + (size_t)s * n, gx, gxbar, coef, gvx, ddc,
                                                     n);
             EpiGy<T> ey{gvx, gvy, coef, gy};
             launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err,
-                           h->n, ey);
+                           h->n, ey, false, E.splitK);
             if (nnz > 0)
                 k_g_sddmm<T><<<ew_grid_g(nnz), kEW, 0, st>>>(h->krow, h->ci, gvy, gvx, xs, xs1, ys,
                                                              coef, ddv, nnz);

@@ -79,15 +79,22 @@ lp_status probe(Handle* h, int reps, int blocks_per_sm, double* out)
     LP_CUDA_TRY(cudaEventCreate(&e0));
     LP_CUDA_TRY(cudaEventCreate(&e1));
     // [0] K side (gathers x, n entries), [1] K^T side (gathers y, m entries);
-    // each without L1 allocation (the SpMV kernels' choice for large vectors)
+    // through L1 when the vector is at most kL1GatherBytes, else without L1
+    // allocation (the SpMV kernels' choice)
     const T* vals[2] = {E.val, E.tval};
     const int32_t* cis[2] = {h->ci, h->tci};
     const T* vec[2] = {E.X[0], E.Y[0]};
+    const int64_t len[2] = {h->n, h->m};
     for (int side = 0; side < 2; ++side) {
+        const bool l1 = len[side] * (int64_t)sizeof(T) <= kL1GatherBytes;
         for (int r = 0; r < reps + 1; ++r) {
             if (r == 1) cudaEventRecord(e0, st);
-            k_gather_probe<T, false><<<grid, kProbeNT, 0, st>>>(vals[side], cis[side], h->nnz,
-                                                                vec[side], sink);
+            if (l1)
+                k_gather_probe<T, true><<<grid, kProbeNT, 0, st>>>(vals[side], cis[side], h->nnz,
+                                                                   vec[side], sink);
+            else
+                k_gather_probe<T, false><<<grid, kProbeNT, 0, st>>>(vals[side], cis[side],
+                                                                    h->nnz, vec[side], sink);
         }
         cudaEventRecord(e1, st);
         h->launches += reps + 1;

@@ -107,6 +107,81 @@ void assign_tasks(const std::vector<int64_t>& task_nz, int cap, int warps,
     for (int t = 0; t < nt; ++t) perm[(size_t)cur[(size_t)owner[(size_t)t]]++] = t;
 }
 
+// Longest worker list (in chunks) of the longest-first assignment of
+// assign_tasks, without building the lists.
+static int64_t lpt_makespan(const std::vector<int64_t>& cost, int workers)
+{
+    std::vector<int64_t> c(cost);
+    std::sort(c.begin(), c.end(), std::greater<int64_t>());
+    using Slot = std::pair<int64_t, int32_t>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> pq;
+    for (int w = 0; w < workers; ++w) pq.push(Slot{0, w});
+    int64_t mx = 0;
+    for (int64_t x : c) {
+        Slot sl = pq.top();
+        pq.pop();
+        sl.first += x;
+        mx = std::max(mx, sl.first);
+        pq.push(sl);
+    }
+    return mx;
+}
+
+SplitPlan split_long_rows(std::vector<int32_t>& rows, std::vector<int64_t>& nz, int cap,
+                          int workers)
+{
+    SplitPlan plan;
+    const int nt = (int)rows.size() - 1;
+    if (!kSpmvWs || nt <= 0 || workers <= 0) return plan;
+    std::vector<int64_t> cost((size_t)nt);
+    int64_t total = 0;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t len = nz[(size_t)t + 1] - nz[(size_t)t];
+        cost[(size_t)t] = std::max<int64_t>(1, (len + cap - 1) / cap);
+        total += cost[(size_t)t];
+    }
+    const double mean = (double)total / workers;
+    if ((double)lpt_makespan(cost, workers) <= 1.15 * std::max(mean, 1.0)) return plan;
+    // pieces of about an eighth of a list (at least two chunks)
+    const int64_t tp = std::max<int64_t>(2, (int64_t)std::ceil(mean / 8.0));
+    std::vector<int32_t> r2;
+    std::vector<int64_t> n2;
+    r2.reserve(rows.size());
+    n2.reserve(nz.size());
+    for (int t = 0; t < nt; ++t) {
+        const int64_t a = nz[(size_t)t], b = nz[(size_t)t + 1];
+        const int64_t c = cost[(size_t)t];
+        const bool one_row = rows[(size_t)t + 1] - rows[(size_t)t] == 1;
+        if (!one_row || b - a <= cap || c < 2 * tp) {
+            r2.push_back(rows[(size_t)t]);
+            n2.push_back(a);
+            plan.task_piece.push_back(-1);
+            continue;
+        }
+        const int64_t np = (c + tp - 1) / tp;
+        const int64_t per = (c + np - 1) / np;   // chunks per piece
+        const int s = (int)plan.info.size() / 2;
+        plan.info.push_back(plan.npieces);
+        int cnt = 0;
+        for (int64_t p0 = a; p0 < b; p0 += per * cap) {
+            r2.push_back(rows[(size_t)t]);
+            n2.push_back(p0);
+            plan.task_piece.push_back(plan.npieces + cnt);
+            plan.pspl.push_back(s);
+            ++cnt;
+        }
+        plan.info.push_back(cnt);
+        plan.npieces += cnt;
+    }
+    r2.push_back(rows.back());
+    n2.push_back(nz.back());
+    plan.n = (int)plan.info.size() / 2;
+    if (plan.n == 0) return SplitPlan{};
+    rows.swap(r2);
+    nz.swap(n2);
+    return plan;
+}
+
 // ------------------------------------------------------------------ kernels
 
 __global__ void k_validate(int64_t m, int64_t n, int64_t nnz, const int64_t* rp,
@@ -629,9 +704,9 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     // (K~ (b / ||b||) = (K~ b) / ||b||), so b is never rewritten.
     double* b = E.XA;          // n
     double* t = E.KXA;         // m
-    double* part = h->scratch;  // partials of ||b||^2 (gT) / ||t||^2 (gK)
-    int* go = reinterpret_cast<int*>(h->scratch + std::max(E.gK, E.gT) + 8);
-    double* inv = h->scratch + std::max(E.gK, E.gT) + 16;   // 1 / ||b||
+    double* part = h->scratch;  // partials of ||b||^2 (npT) / ||t||^2 (npK)
+    int* go = reinterpret_cast<int*>(h->scratch + std::max(E.npK, E.npT) + 8);
+    double* inv = h->scratch + std::max(E.npK, E.npT) + 16;   // 1 / ||b||
     LP_CUDA_TRY((spmv_prepare<double, EpiStore<double>>()));
     k_fill<double><<<grid_for(n), 256, 0, st>>>(b, n, 1.0);
     ++h->launches;
@@ -642,29 +717,60 @@ lp_status setup_scale(Handle* h, const lp_opts* o, double* normK)
     ++h->launches;
     for (int it = 0; it < o->power_iters; ++it) {
         EpiStore<double> e1{b, t, inv, nullptr, go};
-        launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
+        launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1,
+                            false, E.splitK);
         ++h->launches;
         EpiStore<double> e2{t, b, nullptr, part, go};
         launch_spmv<double>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m,
-                            e2);
+                            e2, false, E.splitT);
         ++h->launches;
-        k_pow_inv_norm<<<1, kCtlNT, 0, st>>>(part, E.gT, inv, go);
+        k_pow_inv_norm<<<1, kCtlNT, 0, st>>>(part, E.npT, inv, go);
         ++h->launches;
         LP_CUDA_TRY(cudaGetLastError());
     }
     EpiStore<double> e3{b, t, inv, part, nullptr};
-    launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e3);
+    launch_spmv<double>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e3,
+                        false, E.splitK);
     ++h->launches;
-    k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.gK, part + E.gK + 4);
+    k_sum_final<<<1, kCtlNT, 0, st>>>(part, E.npK, part + E.npK + 4);
     ++h->launches;
     LP_CUDA_TRY(cudaGetLastError());
     double s2 = 0.0;
     int derr = 0;
-    LP_CUDA_TRY(cudaMemcpyAsync(&s2, part + E.gK + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LP_CUDA_TRY(cudaMemcpyAsync(&s2, part + E.npK + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
     LP_CUDA_TRY(cudaMemcpyAsync(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     LP_CUDA_TRY(cudaStreamSynchronize(st));
     if (derr) return LP_DEVICE_TIMEOUT;
     *normK = std::sqrt(s2);
+    return LP_OK;
+}
+
+// Device copy of a split plan (the previous one of the engine is freed); the
+// tickets start at zero.
+template <typename T>
+static lp_status upload_split(Handle* h, const SplitPlan& plan, SplitRows& sp)
+{
+    dev_free(h, (void*)sp.pspl);
+    dev_free(h, (void*)sp.info);
+    dev_free(h, sp.cnt);
+    dev_free(h, sp.slots);
+    sp = SplitRows{};
+    if (plan.n == 0) return LP_OK;
+    int32_t *pspl = nullptr, *info = nullptr;
+    T* slots = nullptr;
+    LP_TRY(dev_alloc_n(h, &pspl, (size_t)plan.npieces));
+    LP_TRY(dev_alloc_n(h, &info, plan.info.size()));
+    LP_TRY(dev_alloc_n(h, &sp.cnt, (size_t)plan.n));
+    LP_TRY(dev_alloc_n(h, &slots, (size_t)plan.npieces));
+    LP_CUDA_TRY(cudaMemcpyAsync(pspl, plan.pspl.data(), plan.pspl.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    LP_CUDA_TRY(cudaMemcpyAsync(info, plan.info.data(), plan.info.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    LP_CUDA_TRY(cudaMemsetAsync(sp.cnt, 0, (size_t)plan.n * sizeof(int), h->stream));
+    sp.pspl = pspl;
+    sp.info = info;
+    sp.slots = slots;
+    sp.n = plan.n;
     return LP_OK;
 }
 
@@ -681,6 +787,10 @@ lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
     int sms = 0;
     LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     const int gK = spmv_grid<T>((int)bk.size() - 1, sms), gT = spmv_grid<T>((int)bt.size() - 1, sms);
+    // long rows cut into pieces where the lists would be unbalanced (the grids
+    // stay those of the uncut schedules)
+    const SplitPlan spK = split_long_rows(bk, nk, sK.cap, gK * kSpmvWorkers);
+    const SplitPlan spT = split_long_rows(bt, nt, sT.cap, gT * kSpmvWorkers);
     std::vector<int32_t> wk, pk, wt, pt;
     assign_tasks(nk, sK.cap, gK * kSpmvWorkers, wk, pk);
     assign_tasks(nt, sT.cap, gT * kSpmvWorkers, wt, pt);
@@ -689,6 +799,30 @@ lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
         dev_free(h, p);
     E.brow = E.bcol = E.wbegK = E.permK = E.wbegT = E.permT = nullptr;
     E.bnzK = E.bnzT = nullptr;
+    LP_TRY(upload_split<T>(h, spK, E.splitK));
+    LP_TRY(upload_split<T>(h, spT, E.splitT));
+    // a piece carries its slot + 1 in the high 32 bits of its first nonzero
+    for (size_t t = 0; t < spK.task_piece.size(); ++t)
+        if (spK.task_piece[t] >= 0) nk[t] |= (int64_t)(spK.task_piece[t] + 1) << 32;
+    for (size_t t = 0; t < spT.task_piece.size(); ++t)
+        if (spT.task_piece[t] >= 0) nt[t] |= (int64_t)(spT.task_piece[t] + 1) << 32;
+    // step partials: one per block, then one per split row
+    const size_t npK = (size_t)gK + (size_t)spK.n, npT = (size_t)gT + (size_t)spT.n;
+    const size_t needD = 2 * npK + 8, needT = std::max<size_t>(npT, (size_t)kEWGrid) + 8;
+    if (needD > E.partD_cap) {
+        dev_free(h, E.partD);
+        E.partD = nullptr;
+        LP_TRY(dev_alloc_n(h, &E.partD, needD));
+        E.partD_cap = needD;
+    }
+    if (needT > E.partT_cap) {
+        dev_free(h, E.partT);
+        E.partT = nullptr;
+        LP_TRY(dev_alloc_n(h, &E.partT, needT));
+        E.partT_cap = needT;
+    }
+    E.npK = (int)npK;
+    E.npT = (int)npT;
     LP_TRY(dev_alloc_n(h, &E.brow, bk.size()));
     LP_TRY(dev_alloc_n(h, &E.bcol, bt.size()));
     LP_TRY(dev_alloc_n(h, &E.bnzK, nk.size()));
@@ -747,11 +881,6 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
         T** vm[] = {&E.q,  &E.Y[0], &E.Y[1], &E.KX[0], &E.KX[1],
                     &E.YS, &E.YA,   &E.KXA,  &E.YANC,  &E.KXANC};
         for (T** p : vm) LP_TRY(dev_alloc_n(h, p, (size_t)m));
-        int sms = 0;
-        LP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-        const size_t gmax = (size_t)spmv_grid<float>(1 << 30, sms);
-        LP_TRY(dev_alloc_n(h, &E.partD, 2 * gmax + 8));
-        LP_TRY(dev_alloc_n(h, &E.partT, (size_t)kEWGrid + 8));
         LP_TRY(dev_alloc_n(h, &E.partR, kRowQ * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.partC, kColQ * (size_t)kEWGrid));
         LP_TRY(dev_alloc_n(h, &E.ctrl, 1));

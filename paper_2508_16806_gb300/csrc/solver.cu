@@ -56,7 +56,7 @@ template <typename T>
 __global__ void __launch_bounds__(kEW)
 k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0,
          const T* __restrict__ kty1, const T* __restrict__ c, const T* __restrict__ l,
-         const T* __restrict__ u, int64_t n, double* part, int after_step)
+         const T* __restrict__ u, int64_t n, double* part, int after_step, int nsplit)
 {
     // after_step = 0: after a check (and at the start); 1: after the K^T launch
     // of an attempt when the primal step is not fused into it (its mode 1 or 3)
@@ -104,6 +104,10 @@ k_primal(const Ctrl* __restrict__ ctrl, T* x0, T* x1, const T* __restrict__ kty0
     }
     const double t[1] = {(double)dx2};
     block_partials<1, kEW>(t, part, gridDim.x);
+    // the K^T launch's split-row slots follow the block partials; every column
+    // is covered above, so they hold nothing of this step
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nsplit; i += kEW) part[gridDim.x + i] = 0.0;
 }
 
 // Halpern iteration, primal half: x^ = clamp(x - tau (c - K^T y), l, u) (the
@@ -256,8 +260,9 @@ struct EpiDual {
     T* ys;
     const T* q;
     const uint8_t* sense;
-    double* part;                   // [2][gridDim.x] partials of this launch
+    double* part;                   // [2][gridDim.x + nsplit] partials of this launch
     int cur; T sigma; T pw; int adapt;
+    int nsplit = 0;                 // split rows of the schedule (set by the kernel)
     struct Pre { T y = 0, kx = 0, q = 0, ys = 0; uint8_t ge = 0; };
     // per-lane sums in T, reduced in FP64: ||y' - y||^2 and the Algorithm 5
     // interaction (y' - y)^T K (x' - x) = sum_i dy_i ((K x')_i - (K x)_i)
@@ -302,15 +307,23 @@ struct EpiDual {
         a.dy2 += d * d;
         a.inter += d * (kxn - p.kx);
     }
+    // a split row's terms: after the block partials of each quantity
+    __device__ void split_acc(int s, const Acc& a) const {
+        if (adapt) {
+            const int np = (int)gridDim.x + nsplit;
+            part[gridDim.x + s] = (double)a.dy2;
+            part[np + gridDim.x + s] = (double)a.inter;
+        }
+    }
     __device__ void finish(Acc& a) const {
+        const int np = (int)gridDim.x + nsplit;
         if (adapt) {
             const double t[2] = {(double)a.dy2, (double)a.inter};
-            block_partials<2, kSpmvNT>(t, part, gridDim.x);
+            block_partials<2, kSpmvNT>(t, part, np);
         }
         // ||x' - x||^2 partials: Ctrl::px[0, npx) (kept in the control block, not in
         // this epilogue, whose members live in registers through the whole SpMV)
-        last_block_decide<kSpmvNT>(ctrl, part, gridDim.x, ctrl->px, ctrl->npx, adapt != 0, adapt,
-                                   true);
+        last_block_decide<kSpmvNT>(ctrl, part, np, ctrl->px, ctrl->npx, adapt != 0, adapt, true);
     }
 };
 
@@ -333,9 +346,10 @@ struct EpiPrimalStep {
     T* kty0; T* kty1;               // KTY[0], KTY[1]
     const T* c; const T* l; const T* u;
     T* xsum;
-    double* part;                   // [gridDim.x] ||x'' - x'||^2 partials
+    double* part;                   // [gridDim.x + nsplit] ||x'' - x'||^2 partials
     int64_t n;
     int mode; T tau; T pw; int adapt;
+    int nsplit = 0;                 // split rows of the schedule (set by the kernel)
     struct Pre { T x = 0, c = 0, l = 0, u = 0, s = 0; };
     struct Acc { T dx2 = T(0); };
     // after begin(): xs0 / ys0 / kty0 are the current half (x', y', K^T y'),
@@ -369,6 +383,10 @@ struct EpiPrimalStep {
         }
         const double t[1] = {(double)dx2};
         block_partials<1, kSpmvNT>(t, part, gridDim.x);
+        // the split rows' slots hold nothing of this step: their columns are
+        // covered by the loop above
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i < nsplit; i += blockDim.x) part[gridDim.x + i] = 0.0;
         return false;
     }
     __device__ const T* xin() const { return ys0; }   // y'
@@ -394,6 +412,9 @@ struct EpiPrimalStep {
             a.dx2 += (v - p.x) * (v - p.x);
         }
     }
+    __device__ void split_acc(int s, const Acc& a) const {
+        if (mode == 1 && adapt) part[gridDim.x + s] = (double)a.dx2;
+    }
     __device__ void finish(Acc& a) const {
         if (mode == 1 && adapt) {
             const double t[1] = {(double)a.dx2};
@@ -418,8 +439,9 @@ struct EpiHalpernDual {
     T* yh;
     const T* q;
     const uint8_t* sense;
-    double* part;
+    double* part;                   // [2][gridDim.x + nsplit]
     T sigma, a, b, g; int hat;
+    int nsplit = 0;                 // split rows of the schedule (set by the kernel)
     // the anchor terms are read in row(): a smaller Pre keeps the SpMV's two
     // prefetched rows per lane in registers
     struct Pre { T y = 0, kx = 0, q = 0; uint8_t ge = 0; };
@@ -458,9 +480,14 @@ struct EpiHalpernDual {
         kx1[i] = a * kxh - b * p.kx + g * kxanc[i];
         if (hat) yh[i] = v;
     }
+    __device__ void split_acc(int s, const Acc& acc) const {
+        const int np = (int)gridDim.x + nsplit;
+        part[gridDim.x + s] = (double)acc.dy2;
+        part[np + gridDim.x + s] = (double)acc.inter;
+    }
     __device__ void finish(Acc& acc) const {
         const double t[2] = {(double)acc.dy2, (double)acc.inter};
-        block_partials<2, kSpmvNT>(t, part, gridDim.x);
+        block_partials<2, kSpmvNT>(t, part, (int)gridDim.x + nsplit);
     }
 };
 
@@ -816,7 +843,7 @@ template <typename T>
 static void launch_primal(Handle* h, Engine<T>& E, cudaStream_t st, int after_step = 0)
 {
     k_primal<T><<<E.gT, kEW, 0, st>>>(E.ctrl, E.X[0], E.X[1], E.KTY[0], E.KTY[1], E.c, E.l, E.u,
-                                      h->n, E.partT, after_step);
+                                      h->n, E.partT, after_step, E.splitT.n);
 }
 
 template <typename T>
@@ -825,7 +852,7 @@ static void launch_dual(Handle* h, Engine<T>& E, cudaStream_t st)
     EpiDual<T> ed{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS, E.q, h->sense,
                   E.partD};
     launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed,
-                   true);
+                   true, E.splitK);
 }
 
 template <typename T>
@@ -835,7 +862,7 @@ static void launch_primal_step(Handle* h, Engine<T>& E, cudaStream_t st, bool wi
     EpiPrimalStep<T, F> ep{E.ctrl, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KTY[0], E.KTY[1], E.c, E.l,
                            E.u, E.XS, E.partT, h->n};
     launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval,
-                   h->dev_err, h->m, ep, true);
+                   h->dev_err, h->m, ep, true, E.splitT);
     if (!F && with_primal) launch_primal<T>(h, E, st, 1);
 }
 
@@ -844,8 +871,9 @@ template <typename T>
 static void launch_primal_t(Handle* h, Engine<T>& E, cudaStream_t st)
 {
     EpiPrimalT<T> et{E.ctrl, E.Y[0], E.Y[1], E.KTY[0], E.KTY[1], E.partT, primal_grid<T>(h->n),
-                     E.partD, E.gK};
-    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
+                     E.partD, E.npK};
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et,
+                   false, E.splitT);
 }
 
 template <typename T>
@@ -862,7 +890,7 @@ static void launch_dual_halpern(Handle* h, Engine<T>& E, cudaStream_t st)
     EpiHalpernDual<T> ed{E.ctrl, E.XH, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YANC, E.KXANC, E.YA,
                          E.q, h->sense, E.partD};
     launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val,
-                   h->dev_err, h->n, ed);
+                   h->dev_err, h->n, ed, false, E.splitK);
 }
 
 // one step attempt: 2 launches (PDHG) or 3 (a Halpern iteration)
@@ -895,9 +923,11 @@ static void launch_check(Handle* h, Engine<T>& E, cudaStream_t st, cudaGraphCond
                                                      E.YS, E.XA, E.YA, E.l, E.u, h->sense, n, m);
     const int* gate = &E.ctrl->want_check;
     EpiStore<T> e1{E.XA, E.KXA, nullptr, nullptr, gate};
-    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1,
+                   false, E.splitK);
     EpiStore<T> e2{E.YA, E.KTYA, nullptr, nullptr, gate};
-    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2,
+                   false, E.splitT);
     k_check_rows<T><<<kEWGrid, kEW, 0, st>>>(E.ctrl, E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YA,
                                              E.KXA, E.YANC, E.q, h->sense, E.Rt, E.Rinv, m,
                                              E.partR);
@@ -1014,9 +1044,11 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
                                                      E.l, E.u, h->sense, h->R, h->C, wxs, wys,
                                                      dwx, dwy, n, m);
     EpiStore<T> e1{E.X[0], E.KX[0], nullptr, nullptr, nullptr};
-    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1);
+    launch_spmv<T>(E.gK, st, E.brow, E.bnzK, E.nblk, E.wbegK, E.permK, h->rp, h->ci, E.val, h->dev_err, h->n, e1,
+                   false, E.splitK);
     EpiStore<T> e2{E.Y[0], E.KTY[0], nullptr, nullptr, nullptr};
-    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2);
+    launch_spmv<T>(E.gT, st, E.bcol, E.bnzT, E.ntblk, E.wbegT, E.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, e2,
+                   false, E.splitT);
     LP_CUDA_TRY(cudaGetLastError());
     if (m > 0)
         LP_CUDA_TRY(cudaMemcpyAsync(E.KXANC, E.KX[0], sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
@@ -1081,7 +1113,7 @@ lp_status run_solve(Handle* h, const lp_opts* o, double eta0, double omega0,
     c.infeas_tol = o->infeas_tol;
     c.check_every = o->check_every;
     c.px = E.partT;
-    c.npx = E.gT;
+    c.npx = E.npT;
     refresh_scalars(c);
     {
         // the time origin is the device clock read now

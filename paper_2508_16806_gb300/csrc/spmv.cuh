@@ -283,12 +283,21 @@ struct StatelessTasks<E, std::void_t<decltype(E::kStatelessTasks)>>
     : std::integral_constant<bool, E::kStatelessTasks> {};
 
 // A chunk of a stage: its task, nonzero range [cs, ce), flags (bit 0 the
-// task's first chunk, bit 1 its last, bit 2 the task is one long row) and the
-// task's rows [r0, r0 + nrows); task < 0 ends the pair's sequence.
+// task's first chunk, bit 1 its last, bit 2 the task is one long row or a piece
+// of one), the task's rows [r0, r0 + nrows) and, for a piece of a split row,
+// its slot (else -1); task < 0 ends the pair's sequence.
 struct WsDesc {
-    int task, cs, ce, flags, r0, nrows;
+    int task, cs, ce, flags, r0, nrows, piece;
 };
 constexpr int kWsFirst = 1, kWsLast = 2, kWsLong = 4;
+
+// Epilogues whose reductions take split rows: they provide
+// split_acc(int s, const Acc&) and a member nsplit (the kernel sets it to
+// SplitRows::n), and lay their partials out with a stride of gridDim.x + nsplit.
+template <class E, class = void>
+struct HasSplitAcc : std::false_type {};
+template <class E>
+struct HasSplitAcc<E, std::void_t<decltype(&E::split_acc)>> : std::true_type {};
 
 template <typename T>
 struct alignas(16) PairStage {
@@ -592,7 +601,7 @@ __global__ void __launch_bounds__(kSpmvNT, MinBlocks<T>::value)
 k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task_nz, int ntasks,
           const int32_t* __restrict__ wbeg, const int32_t* __restrict__ perm,
           const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-          const T* __restrict__ val, int* err, Epi epi)
+          const T* __restrict__ val, int* err, SplitRows sp, Epi epi)
 {
     constexpr int CAPW = cap_w<T>();
     constexpr int VA = 16 / (int)sizeof(T);
@@ -601,6 +610,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
     extern __shared__ __align__(16) unsigned char smem_raw[];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
+    if constexpr (HasSplitAcc<Epi>::value) epi.nsplit = sp.n;
     if (!epi.begin()) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pair = warp >> 1;
@@ -632,14 +642,18 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
         auto task_at = [&](int p) { return p < pend ? perm[p] : ntasks; };
         int ipos = next_live(pbeg);
         int itask = task_at(ipos);
-        int is = 0, ie = 0, ics = 0, ir0 = 0, inr = 0;
-        if (itask < ntasks) {
-            is = (int)task_nz[itask];
-            ie = (int)task_nz[itask + 1];
+        int is = 0, ie = 0, ics = 0, ir0 = 0, inr = 0, ipc = -1;
+        // bounds, rows and piece slot of task itask (a piece has no rows of its own)
+        auto load_task = [&]() {
+            const int64_t tz = task_nz[itask];
+            is = (int)(uint32_t)tz;
+            ipc = (int)(tz >> 32) - 1;
+            ie = (int)(uint32_t)task_nz[itask + 1];
             ir0 = task_row[itask];
-            inr = task_row[itask + 1] - ir0;
+            inr = ipc < 0 ? task_row[itask + 1] - ir0 : 0;
             ics = is;
-        }
+        };
+        if (itask < ntasks) load_task();
         int npos = itask < ntasks ? next_live(ipos + 1) : pend;
         int ntask = task_at(npos);
         bool ended = false;       // the terminator has been issued
@@ -659,27 +673,24 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                     return;
                 }
             }
-            WsDesc d{-1, 0, 0, 0};
+            WsDesc d{-1, 0, 0, 0, 0, 0, -1};
             if (itask < ntasks) {
                 const int cs = ics, ce = ie - ics > CAPW ? ics + CAPW : ie;
                 d.task = itask;
                 d.cs = cs;
                 d.ce = ce;
                 d.flags = (cs == is ? kWsFirst : 0) | (ce == ie ? kWsLast : 0) |
-                          (ie - is > CAPW ? kWsLong : 0);
+                          (ie - is > CAPW || ipc >= 0 ? kWsLong : 0);
                 d.r0 = ir0;
                 d.nrows = inr;
+                d.piece = ipc;
                 if (ce != ie) {
                     ics = ce;
                 } else {
                     ipos = npos;
                     itask = ntask;
                     if (itask < ntasks) {
-                        is = (int)task_nz[itask];
-                        ie = (int)task_nz[itask + 1];
-                        ir0 = task_row[itask];
-                        inr = task_row[itask + 1] - ir0;
-                        ics = is;
+                        load_task();
                         npos = next_live(ipos + 1);
                         ntask = task_at(npos);
                     }
@@ -858,7 +869,33 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
             if (lng) {
                 if (d.flags & kWsLast) {
                     const T a = warp_sum_T(P.v[st][lane]);
-                    if (lane == 0) epi.row(r0, a, pre0, acc);
+                    if (lane == 0) {
+                        if (d.piece < 0) {
+                            epi.row(r0, a, pre0, acc);
+                        } else if (sp.slots == nullptr) {
+                            atomicOr(err, 2);   // a schedule with pieces launched without them
+                        } else {
+                            // a piece of a split row (see SplitRows)
+                            T* slots = static_cast<T*>(sp.slots);
+                            slots[d.piece] = a;
+                            __threadfence();
+                            const int sr = sp.pspl[d.piece];
+                            const int g0 = sp.info[2 * sr], np = sp.info[2 * sr + 1];
+                            if (atomicAdd(&sp.cnt[sr], 1) == np - 1) {
+                                __threadfence();
+                                T v = T(0);
+                                for (int p = 0; p < np; ++p) v += __ldcg(slots + g0 + p);
+                                sp.cnt[sr] = 0;
+                                const typename Epi::Pre pr = epi.load(r0);
+                                typename Epi::Acc sa{};
+                                epi.row(r0, v, pr, sa);
+                                if constexpr (HasSplitAcc<Epi>::value)
+                                    epi.split_acc(sr, sa);
+                                else if constexpr (!std::is_empty<typename Epi::Acc>::value)
+                                    atomicOr(err, 2);   // reductions without a split slot
+                            }
+                        }
+                    }
                 }
             } else {
                 const int v0 = d.cs & ~(VA - 1);
@@ -931,14 +968,42 @@ constexpr int64_t kL1GatherBytes = 96 * 1024;
 #ifndef PDHG_PDL
 #define PDHG_PDL 0
 #endif
+// sp: the split rows of the schedule (none by default; a schedule with pieces
+// must be launched with its SplitRows).
 template <typename T, class Epi>
 inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
                         const int64_t* task_nz, int ntasks, const int32_t* wbeg,
                         const int32_t* perm, const int64_t* rp, const int32_t* ci, const T* val,
-                        int* err, int64_t x_len, const Epi& epi, bool pdl = false)
+                        int* err, int64_t x_len, const Epi& epi, bool pdl = false,
+                        const SplitRows& sp = SplitRows{})
 {
     const size_t sm = spmv_smem_bytes<T>();
     const bool l1 = x_len * (int64_t)sizeof(T) <= kL1GatherBytes;
+    if constexpr (kSpmvWs) {
+        if (pdl && PDHG_PDL) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)grid);
+            cfg.blockDim = dim3(kSpmvNT);
+            cfg.dynamicSmemBytes = sm;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            auto kern = l1 ? k_spmv_ws<T, Epi, true> : k_spmv_ws<T, Epi, false>;
+            (void)cudaLaunchKernelEx(&cfg, kern, task_row, task_nz, ntasks, wbeg, perm, rp, ci,
+                                     val, err, sp, epi);
+            return;
+        }
+        if (l1)
+            k_spmv_ws<T, Epi, true><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg,
+                                                               perm, rp, ci, val, err, sp, epi);
+        else
+            k_spmv_ws<T, Epi, false><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg,
+                                                                perm, rp, ci, val, err, sp, epi);
+        return;
+    }
     if (pdl && PDHG_PDL) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
@@ -950,19 +1015,9 @@ inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        auto kern = kSpmvWs ? (l1 ? k_spmv_ws<T, Epi, true> : k_spmv_ws<T, Epi, false>)
-                            : (l1 ? k_spmv<T, Epi, true> : k_spmv<T, Epi, false>);
+        auto kern = l1 ? k_spmv<T, Epi, true> : k_spmv<T, Epi, false>;
         (void)cudaLaunchKernelEx(&cfg, kern, task_row, task_nz, ntasks, wbeg, perm, rp, ci, val,
                                  err, epi);
-        return;
-    }
-    if constexpr (kSpmvWs) {
-        if (l1)
-            k_spmv_ws<T, Epi, true><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg,
-                                                               perm, rp, ci, val, err, epi);
-        else
-            k_spmv_ws<T, Epi, false><<<grid, kSpmvNT, sm, st>>>(task_row, task_nz, ntasks, wbeg,
-                                                                perm, rp, ci, val, err, epi);
         return;
     }
     if (l1)
@@ -993,6 +1048,7 @@ struct EpiStore {
     const double* scale;     // nullptr = 1
     double* part;            // nullptr = no partials
     const int* gate;         // nullptr = always run; else run when *gate != 0
+    int nsplit = 0;          // split rows of the schedule (set by the kernel)
     struct Pre {};
     struct Acc { double s2 = 0.0; };
     __device__ bool begin() const { return gate == nullptr || *gate != 0; }
@@ -1002,6 +1058,10 @@ struct EpiStore {
         if (scale) v = (T)((double)v * *scale);
         out[r] = v;
         if (part) a.s2 += (double)v * (double)v;
+    }
+    // partials: part[0, gridDim.x + nsplit)
+    __device__ void split_acc(int s, const Acc& a) const {
+        if (part) part[gridDim.x + s] = a.s2;
     }
     __device__ void finish(Acc& a) const {
         if (part) {
@@ -1037,6 +1097,26 @@ std::vector<int32_t> make_row_blocks(const int64_t* rp, int64_t rows, int cap, i
 // each warp's tasks in ascending order.
 void assign_tasks(const std::vector<int64_t>& task_nz, int cap, int warps,
                   std::vector<int32_t>& wbeg, std::vector<int32_t>& perm);
+
+// Split rows of a schedule (host side of SplitRows).  task_piece[t]: the piece
+// slot of task t, or -1; pspl[g]: the split row of piece slot g; info[2 s],
+// info[2 s + 1]: first piece slot and number of pieces of split row s.
+struct SplitPlan {
+    std::vector<int32_t> task_piece, pspl, info;
+    int n = 0, npieces = 0;
+};
+
+// Cuts the one-row tasks of a schedule (rows: task row bounds, nz: task
+// nonzero bounds, both ntasks + 1 entries) into pieces when the longest-first
+// assignment to `workers` lists would leave the longest list more than 15 %
+// above the mean (in chunks of `cap` nonzeros): each one-row task of at least
+// two pieces' worth of chunks becomes pieces of about an eighth of a list (at
+// least two chunks), whole chunks from the row's start.  rows / nz are
+// rewritten in place (a piece repeats its row; the entry after the last piece
+// is the next row); returns the plan (n = 0: nothing cut, rows / nz untouched).
+// Only the warp-specialised SpMV takes pieces: without it nothing is cut.
+SplitPlan split_long_rows(std::vector<int32_t>& rows, std::vector<int64_t>& nz, int cap,
+                          int workers);
 
 // Schedule autotuner (tune.cu).  Candidates: cap in {CAPW, CAPW / 2} nonzeros
 // and max_rows in {kTaskRows, 32, 16} rows per task.  build(cap, max_rows)

@@ -79,7 +79,7 @@ class LpResult(C.Structure):
                 ("setup_s", C.c_double), ("solve_s", C.c_double),
                 ("kernel_launches", C.c_int64),
                 ("x", C.c_void_p), ("y", C.c_void_p),
-                ("memory_space", C.c_int32), ("reserved", C.c_int32),
+                ("memory_space", C.c_int32), ("split_rows", C.c_int32),
                 ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("trace_len", C.c_int64),
                 ("pc_alpha_used", C.c_double), ("attempt_len", C.c_int64)]
 

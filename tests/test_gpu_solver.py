@@ -133,47 +133,77 @@ def test_fp64_adaptive_iterates_track_oracle(L, oracle_mod, name, iters):
 @pytest.mark.parametrize("name", ["lp200x400", "ragged", "shuffled", "powerlaw"])
 def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
     """Parity of the adaptive path (Algorithm 5) over 1000 iterations by replay:
-    the oracle takes the GPU run's step sizes and accept / reject outcomes from
-    its attempt log and computes everything else itself.  Its iterates then
-    track the GPU's to 1e-10, its own eta_bar agrees with the GPU's at every
-    attempt, every GPU outcome is the one its eta_bar gives (unless eta sits
-    within 1e-8 of eta_bar), and its own eta' from Algorithm 5 is the GPU's."""
+    the oracle takes the GPU run's discrete decisions (step sizes and accept /
+    reject outcomes from its attempt log, restart and candidate choices from its
+    trace) and computes everything else itself.  Then its iterates track the
+    GPU's to 1e-10; its own Algorithm 5 quantities (eta_bar, eta') agree with the
+    GPU's within what that iterate agreement allows; and every GPU decision is
+    the oracle's own, except where the oracle's quantities tie at that level
+    (a restart criterion, a candidate comparison or eta <= eta_bar decided by
+    less than the tolerance)."""
     lp = PROBS[name]
     prob = L.Problem(lp)
     x, y, info, tr = prob.solve(tol=1e-13, max_iters=1000, trace_cap=4096, attempt_cap=5000)
     log = info["attempt_log"]
     assert info["attempt_len"] == info["attempts"] == len(log) >= 1000
     rows = np.array([[a[f] for f in L.ATTEMPT_FIELDS] for a in log])
+    checks = np.array([[t["restart"], t["cand_is_avg"]] for t in tr])
     xo, yo, io, tro, att = oracle_mod.solve_logged(lp, tol=1e-13, max_iters=1000,
-                                                   trace_cap=4096, replay=rows)
+                                                   trace_cap=4096, replay=rows,
+                                                   replay_checks=checks)
     assert io["iters"] == info["iters"] == 1000 and io["attempts"] == info["attempts"]
-    assert rel(x, xo) <= 1e-10, rel(x, xo)
-    assert rel(y, yo) <= 1e-10, rel(y, yo)
-    # check records: the same decisions; the KKT figures of the current iterate
-    # carry cancellation (a gap of O(|objective|) terms), so one-ulp step-size
-    # differences already move them by 1e-7 relative within the oracle itself
+    eps_it = 1e-10
+    assert rel(x, xo) <= eps_it, rel(x, xo)
+    assert rel(y, yo) <= eps_it, rel(y, yo)
+    # Tolerances from the iterate agreement: the terms of an attempt are
+    # differences of iterates (||dx||^2, ||dy||^2) and dy^T K dx; with iterates
+    # agreeing to eps_it ||z|| (z the scaled iterate), dz agrees to about
+    # eps_it ||z|| absolute and the interaction to eps_it ||z|| ||K~|| ||dz||, so
+    # eta_bar (a ratio of them) agrees to tol_terms below.  KKT values are
+    # residual norms of the iterates: relative agreement eps_it ||K~|| ||z|| / KKT
+    # (floored at 1e-6, the summation-order level of the gap term's cancellation).
+    _, R, Cs, _ = oracle_mod.ruiz(lp)
+    znorm = np.sqrt(np.sum((xo / Cs) ** 2) + np.sum((yo / R) ** 2))
+    nk = info["norm_K"]
+    decided_by_tie = 0
     assert len(tr) == len(tro)
     for a, b in zip(tr, tro):
         for f in ("k", "attempts", "restart", "cand_is_avg"):
             assert a[f] == b[f], (f, a, b)
-        for f in ("omega", "eta"):
-            assert a[f] == pytest.approx(b[f], rel=1e-10), (f, a[f], b[f])
-        for f in ("kkt_cur", "kkt_cand", "rel_gap", "rel_pres", "rel_dres"):
+        assert a["omega"] == pytest.approx(b["omega"], rel=1e-8), (a, b)
+        tol_kkt = lambda v: max(1e-6, 4 * eps_it * nk * znorm / max(abs(v), 1e-300))
+        for f in ("kkt_cur", "kkt_cand"):
+            assert a[f] == pytest.approx(b[f], rel=tol_kkt(b[f])), (f, a[f], b[f])
+        for f in ("rel_gap", "rel_pres", "rel_dres"):
             assert a[f] == pytest.approx(b[f], rel=1e-6, abs=1e-10), (f, a[f], b[f])
+        # the GPU's decisions against the oracle's own
+        if b["own_cand_is_avg"] != b["cand_is_avg"]:
+            assert abs(b["kkt_cur"] - b["kkt_avg"]) <= tol_kkt(b["kkt_cur"]) * b["kkt_cur"], (a, b)
+            decided_by_tie += 1
+        if b["own_restart"] != b["restart"]:
+            c, t = b["kkt_cand"], tol_kkt(b["kkt_cand"]) * b["kkt_cand"]
+            near = (abs(c - oracle_mod.DEFAULTS["beta_sufficient"] * b["kkt_anchor"]) <= t
+                    or abs(c - oracle_mod.DEFAULTS["beta_necessary"] * b["kkt_anchor"]) <= t
+                    or abs(c - b["kkt_prev"]) <= t)
+            assert near, (a, b)
+            decided_by_tie += 1
     rejected = 0
     for g, o in zip(log, att):
         assert g["k"] == o["k"] and g["eta"] == o["eta"]
-        # eta_bar divides by the interaction dy^T K dx, a sum of terms of both
-        # signs whose summation order differs between the two runs: well above
-        # eta (where eta' = (1 + (k+1)^-0.6) eta does not depend on it and the
-        # step is accepted either way) it is compared loosely
-        tol_eb = 1e-8 if o["eta_bar"] < 2 * g["eta"] else 1e-5
-        assert g["eta_bar"] == pytest.approx(o["eta_bar"], rel=tol_eb), (g, o)
-        if abs(g["eta"] - o["eta_bar"]) > 1e-8 * o["eta_bar"]:
+        dz = np.sqrt(o["dx2"] + o["dy2"])
+        tol_terms = max(1e-8, 8 * eps_it * znorm * (1.0 / max(dz, 1e-300)
+                                                    + nk * dz / max(abs(o["inter"]), 1e-300)))
+        # where eta_bar sits well above eta, eta' = (1 + (k+1)^-0.6) eta does not
+        # depend on it and the step is accepted either way: compared loosely there
+        tol_eb = max(tol_terms, 1e-5) if o["eta_bar"] >= 2 * g["eta"] else tol_terms
+        assert g["eta_bar"] == pytest.approx(o["eta_bar"], rel=tol_eb), (g, o, tol_eb)
+        if abs(g["eta"] - o["eta_bar"]) > tol_eb * o["eta_bar"]:
             assert bool(g["accept"]) == (g["eta"] <= o["eta_bar"]), (g, o)
-        assert g["eta_next"] == pytest.approx(o["eta_next"], rel=1e-8), (g, o)
+        elif bool(g["accept"]) != (g["eta"] <= o["eta_bar"]):
+            decided_by_tie += 1
+        assert g["eta_next"] == pytest.approx(o["eta_next"], rel=tol_terms), (g, o)
         rejected += int(not g["accept"])
-    print(name, "rejected attempts", rejected)
+    print(name, "rejected attempts", rejected, "decisions taken at a tie", decided_by_tie)
 
 
 # ---------------------------------------------------------------- to tolerance

@@ -252,3 +252,44 @@ def test_replay_of_own_log_reproduces_the_run(oracle_mod):
     np.testing.assert_array_equal(x, x2)
     np.testing.assert_array_equal(y, y2)
     assert att == att2 and tr == tr2 and i2["attempts"] == info["attempts"]
+
+
+def test_replay_of_own_checks_reproduces_the_run(oracle_mod):
+    """Replaying a run's own check decisions as well (restart, candidate) still
+    reproduces it bit for bit; its own decisions are logged beside the replayed
+    ones and agree with them, and the logged KKT values the restart criteria
+    compared give the logged decision (Section 2.4.2: sufficient decay, necessary
+    decay without progress, or the artificial restart, which the epoch length
+    decides and which is therefore left out here)."""
+    lp = synth.ragged_lp()
+    x, y, info, tr, att = oracle_mod.solve_logged(lp, tol=1e-9, max_iters=700, check_every=32)
+    rows = np.array([[a[f] for f in oracle_mod.ATTEMPT_FIELDS] for a in att])
+    chk = np.array([[t["restart"], t["cand_is_avg"]] for t in tr])
+    x2, y2, i2, tr2, att2 = oracle_mod.solve_logged(lp, tol=1e-9, max_iters=700, check_every=32,
+                                                    replay=rows, replay_checks=chk)
+    np.testing.assert_array_equal(x, x2)
+    np.testing.assert_array_equal(y, y2)
+    assert att == att2 and tr == tr2
+    assert info["restarts"] > 0
+    d = oracle_mod.DEFAULTS
+    for t in tr[1:]:
+        assert t["own_restart"] == t["restart"] and t["own_cand_is_avg"] == t["cand_is_avg"]
+        c = t["kkt_cand"]
+        crit1 = c <= d["beta_sufficient"] * t["kkt_anchor"]
+        crit2 = c <= d["beta_necessary"] * t["kkt_anchor"] and c > t["kkt_prev"]
+        if crit1 or crit2:
+            assert t["restart"] == 1.0
+
+
+def test_replayed_check_decision_is_followed(oracle_mod):
+    """A replayed restart decision that differs from the run's own is taken (the
+    trace shows the replayed one, the own one beside it) and changes the run."""
+    lp = synth.ragged_lp()
+    x, y, info, tr, _ = oracle_mod.solve_logged(lp, tol=1e-9, max_iters=400, check_every=32)
+    chk = np.array([[t["restart"], t["cand_is_avg"]] for t in tr])
+    c = next(i for i in range(1, len(tr)) if tr[i]["restart"] == 0.0)
+    chk[c, 0] = 1.0
+    x2, y2, i2, tr2, _ = oracle_mod.solve_logged(lp, tol=1e-9, max_iters=400, check_every=32,
+                                                 replay_checks=chk)
+    assert tr2[c]["restart"] == 1.0 and tr2[c]["own_restart"] == 0.0
+    assert i2["restarts"] >= info["restarts"] + 1 or not np.array_equal(x, x2)
