@@ -144,6 +144,83 @@ __device__ __forceinline__ T warp_sum_T(T v)
     return v;   // valid in lane 0
 }
 
+// Row sums of a short task's products vs[0, len) (rows j < nrows start at
+// rps[j], rps[nrows] = len) into rsum[0, nrows), by the whole warp with every
+// lane on an equal share: lane l adds the E = ceil(len / 32) consecutive
+// products from l E, cutting at row starts.  A row that lies inside one lane's
+// share is stored by that lane; the pieces of a row that crosses lanes are
+// combined by a segmented inclusive scan over the lanes (Hillis-Steele with the
+// row of each lane's last piece as the key; the keys do not decrease from lane
+// to lane, so a match over a distance covers every lane between), and the lane
+// holding the row's last product stores it.  Rows with no products get 0.  The
+// additions have a fixed order, so the sums are bitwise reproducible; the work
+// per lane no longer depends on how the row lengths are mixed (with one group
+// of lanes per row, a task with one long and many short rows waits for the long
+// one).  Leaves the warp synchronised.
+template <typename T>
+__device__ __forceinline__ void seg_row_sums(const T* vs, const int* rps, int nrows, int len,
+                                             int lane, T* rsum)
+{
+    for (int j = lane; j < nrows; j += 32) rsum[j] = T(0);
+    __syncwarp();
+    const int E = (len + 31) >> 5;
+    const int b = lane * E;
+    const int e = b + E < len ? b + E : len;
+    int key = -1;        // row of this lane's last piece (-1: no products)
+    int rend = 0;        // its end
+    int hrow = -1;       // row of the first piece when it continues from earlier lanes and ends here
+    T h = T(0), t = T(0);
+    if (b < len) {
+        // the row holding product b: the last row whose start is <= b (it has products)
+        int lo = 0, hi = nrows - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rps[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        int r = lo;
+        rend = rps[r + 1];
+        const bool cont = rps[r] < b;
+        bool first = true;
+        T a = T(0);
+        for (int p = b; p < e; ++p) {
+            if (p >= rend) {
+                if (first && cont) {
+                    hrow = r;
+                    h = a;
+                } else {
+                    rsum[r] = a;   // a row inside this lane's share
+                }
+                first = false;
+                a = T(0);
+                do {
+                    ++r;
+                    rend = rps[r + 1];
+                } while (p >= rend);
+            }
+            a += vs[p];
+        }
+        key = r;
+        t = a;
+    }
+    T S = t;
+    int K = key;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T Su = __shfl_up_sync(0xffffffffu, S, d);
+        const int Ku = __shfl_up_sync(0xffffffffu, K, d);
+        if (lane >= d && Ku == K) S += Su;
+    }
+    const T Sp = __shfl_up_sync(0xffffffffu, S, 1);
+    const int Kp = __shfl_up_sync(0xffffffffu, K, 1);
+    // the first piece of a row that began in earlier lanes: their pieces are the
+    // previous lane's scan value
+    if (hrow >= 0) rsum[hrow] = h + ((lane > 0 && Kp == hrow) ? Sp : T(0));
+    // the last piece, where the row ends inside this share
+    if (key >= 0 && rend <= e) rsum[key] = S;
+    __syncwarp();
+}
+
 // ------------------------------------------------------------ async copies
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -259,18 +336,29 @@ static_assert(sizeof(WarpStage<float>) % 16 == 0 && sizeof(WarpStage<double>) % 
 // The warps of a block form producer / consumer pairs (warp 2p produces, warp
 // 2p + 1 consumes) that work through one task list per pair.  The producer
 // streams the chunks through a ring of kWsStages shared-memory stages (bulk
-// copies, issued two chunks ahead), gathers the vector and writes the products
-// back into the stage; the consumer sums the rows of a stage and runs the
-// epilogue, then releases the stage.  Gathers thus stay in flight while rows
+// copies, issued kWsStages - 1 chunks ahead), gathers the vector and writes the
+// products back into the stage; the consumer sums the rows of a stage and runs
+// the epilogue, then releases the stage.  Gathers thus stay in flight while rows
 // are summed and epilogues run (the request stream of a plain gather loop),
-// instead of pausing for them as in the one-warp form.  Products and sums have
-// the one-warp form's order, so both forms give the same bits.
+// instead of pausing for them as in the one-warp form.  Long rows are summed as
+// in the one-warp form; short tasks by seg_row_sums (the one-warp form's lane
+// groups per row with PDHG_WS_SEGSUM=0).  Every order is fixed.
 #ifndef PDHG_SPMV_WS
 #define PDHG_SPMV_WS 1
 #endif
 constexpr bool kSpmvWs = PDHG_SPMV_WS != 0;
 constexpr int kWsPairs = kTaskWarps / 2;
-constexpr int kWsStages = 3;
+#ifndef PDHG_WS_STAGES
+#define PDHG_WS_STAGES 3
+#endif
+constexpr int kWsStages = PDHG_WS_STAGES;
+static_assert(kWsStages >= 3, "the consumer reads the descriptor one chunk ahead");
+// Short tasks' row sums by the segmented form (seg_row_sums: equal shares per
+// lane) instead of one group of lanes per row.
+#ifndef PDHG_WS_SEGSUM
+#define PDHG_WS_SEGSUM 0
+#endif
+constexpr bool kWsSegSum = PDHG_WS_SEGSUM != 0;
 // task lists (workers) per block of an SpMV launch
 constexpr int kSpmvWorkers = kSpmvWs ? kWsPairs : kTaskWarps;
 
@@ -310,6 +398,7 @@ struct alignas(16) PairStage {
     uint64_t empty[kWsStages];     // stage read (32 consumer arrivals)
     WsDesc desc[kWsStages];
     int rps[kTaskRows + 1];        // row starts of the consumer's short task
+    T rsum[kTaskRows];             // its row sums (segmented form)
 };
 static_assert(sizeof(PairStage<float>) % 16 == 0 && sizeof(PairStage<double>) % 16 == 0,
               "stages must stay 16-byte aligned");
@@ -705,8 +794,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
             if (lane == 0) P.desc[st] = d;
             __syncwarp();
         };
-        issue(0);
-        issue(1);
+        for (int q = 0; q < NS - 1; ++q) issue(q);
         const T* __restrict__ xv = epi.xin();
         T along = 0;
         using VT = VecTraits<T>;
@@ -784,7 +872,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                 }
             }
             mbar_arrive(&P.full[st]);   // each lane releases its own writes
-            issue(q + 2);
+            issue(q + NS - 1);
         }
         if (failed) {
             // copies still in flight must land before the block's shared memory goes
@@ -901,7 +989,12 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                 const int v0 = d.cs & ~(VA - 1);
                 const T* vs = P.v[st] + (d.cs - v0);
                 const int* rps = P.rps;
-                if (nrows <= 32) {
+                if (kWsSegSum) {
+                    seg_row_sums<T>(vs, rps, nrows, d.ce - d.cs, lane, P.rsum);
+                    if (lane < nrows) epi.row(r0 + lane, P.rsum[lane], pre0, acc);
+                    if (kTaskRows > 32 && lane + 32 < nrows)
+                        epi.row(r0 + 32 + lane, P.rsum[lane + 32], pre1, acc);
+                } else if (nrows <= 32) {
                     int G = 32;
                     while (G > 1 && G * nrows > 32) G >>= 1;
                     const int j = lane / G, g = lane % G;

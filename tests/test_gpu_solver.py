@@ -130,17 +130,29 @@ def test_fp64_adaptive_iterates_track_oracle(L, oracle_mod, name, iters):
     _check_trace(tr, tro)
 
 
+def _replay(oracle_mod, lp, rows, checks, y0=None):
+    x0 = None if y0 is None else oracle_mod.start_point(lp)[0]
+    return oracle_mod.solve_logged(lp, tol=1e-13, max_iters=1000, trace_cap=4096, replay=rows,
+                                   replay_checks=checks, x0=x0, y0=y0)
+
+
 @pytest.mark.parametrize("name", ["lp200x400", "ragged", "shuffled", "powerlaw"])
 def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
-    """Parity of the adaptive path (Algorithm 5) over 1000 iterations by replay:
-    the oracle takes the GPU run's discrete decisions (step sizes and accept /
+    """Parity of the adaptive path (Algorithm 5) over 1000 iterations by replay.
+
+    The oracle takes the GPU run's discrete decisions (step sizes and accept /
     reject outcomes from its attempt log, restart and candidate choices from its
-    trace) and computes everything else itself.  Then its iterates track the
-    GPU's to 1e-10; its own Algorithm 5 quantities (eta_bar, eta') agree with the
-    GPU's within what that iterate agreement allows; and every GPU decision is
-    the oracle's own, except where the oracle's quantities tie at that level
-    (a restart criterion, a candidate comparison or eta <= eta_bar decided by
-    less than the tolerance)."""
+    trace) and computes everything else itself.  A replayed schedule can still
+    amplify rounding differences where it accepts steps beyond 1/||K~||: the
+    oracle replaying the same schedule from a start moved by 1e-13 (about the
+    rounding a 1000-step run accumulates) departs from its own replay, on the
+    ragged and power-law LPs by more than 1e-6 in an attempt's terms after a
+    few hundred attempts.  Up to that onset of the oracle's own divergence
+    every quantity the GPU reports agrees with the oracle's replay within the
+    rounding level (derived below) plus ten times the gap between the oracle's
+    two replays, and every GPU decision is the oracle's own except where the
+    oracle's quantities tie at that level.  Where no onset occurs within the
+    1000 iterations, the final iterates agree to 1e-10 as well."""
     lp = PROBS[name]
     prob = L.Problem(lp)
     x, y, info, tr = prob.solve(tol=1e-13, max_iters=1000, trace_cap=4096, attempt_cap=5000)
@@ -148,62 +160,79 @@ def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
     assert info["attempt_len"] == info["attempts"] == len(log) >= 1000
     rows = np.array([[a[f] for f in L.ATTEMPT_FIELDS] for a in log])
     checks = np.array([[t["restart"], t["cand_is_avg"]] for t in tr])
-    xo, yo, io, tro, att = oracle_mod.solve_logged(lp, tol=1e-13, max_iters=1000,
-                                                   trace_cap=4096, replay=rows,
-                                                   replay_checks=checks)
-    assert io["iters"] == info["iters"] == 1000 and io["attempts"] == info["attempts"]
-    eps_it = 1e-10
-    assert rel(x, xo) <= eps_it, rel(x, xo)
-    assert rel(y, yo) <= eps_it, rel(y, yo)
-    # Tolerances from the iterate agreement: the terms of an attempt are
-    # differences of iterates (||dx||^2, ||dy||^2) and dy^T K dx; with iterates
-    # agreeing to eps_it ||z|| (z the scaled iterate), dz agrees to about
-    # eps_it ||z|| absolute and the interaction to eps_it ||z|| ||K~|| ||dz||, so
-    # eta_bar (a ratio of them) agrees to tol_terms below.  KKT values are
-    # residual norms of the iterates: relative agreement eps_it ||K~|| ||z|| / KKT
-    # (floored at 1e-6, the summation-order level of the gap term's cancellation).
+    xo, yo, io, tro, att = _replay(oracle_mod, lp, rows, checks)
+    y0p = 1e-13 * np.random.default_rng(1).normal(size=lp.m)
+    xp, yp, ip, trp, attp = _replay(oracle_mod, lp, rows, checks, y0=y0p)
+    assert io["iters"] == info["iters"] == ip["iters"] == 1000
+    assert io["attempts"] == info["attempts"] == ip["attempts"]
+    assert len(tr) == len(tro) == len(trp)
+    # onset of the oracle's own divergence under the replayed schedule
+    def gap(o, p, f):
+        return abs(p[f] - o[f]) / max(abs(o[f]), 1e-300)
+    onset = next((i for i, (o, p) in enumerate(zip(att, attp))
+                  if max(gap(o, p, "eta_bar"), gap(o, p, "dx2"), gap(o, p, "dy2")) > 1e-6),
+                 len(att))
+    assert onset >= 100, onset
+    if onset == len(att):
+        assert rel(x, xo) <= 1e-10, rel(x, xo)
+        assert rel(y, yo) <= 1e-10, rel(y, yo)
+    band = lambda o, p: 10.0 * abs(p - o)
+    # rounding-level tolerances: the terms of an attempt are differences of
+    # iterates (||dx||^2, ||dy||^2) and dy^T K dx; with iterates agreeing to
+    # eps ||z||, eta_bar (a ratio of them) agrees to tol_terms below; KKT values
+    # are residual norms of the iterates (relative eps ||K~|| ||z|| / KKT,
+    # floored at 1e-6, the summation-order level of the gap's cancellation)
+    eps = 1e-13
     _, R, Cs, _ = oracle_mod.ruiz(lp)
     znorm = np.sqrt(np.sum((xo / Cs) ** 2) + np.sum((yo / R) ** 2))
     nk = info["norm_K"]
-    decided_by_tie = 0
-    assert len(tr) == len(tro)
-    for a, b in zip(tr, tro):
+    tied = 0
+    last_attempt = log[onset - 1]["k"] if onset < len(log) else np.inf
+    for a, b, c in zip(tr, tro, trp):
         for f in ("k", "attempts", "restart", "cand_is_avg"):
             assert a[f] == b[f], (f, a, b)
-        assert a["omega"] == pytest.approx(b["omega"], rel=1e-8), (a, b)
-        tol_kkt = lambda v: max(1e-6, 4 * eps_it * nk * znorm / max(abs(v), 1e-300))
-        for f in ("kkt_cur", "kkt_cand"):
-            assert a[f] == pytest.approx(b[f], rel=tol_kkt(b[f])), (f, a[f], b[f])
-        for f in ("rel_gap", "rel_pres", "rel_dres"):
-            assert a[f] == pytest.approx(b[f], rel=1e-6, abs=1e-10), (f, a[f], b[f])
+        if a["k"] > last_attempt:
+            break
+        assert abs(a["omega"] - b["omega"]) <= 1e-10 * b["omega"] + band(b["omega"], c["omega"])
+        for f in ("kkt_cur", "kkt_cand", "rel_gap", "rel_pres", "rel_dres"):
+            t = max(1e-6 * abs(b[f]), 4 * eps * nk * znorm, 1e-12) + band(b[f], c[f])
+            assert abs(a[f] - b[f]) <= t, (f, a[f], b[f], c[f])
         # the GPU's decisions against the oracle's own
         if b["own_cand_is_avg"] != b["cand_is_avg"]:
-            assert abs(b["kkt_cur"] - b["kkt_avg"]) <= tol_kkt(b["kkt_cur"]) * b["kkt_cur"], (a, b)
-            decided_by_tie += 1
+            t = (1e-6 * b["kkt_cur"] + band(b["kkt_cur"], c["kkt_cur"])
+                 + band(b["kkt_avg"], c["kkt_avg"]))
+            assert abs(b["kkt_cur"] - b["kkt_avg"]) <= t, (a, b)
+            tied += 1
         if b["own_restart"] != b["restart"]:
-            c, t = b["kkt_cand"], tol_kkt(b["kkt_cand"]) * b["kkt_cand"]
-            near = (abs(c - oracle_mod.DEFAULTS["beta_sufficient"] * b["kkt_anchor"]) <= t
-                    or abs(c - oracle_mod.DEFAULTS["beta_necessary"] * b["kkt_anchor"]) <= t
-                    or abs(c - b["kkt_prev"]) <= t)
+            cnd = b["kkt_cand"]
+            t = 1e-6 * cnd + band(cnd, c["kkt_cand"]) + band(b["kkt_anchor"], c["kkt_anchor"])
+            d = oracle_mod.DEFAULTS
+            near = (abs(cnd - d["beta_sufficient"] * b["kkt_anchor"]) <= t
+                    or abs(cnd - d["beta_necessary"] * b["kkt_anchor"]) <= t
+                    or abs(cnd - b["kkt_prev"]) <= t + band(b["kkt_prev"], c["kkt_prev"]))
             assert near, (a, b)
-            decided_by_tie += 1
+            tied += 1
     rejected = 0
-    for g, o in zip(log, att):
+    for g, o, p in list(zip(log, att, attp))[:onset]:
         assert g["k"] == o["k"] and g["eta"] == o["eta"]
         dz = np.sqrt(o["dx2"] + o["dy2"])
-        tol_terms = max(1e-8, 8 * eps_it * znorm * (1.0 / max(dz, 1e-300)
-                                                    + nk * dz / max(abs(o["inter"]), 1e-300)))
+        tol_terms = max(1e-12, 8 * eps * znorm * (1.0 / max(dz, 1e-300)
+                                                  + nk * dz / max(abs(o["inter"]), 1e-300)))
+        eb = tol_terms * o["eta_bar"] + band(o["eta_bar"], p["eta_bar"])
         # where eta_bar sits well above eta, eta' = (1 + (k+1)^-0.6) eta does not
         # depend on it and the step is accepted either way: compared loosely there
-        tol_eb = max(tol_terms, 1e-5) if o["eta_bar"] >= 2 * g["eta"] else tol_terms
-        assert g["eta_bar"] == pytest.approx(o["eta_bar"], rel=tol_eb), (g, o, tol_eb)
-        if abs(g["eta"] - o["eta_bar"]) > tol_eb * o["eta_bar"]:
+        if o["eta_bar"] >= 2 * g["eta"]:
+            eb = max(eb, 1e-5 * o["eta_bar"])
+        assert abs(g["eta_bar"] - o["eta_bar"]) <= eb, (g, o, p)
+        if abs(g["eta"] - o["eta_bar"]) > eb:
             assert bool(g["accept"]) == (g["eta"] <= o["eta_bar"]), (g, o)
         elif bool(g["accept"]) != (g["eta"] <= o["eta_bar"]):
-            decided_by_tie += 1
-        assert g["eta_next"] == pytest.approx(o["eta_next"], rel=tol_terms), (g, o)
+            tied += 1
+        en = tol_terms * o["eta_next"] + band(o["eta_next"], p["eta_next"])
+        assert abs(g["eta_next"] - o["eta_next"]) <= en, (g, o, p)
         rejected += int(not g["accept"])
-    print(name, "rejected attempts", rejected, "decisions taken at a tie", decided_by_tie)
+    print(name, "onset", onset, "of", len(att), "rejected attempts", rejected,
+          "decisions taken at a tie", tied)
 
 
 # ---------------------------------------------------------------- to tolerance
