@@ -153,6 +153,10 @@ struct SplitRows {
     int* cnt = nullptr;              // [n] tickets taken in the current launch (0 between launches)
     void* slots = nullptr;           // [npieces] piece sums (the launch's T)
     int n = 0;                       // split rows
+    // Also carried per launch: short tasks' rows summed by seg_row_sums (equal
+    // shares per lane) instead of one group of lanes per row; the host sets it
+    // for FP64 schedules whose lane groups would be unbalanced.
+    int segsum = 0;
 };
 
 // State and scaled data of one precision T (double or float).

@@ -182,6 +182,33 @@ SplitPlan split_long_rows(std::vector<int32_t>& rows, std::vector<int64_t>& nz, 
     return plan;
 }
 
+double lane_group_imbalance(const int64_t* rp, const std::vector<int32_t>& rows,
+                            const std::vector<int64_t>& nz, int cap)
+{
+    double busiest = 0.0, equal = 0.0;
+    for (size_t t = 0; t + 1 < rows.size(); ++t) {
+        const int64_t len = nz[t + 1] - nz[t];
+        const int r0 = rows[t], nr = rows[t + 1] - rows[t];
+        if (len <= 0 || len > cap || nr <= 0) continue;   // long rows and pieces: no lane groups
+        int64_t steps = 0;
+        if (nr <= 32) {
+            int G = 32;
+            while (G > 1 && G * nr > 32) G >>= 1;
+            for (int j = 0; j < nr; ++j)
+                steps = std::max<int64_t>(steps, (rp[r0 + j + 1] - rp[r0 + j] + G - 1) / G);
+        } else {
+            for (int j = 0; j < 32; ++j) {
+                int64_t s = rp[r0 + j + 1] - rp[r0 + j];
+                if (j + 32 < nr) s += rp[r0 + j + 33] - rp[r0 + j + 32];
+                steps = std::max(steps, s);
+            }
+        }
+        busiest += (double)steps;
+        equal += (double)((len + 31) / 32);
+    }
+    return equal > 0.0 ? busiest / equal : 1.0;
+}
+
 // ------------------------------------------------------------------ kernels
 
 __global__ void k_validate(int64_t m, int64_t n, int64_t nnz, const int64_t* rp,
@@ -801,6 +828,17 @@ lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
     E.bnzK = E.bnzT = nullptr;
     LP_TRY(upload_split<T>(h, spK, E.splitK));
     LP_TRY(upload_split<T>(h, spT, E.splitT));
+    // FP64 row sums: GB300's FP64 pipe takes a whole warp instruction however
+    // few lanes are active, so unbalanced lane groups waste it (on the 1M x 2M
+    // power-law LP the pipe was 81 % busy on the K side, where the busiest lane
+    // of a task does 6.1 times an equal share); equal shares there (K side
+    // 304 -> 269 us), lane groups where they are balanced (K^T side: 197 us
+    // against 249 us with equal shares).  FP32 keeps lane groups (equal shares
+    // measured slower on both sides).
+    if (sizeof(T) == 8) {
+        E.splitK.segsum = lane_group_imbalance(h->h_rp.data(), bk, nk, sK.cap) > 3.0 ? 1 : 0;
+        E.splitT.segsum = lane_group_imbalance(h->h_trp.data(), bt, nt, sT.cap) > 3.0 ? 1 : 0;
+    }
     // a piece carries its slot + 1 in the high 32 bits of its first nonzero
     for (size_t t = 0; t < spK.task_piece.size(); ++t)
         if (spK.task_piece[t] >= 0) nk[t] |= (int64_t)(spK.task_piece[t] + 1) << 32;

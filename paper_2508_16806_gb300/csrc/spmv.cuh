@@ -354,7 +354,8 @@ constexpr int kWsPairs = kTaskWarps / 2;
 constexpr int kWsStages = PDHG_WS_STAGES;
 static_assert(kWsStages >= 3, "the consumer reads the descriptor one chunk ahead");
 // Short tasks' row sums by the segmented form (seg_row_sums: equal shares per
-// lane) instead of one group of lanes per row.
+// lane) instead of one group of lanes per row, for every schedule (otherwise
+// only where SplitRows::segsum asks for it).
 #ifndef PDHG_WS_SEGSUM
 #define PDHG_WS_SEGSUM 0
 #endif
@@ -989,7 +990,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                 const int v0 = d.cs & ~(VA - 1);
                 const T* vs = P.v[st] + (d.cs - v0);
                 const int* rps = P.rps;
-                if (kWsSegSum) {
+                if (kWsSegSum || sp.segsum) {
                     seg_row_sums<T>(vs, rps, nrows, d.ce - d.cs, lane, P.rsum);
                     if (lane < nrows) epi.row(r0 + lane, P.rsum[lane], pre0, acc);
                     if (kTaskRows > 32 && lane + 32 < nrows)
@@ -1210,6 +1211,15 @@ struct SplitPlan {
 // Only the warp-specialised SpMV takes pieces: without it nothing is cut.
 SplitPlan split_long_rows(std::vector<int32_t>& rows, std::vector<int64_t>& nz, int cap,
                           int workers);
+
+// Imbalance of the one-group-of-lanes-per-row sums of a schedule's short tasks:
+// the steps of each task's busiest lane (a row of length L summed by G lanes
+// takes ceil(L / G) steps; G the largest power of two with G rows <= 32; above
+// 32 rows a lane sums two rows), added over the tasks, divided by the steps of
+// equal shares (ceil(nonzeros / 32) per task).  rp: host row pointers; rows,
+// nz: task bounds.
+double lane_group_imbalance(const int64_t* rp, const std::vector<int32_t>& rows,
+                            const std::vector<int64_t>& nz, int cap);
 
 // Schedule autotuner (tune.cu).  Candidates: cap in {CAPW, CAPW / 2} nonzeros
 // and max_rows in {kTaskRows, 32, 16} rows per task.  build(cap, max_rows)

@@ -1,6 +1,7 @@
 """Batched restarted PDHG (lp_batch_create / lp_batch_solve / lp_solve_batch):
 every LP of a batch follows the same per-LP method as lp_solve, checked against
-single solves and against the FP64 oracle's KKT evaluation."""
+single solves, against the FP64 oracle's own runs and against its KKT
+evaluation."""
 import ctypes as C
 
 import numpy as np
@@ -50,6 +51,24 @@ def test_batch_tracks_single_solves_fixed_step(L, iters):
         assert info["restarts"] == si["restarts"]
         assert info["norm_K"] == pytest.approx(si["norm_K"], rel=1e-12)
         assert rel(x, xs) <= 1e-10 and rel(y, ys) <= 1e-10
+    batch.close()
+
+
+@pytest.mark.parametrize("iters", [64, 1000])
+def test_batch_tracks_oracle_fixed_step(L, oracle_mod, iters):
+    """Fixed-step restarted PDHG: each LP of the batch matches the FP64 oracle's
+    own run directly (iterates to 1e-10 relative, same restarts, the same
+    Algorithm 2 norm to 1e-12)."""
+    batch = L.Batch(LPS)
+    out = batch.solve(tol=1e-13, max_iters=iters, adaptive_step=0)
+    for lp, (x, y, info) in zip(LPS, out):
+        xo, yo, io, _ = oracle_mod.solve(lp, tol=1e-13, max_iters=iters, adaptive_step=0,
+                                         trace_cap=4)
+        assert info["iters"] == io["iters"] == iters
+        assert info["restarts"] == io["restarts"]
+        assert info["norm_K"] == pytest.approx(io["norm_K"], rel=1e-12)
+        assert rel(x, xo) <= 1e-10, rel(x, xo)
+        assert rel(y, yo) <= 1e-10, rel(y, yo)
     batch.close()
 
 
