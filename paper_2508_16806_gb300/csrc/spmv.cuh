@@ -840,30 +840,42 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                         VT::unpacki(*reinterpret_cast<const typename VT::I*>(ibuf + off), ii[k]);
                     }
                 }
+                if (d.flags & kWsLong) {
+                    // a long row's lane sums take the products by fused multiply-adds
+                    // (one FP64 instruction per nonzero instead of two)
 #pragma unroll
-                for (int k = 0; k < UG; ++k) {
-                    const int off = (k * 32 + lane) * VEC;
+                    for (int k = 0; k < UG; ++k) {
+                        const int off = (k * 32 + lane) * VEC;
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        const int p = off + v;
-                        if (p >= vo && p < lim) {
-                            if constexpr (L1G) vv[k][v] *= __ldg(xv + ii[k][v]);
-                            else vv[k][v] *= ld_gather(xv + ii[k][v]);
-                        } else {
-                            vv[k][v] = T(0);
+                        for (int v = 0; v < VEC; ++v) {
+                            const int p = off + v;
+                            if (p >= vo && p < lim) {
+                                T g;
+                                if constexpr (L1G) g = __ldg(xv + ii[k][v]);
+                                else g = ld_gather(xv + ii[k][v]);
+                                along = fma(vv[k][v], g, along);
+                            }
                         }
                     }
-                }
-                if (d.flags & kWsLong) {
-#pragma unroll
-                    for (int k = 0; k < UG; ++k)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) along += vv[k][v];
                     if (d.flags & kWsLast) {
                         __syncwarp();   // every lane has read its values
                         vbuf[lane] = along;
                     }
                 } else {
+#pragma unroll
+                    for (int k = 0; k < UG; ++k) {
+                        const int off = (k * 32 + lane) * VEC;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const int p = off + v;
+                            if (p >= vo && p < lim) {
+                                if constexpr (L1G) vv[k][v] *= __ldg(xv + ii[k][v]);
+                                else vv[k][v] *= ld_gather(xv + ii[k][v]);
+                            } else {
+                                vv[k][v] = T(0);
+                            }
+                        }
+                    }
 #pragma unroll
                     for (int k = 0; k < UG; ++k) {
                         const int off = (k * 32 + lane) * VEC;
