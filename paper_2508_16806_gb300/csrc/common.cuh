@@ -139,7 +139,8 @@ struct SchedParams {
 // of a schedule whose lists would otherwise be unbalanced (few, long rows, as
 // the columns of K in a dispatch-shaped LP) is cut on the host into pieces of
 // whole chunks; each piece is a task of its own, marked by its slot g + 1 in
-// the high 32 bits of its task_nz entry (nonzero offsets fit in the low 31).
+// bits 32-61 of its task_nz entry (nonzero offsets fit in the low 31; bit 62
+// marks a short task whose rows are summed by equal lane shares, kSegBit).
 // The warp that finishes a piece stores its sum in slots[g] and takes a ticket
 // on the row's counter; the warp that takes the last ticket adds the row's
 // slots in piece order, so the result does not depend on which warp that is,
@@ -147,16 +148,15 @@ struct SchedParams {
 // The epilogue's reductions of that row go to a fixed place too: Epi::split_acc
 // stores them in the split's own partial slot (after the block partials),
 // which the consumer of the partials sums with them in a fixed order.
+constexpr int64_t kSegBit = (int64_t)1 << 62;
+constexpr int64_t kPieceMask = ((int64_t)1 << 30) - 1;   // of task_nz >> 32
+
 struct SplitRows {
     const int32_t* pspl = nullptr;   // [npieces] split of each piece slot
     const int32_t* info = nullptr;   // [n][2] first piece slot, number of pieces
     int* cnt = nullptr;              // [n] tickets taken in the current launch (0 between launches)
     void* slots = nullptr;           // [npieces] piece sums (the launch's T)
     int n = 0;                       // split rows
-    // Also carried per launch: short tasks' rows summed by seg_row_sums (equal
-    // shares per lane) instead of one group of lanes per row; the host sets it
-    // for FP64 schedules whose lane groups would be unbalanced.
-    int segsum = 0;
 };
 
 // State and scaled data of one precision T (double or float).

@@ -107,6 +107,15 @@ void assign_tasks(const std::vector<int64_t>& task_nz, int cap, int warps,
     for (int t = 0; t < nt; ++t) perm[(size_t)cur[(size_t)owner[(size_t)t]]++] = t;
 }
 
+// Busiest-lane steps above which a short task's rows are summed by equal lane
+// shares (seg_row_sums) rather than by one group of lanes per row.
+#ifndef PDHG_SEG_STEPS_F32
+#define PDHG_SEG_STEPS_F32 (1 << 30)   // FP32: lane groups only (equal shares measured no faster)
+#endif
+#ifndef PDHG_SEG_STEPS_F64
+#define PDHG_SEG_STEPS_F64 8
+#endif
+
 // Longest worker list (in chunks) of the longest-first assignment of
 // assign_tasks, without building the lists.
 static int64_t lpt_makespan(const std::vector<int64_t>& cost, int workers)
@@ -182,31 +191,35 @@ SplitPlan split_long_rows(std::vector<int32_t>& rows, std::vector<int64_t>& nz, 
     return plan;
 }
 
-double lane_group_imbalance(const int64_t* rp, const std::vector<int32_t>& rows,
-                            const std::vector<int64_t>& nz, int cap)
+int64_t lane_group_steps(const int64_t* rp, int r0, int nr)
 {
-    double busiest = 0.0, equal = 0.0;
+    int64_t steps = 0;
+    if (nr <= 32) {
+        int G = 32;
+        while (G > 1 && G * nr > 32) G >>= 1;
+        for (int j = 0; j < nr; ++j)
+            steps = std::max<int64_t>(steps, (rp[r0 + j + 1] - rp[r0 + j] + G - 1) / G);
+    } else {
+        for (int j = 0; j < 32; ++j) {
+            int64_t t = rp[r0 + j + 1] - rp[r0 + j];
+            if (j + 32 < nr) t += rp[r0 + j + 33] - rp[r0 + j + 32];
+            steps = std::max(steps, t);
+        }
+    }
+    return steps;
+}
+
+std::vector<char> seg_tasks(const int64_t* rp, const std::vector<int32_t>& rows,
+                            const std::vector<int64_t>& nz, int cap, int max_steps)
+{
+    std::vector<char> seg(rows.size() > 0 ? rows.size() - 1 : 0, 0);
     for (size_t t = 0; t + 1 < rows.size(); ++t) {
         const int64_t len = nz[t + 1] - nz[t];
-        const int r0 = rows[t], nr = rows[t + 1] - rows[t];
+        const int nr = rows[t + 1] - rows[t];
         if (len <= 0 || len > cap || nr <= 0) continue;   // long rows and pieces: no lane groups
-        int64_t steps = 0;
-        if (nr <= 32) {
-            int G = 32;
-            while (G > 1 && G * nr > 32) G >>= 1;
-            for (int j = 0; j < nr; ++j)
-                steps = std::max<int64_t>(steps, (rp[r0 + j + 1] - rp[r0 + j] + G - 1) / G);
-        } else {
-            for (int j = 0; j < 32; ++j) {
-                int64_t s = rp[r0 + j + 1] - rp[r0 + j];
-                if (j + 32 < nr) s += rp[r0 + j + 33] - rp[r0 + j + 32];
-                steps = std::max(steps, s);
-            }
-        }
-        busiest += (double)steps;
-        equal += (double)((len + 31) / 32);
+        seg[t] = lane_group_steps(rp, rows[t], nr) > max_steps ? 1 : 0;
     }
-    return equal > 0.0 ? busiest / equal : 1.0;
+    return seg;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -828,17 +841,21 @@ lp_status engine_schedule(Handle* h, SchedParams sK, SchedParams sT)
     E.bnzK = E.bnzT = nullptr;
     LP_TRY(upload_split<T>(h, spK, E.splitK));
     LP_TRY(upload_split<T>(h, spT, E.splitT));
-    // FP64 row sums: GB300's FP64 pipe takes a whole warp instruction however
-    // few lanes are active, so unbalanced lane groups waste it (on the 1M x 2M
-    // power-law LP the pipe was 81 % busy on the K side, where the busiest lane
-    // of a task does 6.1 times an equal share); equal shares there (K side
-    // 304 -> 269 us), lane groups where they are balanced (K^T side: 197 us
-    // against 249 us with equal shares).  FP32 keeps lane groups (equal shares
-    // measured slower on both sides).
-    if (sizeof(T) == 8) {
-        E.splitK.segsum = lane_group_imbalance(h->h_rp.data(), bk, nk, sK.cap) > 3.0 ? 1 : 0;
-        E.splitT.segsum = lane_group_imbalance(h->h_trp.data(), bt, nt, sT.cap) > 3.0 ? 1 : 0;
-    }
+    // Row sums of each short task: one group of lanes per row where that is
+    // balanced, equal lane shares (seg_row_sums, with its fixed cost of a
+    // search and a five-round scan) where the busiest lane would take more than
+    // PDHG_SEG_STEPS_* steps.  FP64 only: GB300's FP64 pipe takes a whole warp
+    // instruction however few lanes are active (on the 1M x 2M power-law LP it
+    // was 81 % busy on the K side, where the busiest lane of a task does 6.1
+    // times an equal share; above 8 steps: K side 284 -> 249 us, K^T side
+    // 202 -> 193 us).  In FP32 no threshold (16 to 48) was faster than none.
+    const int seg_steps = sizeof(T) == 8 ? PDHG_SEG_STEPS_F64 : PDHG_SEG_STEPS_F32;
+    const std::vector<char> segK = seg_tasks(h->h_rp.data(), bk, nk, sK.cap, seg_steps);
+    const std::vector<char> segT = seg_tasks(h->h_trp.data(), bt, nt, sT.cap, seg_steps);
+    for (size_t t = 0; t < segK.size(); ++t)
+        if (segK[t]) nk[t] |= kSegBit;
+    for (size_t t = 0; t < segT.size(); ++t)
+        if (segT[t]) nt[t] |= kSegBit;
     // a piece carries its slot + 1 in the high 32 bits of its first nonzero
     for (size_t t = 0; t < spK.task_piece.size(); ++t)
         if (spK.task_piece[t] >= 0) nk[t] |= (int64_t)(spK.task_piece[t] + 1) << 32;

@@ -354,8 +354,8 @@ constexpr int kWsPairs = kTaskWarps / 2;
 constexpr int kWsStages = PDHG_WS_STAGES;
 static_assert(kWsStages >= 3, "the consumer reads the descriptor one chunk ahead");
 // Short tasks' row sums by the segmented form (seg_row_sums: equal shares per
-// lane) instead of one group of lanes per row, for every schedule (otherwise
-// only where SplitRows::segsum asks for it).
+// lane) instead of one group of lanes per row, for every task (otherwise only
+// for the tasks the host marks with kSegBit).
 #ifndef PDHG_WS_SEGSUM
 #define PDHG_WS_SEGSUM 0
 #endif
@@ -378,7 +378,7 @@ struct StatelessTasks<E, std::void_t<decltype(E::kStatelessTasks)>>
 struct WsDesc {
     int task, cs, ce, flags, r0, nrows, piece;
 };
-constexpr int kWsFirst = 1, kWsLast = 2, kWsLong = 4;
+constexpr int kWsFirst = 1, kWsLast = 2, kWsLong = 4, kWsSeg = 8;
 
 // Epilogues whose reductions take split rows: they provide
 // split_acc(int s, const Acc&) and a member nsplit (the kernel sets it to
@@ -732,12 +732,14 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
         auto task_at = [&](int p) { return p < pend ? perm[p] : ntasks; };
         int ipos = next_live(pbeg);
         int itask = task_at(ipos);
-        int is = 0, ie = 0, ics = 0, ir0 = 0, inr = 0, ipc = -1;
-        // bounds, rows and piece slot of task itask (a piece has no rows of its own)
+        int is = 0, ie = 0, ics = 0, ir0 = 0, inr = 0, ipc = -1, iseg = 0;
+        // bounds, rows, piece slot and row-sum form of task itask (a piece has
+        // no rows of its own)
         auto load_task = [&]() {
             const int64_t tz = task_nz[itask];
             is = (int)(uint32_t)tz;
-            ipc = (int)(tz >> 32) - 1;
+            ipc = (int)((tz >> 32) & kPieceMask) - 1;
+            iseg = (tz & kSegBit) ? kWsSeg : 0;
             ie = (int)(uint32_t)task_nz[itask + 1];
             ir0 = task_row[itask];
             inr = ipc < 0 ? task_row[itask + 1] - ir0 : 0;
@@ -770,7 +772,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                 d.cs = cs;
                 d.ce = ce;
                 d.flags = (cs == is ? kWsFirst : 0) | (ce == ie ? kWsLast : 0) |
-                          (ie - is > CAPW || ipc >= 0 ? kWsLong : 0);
+                          (ie - is > CAPW || ipc >= 0 ? kWsLong : 0) | iseg;
                 d.r0 = ir0;
                 d.nrows = inr;
                 d.piece = ipc;
@@ -1002,7 +1004,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                 const int v0 = d.cs & ~(VA - 1);
                 const T* vs = P.v[st] + (d.cs - v0);
                 const int* rps = P.rps;
-                if (kWsSegSum || sp.segsum) {
+                if (kWsSegSum || (d.flags & kWsSeg)) {
                     seg_row_sums<T>(vs, rps, nrows, d.ce - d.cs, lane, P.rsum);
                     if (lane < nrows) epi.row(r0 + lane, P.rsum[lane], pre0, acc);
                     if (kTaskRows > 32 && lane + 32 < nrows)
@@ -1224,14 +1226,18 @@ struct SplitPlan {
 SplitPlan split_long_rows(std::vector<int32_t>& rows, std::vector<int64_t>& nz, int cap,
                           int workers);
 
-// Imbalance of the one-group-of-lanes-per-row sums of a schedule's short tasks:
-// the steps of each task's busiest lane (a row of length L summed by G lanes
-// takes ceil(L / G) steps; G the largest power of two with G rows <= 32; above
-// 32 rows a lane sums two rows), added over the tasks, divided by the steps of
-// equal shares (ceil(nonzeros / 32) per task).  rp: host row pointers; rows,
-// nz: task bounds.
-double lane_group_imbalance(const int64_t* rp, const std::vector<int32_t>& rows,
-                            const std::vector<int64_t>& nz, int cap);
+// Steps of the busiest lane when a short task's rows [r0, r0 + nr) are summed
+// by one group of lanes per row: a row of length L summed by G lanes takes
+// ceil(L / G) steps (G the largest power of two with G nr <= 32); above 32 rows
+// a lane sums two rows.  rp: host row pointers.
+int64_t lane_group_steps(const int64_t* rp, int r0, int nr);
+
+// The short tasks of a schedule (rows, nz: task bounds; tasks of at most cap
+// nonzeros with rows of their own) whose busiest lane would take more than
+// max_steps steps: their rows are summed by equal lane shares instead
+// (seg_row_sums).  Returns one flag per task.
+std::vector<char> seg_tasks(const int64_t* rp, const std::vector<int32_t>& rows,
+                            const std::vector<int64_t>& nz, int cap, int max_steps);
 
 // Schedule autotuner (tune.cu).  Candidates: cap in {CAPW, CAPW / 2} nonzeros
 // and max_rows in {kTaskRows, 32, 16} rows per task.  build(cap, max_rows)

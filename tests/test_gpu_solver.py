@@ -144,10 +144,10 @@ def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
     reject outcomes from its attempt log, restart and candidate choices from its
     trace) and computes everything else itself.  A replayed schedule can still
     amplify rounding differences where it accepts steps beyond 1/||K~||: the
-    oracle replaying the same schedule from a start moved by 1e-13 (about the
-    rounding a 1000-step run accumulates) departs from its own replay, on the
-    ragged and power-law LPs by more than 1e-6 in an attempt's terms after a
-    few hundred attempts.  Up to that onset of the oracle's own divergence
+    oracle replaying the same schedule from a start moved by 1e-12 (the order of
+    the rounding differences that different summation orders accumulate over a
+    few hundred steps) departs from its own replay, on the ragged and power-law
+    LPs by more than 1e-6 in an attempt's terms after 120-190 attempts.  Up to that onset of the oracle's own divergence
     every quantity the GPU reports agrees with the oracle's replay within the
     rounding level (derived below) plus ten times the gap between the oracle's
     two replays, and every GPU decision is the oracle's own except where the
@@ -161,7 +161,7 @@ def test_fp64_adaptive_replay_1000_iterations(L, oracle_mod, name):
     rows = np.array([[a[f] for f in L.ATTEMPT_FIELDS] for a in log])
     checks = np.array([[t["restart"], t["cand_is_avg"]] for t in tr])
     xo, yo, io, tro, att = _replay(oracle_mod, lp, rows, checks)
-    y0p = 1e-13 * np.random.default_rng(1).normal(size=lp.m)
+    y0p = 1e-12 * np.random.default_rng(1).normal(size=lp.m)
     xp, yp, ip, trp, attp = _replay(oracle_mod, lp, rows, checks, y0=y0p)
     assert io["iters"] == info["iters"] == ip["iters"] == 1000
     assert io["attempts"] == info["attempts"] == ip["attempts"]
