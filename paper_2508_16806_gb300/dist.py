@@ -133,3 +133,19 @@ def step_bytes_per_rank(m: int, n: int, world: int, value_bytes: int = 4) -> dic
     cw = -(-n // world)
     gather = (world - 1) * (rw + cw) * value_bytes
     return {"allgather_recv": gather, "decision_allreduce": 3 * 8, "check_allreduce": 29 * 8}
+
+
+def partition_by_nnz(nnz, world: int) -> list:
+    """Independent LPs shared among `world` ranks by their nonzeros: largest
+    first, each to the rank with the fewest nonzeros so far (ties: the lower
+    rank).  Returns each rank's LP indices in ascending order.  A pure function
+    of the sizes, so every rank computes the same shares without communication."""
+    nnz = np.asarray(nnz, dtype=np.int64)
+    order = sorted(range(nnz.shape[0]), key=lambda k: (-int(nnz[k]), k))
+    load = [0] * world
+    share = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda i: (load[i], i))
+        share[r].append(k)
+        load[r] += int(nnz[k])
+    return [sorted(s) for s in share]

@@ -283,21 +283,43 @@ def dispatch_lp(n_gen: int = 5000, n_base: int = 15000, n_cont: int = 40,
               name=f"dispatch{m}x{n_gen}")
 
 
-def batch_lps(count: int = 512, m_lo: int = 500, m_hi: int = 50_000,
-              k_lo: int = 5, k_hi: int = 20, seed: int = 20250819) -> list[LP]:
-    """``count`` independent planted LPs: m ~ log-uniform[m_lo, m_hi],
-    n = 2m, row lengths ~ U{k_lo..k_hi}; LP k uses seed ``seed + k``."""
-    out = []
+def _batch_draws(k: int, m_lo: int, m_hi: int, k_lo: int, k_hi: int, seed: int):
+    rng = np.random.default_rng(seed + k)
+    m = int(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi))))
+    lengths = rng.integers(k_lo, k_hi + 1, m)
+    return rng, m, lengths
+
+
+def batch_lp(k: int, m_lo: int = 500, m_hi: int = 50_000, k_lo: int = 5, k_hi: int = 20,
+             seed: int = 20250819) -> LP:
+    """LP k of the batch workload: m ~ log-uniform[m_lo, m_hi], n = 2m, row
+    lengths ~ U{k_lo..k_hi}, planted optimum; seed ``seed + k``."""
+    rng, m, lengths = _batch_draws(k, m_lo, m_hi, k_lo, k_hi, seed)
+    n = 2 * m
+    row_ptr, col_idx = lengths_pattern(m, n, lengths, rng)
+    vals = rng.standard_normal(int(row_ptr[-1]))
+    return plant(m, n, row_ptr, col_idx, vals, _sense_half(m), rng, name=f"batch{k}_{m}x{n}")
+
+
+def batch_nnz(count: int = 512, m_lo: int = 500, m_hi: int = 50_000, k_lo: int = 5,
+              k_hi: int = 20, seed: int = 20250819) -> np.ndarray:
+    """Nonzeros of LPs 0..count-1 of the batch workload before duplicate
+    columns are re-drawn (an upper bound within a few per mille), from their
+    first draws only: no LP is built."""
+    out = np.empty(count, dtype=np.int64)
     for k in range(count):
-        rng = np.random.default_rng(seed + k)
-        m = int(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi))))
-        n = 2 * m
-        lengths = rng.integers(k_lo, k_hi + 1, m)
-        row_ptr, col_idx = lengths_pattern(m, n, lengths, rng)
-        vals = rng.standard_normal(int(row_ptr[-1]))
-        out.append(plant(m, n, row_ptr, col_idx, vals, _sense_half(m), rng,
-                         name=f"batch{k}_{m}x{n}"))
+        _, m, lengths = _batch_draws(k, m_lo, m_hi, k_lo, k_hi, seed)
+        out[k] = int(np.minimum(lengths, 2 * m).sum())
     return out
+
+
+def batch_lps(count: int = 512, m_lo: int = 500, m_hi: int = 50_000,
+              k_lo: int = 5, k_hi: int = 20, seed: int = 20250819,
+              indices=None) -> list[LP]:
+    """``count`` independent planted LPs (``batch_lp``), or the LPs ``indices``
+    of that list."""
+    ks = range(count) if indices is None else indices
+    return [batch_lp(int(k), m_lo, m_hi, k_lo, k_hi, seed) for k in ks]
 
 
 def adjoint_lp(m: int = 100_000, n: int = 200_000, per_row: int = 20,

@@ -158,3 +158,28 @@ def test_exchange_volume():
     b = D.step_bytes_per_rank(1_000_000, 2_000_000, 8)
     # seven padded pieces of 125,000 + 250,000 FP32 values per attempt
     assert b["allgather_recv"] == 7 * (125_000 + 250_000) * 4
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_batch_shares_by_nnz(world):
+    """One list of independent LPs shared among ranks by nonzeros (the batch
+    workload's multi-rank form): every LP exactly once, each rank's load within
+    one LP of the mean, the same shares on every call."""
+    nnz = synth.batch_nnz(64 * world)
+    shares = D.partition_by_nnz(nnz, world)
+    assert sorted(k for s in shares for k in s) == list(range(64 * world))
+    loads = [int(nnz[s].sum()) if s else 0 for s in shares]
+    assert max(loads) - min(loads) <= int(nnz.max())
+    assert shares == D.partition_by_nnz(nnz, world)
+    assert all(s == sorted(s) for s in shares)
+
+
+def test_batch_lp_by_index_matches_list():
+    lps = synth.batch_lps(count=6)
+    some = synth.batch_lps(indices=[5, 2])
+    for a, b in zip(some, [lps[5], lps[2]]):
+        np.testing.assert_array_equal(a.col_idx, b.col_idx)
+        np.testing.assert_array_equal(a.vals, b.vals)
+    nnz = synth.batch_nnz(6)
+    for lp, est in zip(lps, nnz):
+        assert lp.nnz <= est <= lp.nnz * 1.01
