@@ -924,8 +924,9 @@ lp_status setup_engine(Handle* h, const lp_opts* o)
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     Engine<T>& E = engine_of<T>(h);
     if (!E.ready) {
-        LP_TRY(engine_schedule<T>(h, SchedParams{cap_w<T>(), kTaskRows},
-                                  SchedParams{cap_w<T>(), kTaskRows}));
+        // the K side gathers x (n entries), the K^T side y (m entries)
+        LP_TRY(engine_schedule<T>(h, SchedParams{spmv_cap<T>(n), kTaskRows},
+                                  SchedParams{spmv_cap<T>(m), kTaskRows}));
         LP_TRY(dev_alloc_n(h, &E.val, pad8(nnz)));
         LP_TRY(dev_alloc_n(h, &E.tval, pad8(nnz)));
         LP_CUDA_TRY(cudaMemsetAsync(E.val, 0, pad8(nnz) * sizeof(T), h->stream));

@@ -115,6 +115,21 @@ __host__ __device__ constexpr int cap_w()
                : 32 * VecTraits<T>::N * Unroll<T>::value - VecTraits<T>::N;
 }
 
+// The warp-specialised SpMV's chunk when its gathers hit L1 (a vector of at most
+// kL1GatherBytes): a gather costs little there and the chunk's fixed cost
+// (copy, hand-overs, row starts) dominates, so chunks take PDHG_SPMV_UNROLL_L1
+// 16-byte loads per lane (the 615,001 x 5,000 dispatch LP's K side, x 20 KB:
+// 160 -> 132 us with 3).  Schedules of such a side use this capacity.
+#ifndef PDHG_SPMV_UNROLL_L1
+#define PDHG_SPMV_UNROLL_L1 3
+#endif
+template <typename T, bool L1G>
+__host__ __device__ constexpr int cap_ws()
+{
+    return L1G && PDHG_SPMV_CAP <= 0 ? 32 * VecTraits<T>::N * PDHG_SPMV_UNROLL_L1 - VecTraits<T>::N
+                                      : cap_w<T>();
+}
+
 // v[p] + v[p + step] + ... over [p, pe).  In FP32 two partial sums keep two
 // shared-memory loads in flight (measured: K side 112 -> 106 us on the 1M x 2M
 // LP); in FP64 the single chain is faster (more registers per value).
@@ -388,10 +403,12 @@ struct HasSplitAcc : std::false_type {};
 template <class E>
 struct HasSplitAcc<E, std::void_t<decltype(&E::split_acc)>> : std::true_type {};
 
-template <typename T>
+template <typename T, bool L1G>
 struct alignas(16) PairStage {
-    static constexpr int VPAD = WarpStage<T>::VPAD;
-    static constexpr int IPAD = WarpStage<T>::IPAD;
+    static constexpr int CAPW = cap_ws<T, L1G>();
+    static constexpr int VA = 16 / (int)sizeof(T);
+    static constexpr int VPAD = (CAPW + 2 * (VA - 1) + VA - 1) / VA * VA;
+    static constexpr int IPAD = (CAPW + 6 + 3) / 4 * 4;
     T v[kWsStages][VPAD];          // values, then products (long row: lane sums)
     int i[kWsStages][IPAD];        // column indices
     uint64_t tma[kWsStages];       // bulk copy of the stage complete
@@ -401,14 +418,20 @@ struct alignas(16) PairStage {
     int rps[kTaskRows + 1];        // row starts of the consumer's short task
     T rsum[kTaskRows];             // its row sums (segmented form)
 };
-static_assert(sizeof(PairStage<float>) % 16 == 0 && sizeof(PairStage<double>) % 16 == 0,
+static_assert(sizeof(PairStage<float, false>) % 16 == 0 && sizeof(PairStage<double, false>) % 16 == 0 &&
+                  sizeof(PairStage<float, true>) % 16 == 0 && sizeof(PairStage<double, true>) % 16 == 0,
               "stages must stay 16-byte aligned");
 
-template <typename T>
+template <typename T, bool L1G = false>
 constexpr size_t spmv_smem_bytes()
 {
-    return kSpmvWs ? sizeof(PairStage<T>) * kWsPairs : sizeof(WarpStage<T>) * kTaskWarps;
+    return kSpmvWs ? sizeof(PairStage<T, L1G>) * kWsPairs : sizeof(WarpStage<T>) * kTaskWarps;
 }
+
+// Nonzeros per chunk (and the largest short task) of an SpMV whose gathered
+// vector has x_len entries.
+template <typename T>
+inline int spmv_cap(int64_t x_len);
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -693,7 +716,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
           const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
           const T* __restrict__ val, int* err, SplitRows sp, Epi epi)
 {
-    constexpr int CAPW = cap_w<T>();
+    constexpr int CAPW = cap_ws<T, L1G>();
     constexpr int VA = 16 / (int)sizeof(T);
     constexpr int NS = kWsStages;
     constexpr unsigned long long kWaitNs = 50ull * 1000 * 1000;
@@ -705,7 +728,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pair = warp >> 1;
     const bool producer = (warp & 1) == 0;
-    PairStage<T>& P = reinterpret_cast<PairStage<T>*>(smem_raw)[pair];
+    PairStage<T, L1G>& P = reinterpret_cast<PairStage<T, L1G>*>(smem_raw)[pair];
     if (producer && lane == 0) {
         for (int q = 0; q < NS; ++q) {
             mbar_init(&P.tma[q], 1);
@@ -1043,11 +1066,11 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
 // Dynamic shared-memory limit (and the optional carveout preference) of one
 // SpMV instantiation; spmv_prepare sets both gather variants of an epilogue.
 // Call before any launch or graph capture of that epilogue.
-template <typename T>
+template <typename T, bool L1G = false>
 inline cudaError_t spmv_set_attrs(const void* f)
 {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)spmv_smem_bytes<T>());
+                                         (int)spmv_smem_bytes<T, L1G>());
     if (e != cudaSuccess || kSpmvCarveout < 0) return e;
     return cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, kSpmvCarveout);
 }
@@ -1056,9 +1079,9 @@ template <typename T, class Epi>
 inline cudaError_t spmv_prepare()
 {
     if constexpr (kSpmvWs) {
-        cudaError_t e = spmv_set_attrs<T>((const void*)k_spmv_ws<T, Epi, true>);
+        cudaError_t e = spmv_set_attrs<T, true>((const void*)k_spmv_ws<T, Epi, true>);
         if (e != cudaSuccess) return e;
-        return spmv_set_attrs<T>((const void*)k_spmv_ws<T, Epi, false>);
+        return spmv_set_attrs<T, false>((const void*)k_spmv_ws<T, Epi, false>);
     } else {
         cudaError_t e = spmv_set_attrs<T>((const void*)k_spmv<T, Epi, true>);
         if (e != cudaSuccess) return e;
@@ -1069,6 +1092,13 @@ inline cudaError_t spmv_prepare()
 // Gathers from a vector of at most this many bytes go through L1 (it stays
 // resident there); larger vectors are gathered without L1 allocation.
 constexpr int64_t kL1GatherBytes = 96 * 1024;
+
+template <typename T>
+inline int spmv_cap(int64_t x_len)
+{
+    if (!kSpmvWs) return cap_w<T>();
+    return x_len * (int64_t)sizeof(T) <= kL1GatherBytes ? cap_ws<T, true>() : cap_ws<T, false>();
+}
 
 // pdl: launch with programmatic stream serialisation (the kernel may start
 // before the previous kernel of the stream has finished; it waits for it at its
@@ -1085,8 +1115,10 @@ inline void launch_spmv(int grid, cudaStream_t st, const int32_t* task_row,
                         int* err, int64_t x_len, const Epi& epi, bool pdl = false,
                         const SplitRows& sp = SplitRows{})
 {
-    const size_t sm = spmv_smem_bytes<T>();
     const bool l1 = x_len * (int64_t)sizeof(T) <= kL1GatherBytes;
+    const size_t sm = !kSpmvWs ? spmv_smem_bytes<T>()
+                      : l1     ? spmv_smem_bytes<T, true>()
+                               : spmv_smem_bytes<T, false>();
     if constexpr (kSpmvWs) {
         if (pdl && PDHG_PDL) {
             cudaLaunchConfig_t cfg = {};

@@ -39,14 +39,15 @@ PROBS = {
 }
 
 
-def _check_trace(tr, tro, rtol=1e-8):
+def _check_trace(tr, tro, rtol=1e-8, omega_rtol=1e-10):
     assert len(tr) == len(tro)
     for a, b in zip(tr, tro):
         assert a["k"] == b["k"] and a["attempts"] == b["attempts"]
         assert a["restart"] == b["restart"], (a, b)
         assert a["cand_is_avg"] == b["cand_is_avg"] == 1.0
-        for f in ("omega", "eta"):
-            assert a[f] == pytest.approx(b[f], rel=1e-10), (f, a[f], b[f])
+        assert a["eta"] == pytest.approx(b["eta"], rel=1e-10), ("eta", a["eta"], b["eta"])
+        assert a["omega"] == pytest.approx(b["omega"], rel=omega_rtol), ("omega", a["omega"],
+                                                                        b["omega"])
         for f in ("kkt_cur", "kkt_avg", "kkt_cand", "rel_gap", "rel_pres", "rel_dres"):
             assert a[f] == pytest.approx(b[f], rel=rtol, abs=1e-10), (f, a[f], b[f])
 
@@ -81,7 +82,10 @@ def test_fp64_halpern_solve_matches_oracle(L, oracle_mod, tol):
     assert info["status"] == L.LP_OPTIMAL == io["status"]
     assert info["iters"] == io["iters"]
     assert float(lp.c @ x) == pytest.approx(float(lp.c @ xo), rel=1e-6)
-    _check_trace(tr, tro, rtol=1e-6)
+    # thousands of iterations: Algorithm 4's omega is a ratio of differences of
+    # restart points, which carry the two runs' accumulated summation-order
+    # differences; compared at 1e-8 here (1e-10 in the 700-iteration tracking)
+    _check_trace(tr, tro, rtol=1e-6, omega_rtol=1e-8)
     k = oracle_mod.kkt(lp, x, y)
     assert max(k["rel_gap"], k["rel_pres"], k["rel_dres"]) <= tol * (1 + 1e-6)
 
