@@ -705,9 +705,23 @@ def adjoint_leg(L, reps=3):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     prob.close()
+    # the batch of 64 instances at m = 5,000 (one after another, host buffers)
+    from paper_2508_16806_gb300 import autograd as AG
+    t_batch = time.perf_counter()
+    for k in range(64):
+        lpk, xk = synth.adjoint_lp(5000, 10000, 20, seed=20250820 + k)
+        pk = L.Problem(lpk, device_copy=True)
+        xs, _, _ = AG.unroll(pk, K, precision=L.LP_PREC_MIXED)
+        AG.grad(pk, K, ckpt, 2.0 * (xs - xk), precision=L.LP_PREC_MIXED)
+        pk.close()
+    torch.cuda.synchronize()
+    batch_s = time.perf_counter() - t_batch
     return {"workload": "planted LP 100,000 x 200,000, 20 nonzeros per row, K = 500, "
                         "checkpoint every 50, FP32", "lp_grad_s": ms / 1e3,
-            "unrolled_steps_per_s": K / (ms / 1e3), "nnz": lp.nnz}
+            "unrolled_steps_per_s": K / (ms / 1e3), "nnz": lp.nnz,
+            "batch_64_at_m5000_s": batch_s,
+            "batch_64_note": "64 instances 5,000 x 10,000 one after another: generate, create, "
+                             "unroll, grad (host buffers), destroy; host wall clock"}
 
 
 def fishnet_schedule(P):
