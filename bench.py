@@ -621,8 +621,9 @@ def dispatch_leg(L, tol):
 def batch_leg(L, tol):
     """The 512 planted LPs: one lp_batch_solve (mixed, autotuned schedules) after
     a warm-up, CUDA events; per-LP device time to tol; the same 512 LPs by the
-    batched FP64 path and by a loop of plain FP64 single solves (the north
-    star's comparison: each lp_solve timed with CUDA events, creation apart);
+    batched FP64 path and by a loop of plain FP64 single solves (the FP64 GPU
+    path the batched form is compared with: each lp_solve timed with CUDA
+    events, creation apart);
     the oracle's FP64 error on a sample of 16 batch results."""
     import torch
     from paper_2508_16806_gb300 import synth
