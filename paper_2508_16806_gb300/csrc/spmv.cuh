@@ -130,6 +130,16 @@ __host__ __device__ constexpr int cap_ws()
                                       : cap_w<T>();
 }
 
+// v[p] x[p] + v[p + step] x[p + step] + ... over [p, pe) by fused multiply-adds
+// (one chain).
+template <typename T>
+__device__ __forceinline__ T strided_dot(const T* v, const T* x, int p, int pe, int step)
+{
+    T a = 0;
+    for (; p < pe; p += step) a = fma(v[p], x[p], a);
+    return a;
+}
+
 // v[p] + v[p + step] + ... over [p, pe).  In FP32 two partial sums keep two
 // shared-memory loads in flight (measured: K side 112 -> 106 us on the 1M x 2M
 // LP); in FP64 the single chain is faster (more registers per value).
@@ -172,9 +182,10 @@ __device__ __forceinline__ T warp_sum_T(T v)
 // per lane no longer depends on how the row lengths are mixed (with one group
 // of lanes per row, a task with one long and many short rows waits for the long
 // one).  Leaves the warp synchronised.
+// With xs, the terms are the products vs[p] xs[p], taken by fused multiply-adds.
 template <typename T>
 __device__ __forceinline__ void seg_row_sums(const T* vs, const int* rps, int nrows, int len,
-                                             int lane, T* rsum)
+                                             int lane, T* rsum, const T* xs = nullptr)
 {
     for (int j = lane; j < nrows; j += 32) rsum[j] = T(0);
     __syncwarp();
@@ -213,7 +224,7 @@ __device__ __forceinline__ void seg_row_sums(const T* vs, const int* rps, int nr
                     rend = rps[r + 1];
                 } while (p >= rend);
             }
-            a += vs[p];
+            a = xs ? fma(vs[p], xs[p], a) : a + vs[p];
         }
         key = r;
         t = a;
@@ -403,6 +414,12 @@ struct HasSplitAcc : std::false_type {};
 template <class E>
 struct HasSplitAcc<E, std::void_t<decltype(&E::split_acc)>> : std::true_type {};
 
+// FP64: a short task's products are not formed by the producer; it stores the
+// gathered entries beside the values and the consumer adds v x by fused
+// multiply-adds (one FP64 instruction per nonzero instead of a multiply and an
+// add: GB300's FP64 pipe bounds the FP64 SpMVs).
+template <typename T> struct WsFmaSum { static constexpr bool value = sizeof(T) == 8; };
+
 template <typename T, bool L1G>
 struct alignas(16) PairStage {
     static constexpr int CAPW = cap_ws<T, L1G>();
@@ -417,6 +434,9 @@ struct alignas(16) PairStage {
     WsDesc desc[kWsStages];
     int rps[kTaskRows + 1];        // row starts of the consumer's short task
     T rsum[kTaskRows];             // its row sums (segmented form)
+    // the gathered vector entries of a short task's chunk (kWsFmaSum: the
+    // consumer forms the products by fused multiply-adds into its row sums)
+    T xg[WsFmaSum<T>::value ? kWsStages : 1][WsFmaSum<T>::value ? VPAD : 16 / sizeof(T)];
 };
 static_assert(sizeof(PairStage<float, false>) % 16 == 0 && sizeof(PairStage<double, false>) % 16 == 0 &&
                   sizeof(PairStage<float, true>) % 16 == 0 && sizeof(PairStage<double, true>) % 16 == 0,
@@ -886,6 +906,29 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                         __syncwarp();   // every lane has read its values
                         vbuf[lane] = along;
                     }
+                } else if constexpr (WsFmaSum<T>::value) {
+                    // the gathered entries go beside the values (see WsFmaSum)
+                    T* xbuf = P.xg[st];
+#pragma unroll
+                    for (int k = 0; k < UG; ++k) {
+                        const int off = (k * 32 + lane) * VEC;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const int p = off + v;
+                            if (p >= vo && p < lim) {
+                                if constexpr (L1G) vv[k][v] = __ldg(xv + ii[k][v]);
+                                else vv[k][v] = ld_gather(xv + ii[k][v]);
+                            } else {
+                                vv[k][v] = T(0);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < UG; ++k) {
+                        const int off = (k * 32 + lane) * VEC;
+                        if (off < lim)
+                            *reinterpret_cast<typename VT::V*>(xbuf + off) = VT::pack(vv[k]);
+                    }
                 } else {
 #pragma unroll
                     for (int k = 0; k < UG; ++k) {
@@ -1026,9 +1069,11 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
             } else {
                 const int v0 = d.cs & ~(VA - 1);
                 const T* vs = P.v[st] + (d.cs - v0);
+                // FP64: the gathered entries, multiplied in here (WsFmaSum)
+                const T* xs = WsFmaSum<T>::value ? P.xg[st] + (d.cs - v0) : nullptr;
                 const int* rps = P.rps;
                 if (kWsSegSum || (d.flags & kWsSeg)) {
-                    seg_row_sums<T>(vs, rps, nrows, d.ce - d.cs, lane, P.rsum);
+                    seg_row_sums<T>(vs, rps, nrows, d.ce - d.cs, lane, P.rsum, xs);
                     if (lane < nrows) epi.row(r0 + lane, P.rsum[lane], pre0, acc);
                     if (kTaskRows > 32 && lane + 32 < nrows)
                         epi.row(r0 + 32 + lane, P.rsum[lane + 32], pre1, acc);
@@ -1039,7 +1084,8 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                     T a = 0;
                     if (j < nrows) {
                         const int pb = rps[j], pe = rps[j + 1];
-                        a = strided_sum(vs, pb + g, pe, G);
+                        if constexpr (WsFmaSum<T>::value) a = strided_dot(vs, xs, pb + g, pe, G);
+                        else a = strided_sum(vs, pb + g, pe, G);
                     }
                     for (int o = G >> 1; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o, G);
                     const T v = __shfl_sync(0xffffffffu, a, (lane * G) & 31);
@@ -1050,7 +1096,10 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
                         const int j = lane + 32 * half;
                         if (j < nrows) {
                             const int pb = rps[j], pe = rps[j + 1];
-                            epi.row(r0 + j, strided_sum(vs, pb, pe, 1), half ? pre1 : pre0, acc);
+                            T v;
+                            if constexpr (WsFmaSum<T>::value) v = strided_dot(vs, xs, pb, pe, 1);
+                            else v = strided_sum(vs, pb, pe, 1);
+                            epi.row(r0 + j, v, half ? pre1 : pre0, acc);
                         }
                     }
                 }
