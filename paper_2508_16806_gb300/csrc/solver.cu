@@ -824,9 +824,10 @@ static int primal_grid(int64_t n)
 // Whether the primal step of a PDHG attempt runs in the K^T launch's epilogue.
 // FP32: yes (on the 1M x 2M power-law LP the K^T launch with the fused step
 // takes 109 us against 114 + 16 us for the product and a separate primal
-// kernel).  FP64: no; its five prefetched operands per row (two rows per lane)
-// spill registers in the SpMV, and the fused launch took 247 us against
-// 183 + 33 us for the product and k_primal after it.
+// kernel).  FP64: no; with FP64's fused products the fused launch no longer
+// spills but takes 212 us against 173 + 33 us for the product and k_primal
+// after it (the elementwise step costs more inside the SpMV, where the FP64 pipe
+// is already the limit, than as its own streaming pass).
 #ifndef PDHG_FUSE_PRIMAL_F32
 #define PDHG_FUSE_PRIMAL_F32 1
 #endif
