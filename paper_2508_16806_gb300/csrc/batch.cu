@@ -57,6 +57,10 @@ struct BatchSched {
     int32_t *lpK = nullptr, *lpT = nullptr;          // task -> LP
     int32_t *wbegK = nullptr, *permK = nullptr;      // per-warp task lists (K)
     int32_t *wbegT = nullptr, *permT = nullptr;      // per-warp task lists (K^T)
+    // the lists without the tasks of finished LPs (rebuilt at each check) and
+    // their ends: list w is permKl[wbegK[w], wendK[w])
+    int32_t *permKl = nullptr, *permTl = nullptr, *wendK = nullptr, *wendT = nullptr;
+    int wK = 0, wT = 0;                              // lists per schedule
     int32_t *t0K = nullptr, *t0T = nullptr;          // LP -> first task [B + 1]
     double *partK = nullptr, *partT = nullptr;       // per-task step partials [1 | 2][nt]
     double *partR = nullptr, *partC = nullptr;       // per-task check partials [kRowQ | kColQ][nt]
@@ -705,7 +709,8 @@ lp_status build_sched(BatchHandle* bh, SchedParams pK, SchedParams pT)
         for (void* p : {(void*)S.taskK, (void*)S.taskT, (void*)S.lpK, (void*)S.lpT,
                         (void*)S.t0K, (void*)S.t0T, (void*)S.nzK, (void*)S.nzT, (void*)S.partK,
                         (void*)S.partT, (void*)S.partR, (void*)S.partC, (void*)S.wbegK,
-                        (void*)S.permK, (void*)S.wbegT, (void*)S.permT})
+                        (void*)S.permK, (void*)S.wbegT, (void*)S.permT, (void*)S.permKl,
+                        (void*)S.permTl, (void*)S.wendK, (void*)S.wendT})
             dev_free(h, p);
     }
     std::vector<int32_t> tK, tT, lK, lT, k0(B + 1), c0(B + 1);
@@ -765,6 +770,12 @@ lp_status build_sched(BatchHandle* bh, SchedParams pK, SchedParams pT)
     LP_TRY(up32(&S.permK, pk));
     LP_TRY(up32(&S.wbegT, wt));
     LP_TRY(up32(&S.permT, pt));
+    S.wK = (int)wk.size() - 1;
+    S.wT = (int)wt.size() - 1;
+    LP_TRY(dev_alloc_n(h, &S.permKl, pk.size() + 1));
+    LP_TRY(dev_alloc_n(h, &S.permTl, pt.size() + 1));
+    LP_TRY(dev_alloc_n(h, &S.wendK, (size_t)S.wK + 1));
+    LP_TRY(dev_alloc_n(h, &S.wendT, (size_t)S.wT + 1));
     LP_TRY(dev_alloc_n(h, &S.partK, (size_t)S.ntK + 8));
     LP_TRY(dev_alloc_n(h, &S.partT, 2 * (size_t)S.ntT + 8));
     LP_TRY(dev_alloc_n(h, &S.partR, kRowQ * (size_t)S.ntK + 8));
@@ -925,6 +936,46 @@ lp_status batch_scale(BatchHandle* bh, const lp_opts* o, double* normK_dev)
     return LP_OK;
 }
 
+// The task lists without the tasks of finished LPs: one warp per list keeps,
+// in order, the entries of perm[wbeg[w], wbeg[w + 1]) whose LP is not done and
+// writes them to perm_live from wbeg[w] on; wend[w] is where they end.  Late in
+// a batched solve most LPs have finished, and the SpMV's lists would otherwise
+// step over their tasks one by one at every launch.
+__global__ void kb_compact_tasks(const int32_t* __restrict__ wbeg, const int32_t* __restrict__ perm,
+                                 const int32_t* __restrict__ task_lp, const Ctrl* __restrict__ ctrl,
+                                 int workers, int32_t* __restrict__ perm_live,
+                                 int32_t* __restrict__ wend)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (w >= workers) return;
+    const int b = wbeg[w], e = wbeg[w + 1];
+    int out = b;
+    for (int p0 = b; p0 < e; p0 += 32) {
+        const int p = p0 + lane;
+        int t = 0;
+        bool keep = false;
+        if (p < e) {
+            t = perm[p];
+            keep = !ctrl[task_lp[t]].done;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        if (keep) perm_live[out + __popc(mask & ((1u << lane) - 1u))] = t;
+        out += __popc(mask);
+    }
+    if (lane == 0) wend[w] = out;
+}
+
+template <typename T>
+void b_compact(BatchHandle* bh, cudaStream_t st)
+{
+    BatchSched<T>& S = sched_of<T>(bh);
+    kb_compact_tasks<<<(S.wK * 32 + 255) / 256, 256, 0, st>>>(S.wbegK, S.permK, S.lpK, bh->ctrl,
+                                                             S.wK, S.permKl, S.wendK);
+    kb_compact_tasks<<<(S.wT * 32 + 255) / 256, 256, 0, st>>>(S.wbegT, S.permT, S.lpT, bh->ctrl,
+                                                             S.wT, S.permTl, S.wendT);
+}
+
 template <typename T>
 void b_launch_attempt(BatchHandle* bh, cudaStream_t st)
 {
@@ -935,10 +986,15 @@ void b_launch_attempt(BatchHandle* bh, cudaStream_t st)
                                                 E.KTY[1], E.c, E.l, E.u, E.XS, h->n);
     EpiBDual<T> ed{bh->ctrl, S.lpK, E.X[0], E.X[1], E.Y[0], E.Y[1], E.KX[0], E.KX[1], E.YS,
                    E.q, h->sense, S.partK};
-    launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permK, h->rp, h->ci, E.val, h->dev_err, h->n, ed);
+    SplitRows lK, lT;
+    lK.wend = S.wendK;
+    lT.wend = S.wendT;
+    launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permKl, h->rp, h->ci, E.val, h->dev_err,
+                   h->n, ed, false, lK);
     EpiBPrimalT<T> et{bh->ctrl, S.lpT, E.Y[0], E.Y[1], E.X[0], E.X[1], E.KTY[0], E.KTY[1],
                       S.partT, S.ntT};
-    launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permT, h->trp, h->tci, E.tval, h->dev_err, h->m, et);
+    launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permTl, h->trp, h->tci, E.tval,
+                   h->dev_err, h->m, et, false, lT);
     kb_step_ctrl<<<(bh->meta.B + kBW - 1) / kBW, kBW * 32, 0, st>>>(
         bh->ctrl, bh->meta.B, S.t0K, S.t0T, S.partK, S.partT, S.ntT);
 }
@@ -952,13 +1008,20 @@ void b_launch_check(BatchHandle* bh, cudaStream_t st, cudaGraphConditionalHandle
     BatchSched<T>& S = sched_of<T>(bh);
     const int64_t m = h->m, n = h->n;
     const int B = bh->meta.B;
+    // drop the tasks of the LPs that finished at the previous check
+    b_compact<T>(bh, st);
     kb_check_prep<T><<<grid_n(n + m), kEW, 0, st>>>(bh->ctrl, bh->meta.lp_row, bh->meta.lp_col,
                                                      E.X[0], E.X[1], E.Y[0], E.Y[1], E.XS, E.YS,
                                                      E.XA, E.YA, E.l, E.u, h->sense, n, m);
+    SplitRows lK, lT;
+    lK.wend = S.wendK;
+    lT.wend = S.wendT;
     EpiBStore<T> e1{E.XA, E.KXA, nullptr, S.lpK, nullptr, bh->ctrl};
-    launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permK, h->rp, h->ci, E.val, h->dev_err, n, e1);
+    launch_spmv<T>(S.gK, st, S.taskK, S.nzK, S.ntK, S.wbegK, S.permKl, h->rp, h->ci, E.val,
+                   h->dev_err, n, e1, false, lK);
     EpiBStore<T> e2{E.YA, E.KTYA, nullptr, S.lpT, nullptr, bh->ctrl};
-    launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permT, h->trp, h->tci, E.tval, h->dev_err, m, e2);
+    launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permTl, h->trp, h->tci, E.tval,
+                   h->dev_err, m, e2, false, lT);
     kb_check_rows<T><<<(S.ntK + 7) / 8, kEW, 0, st>>>(bh->ctrl, S.taskK, S.lpK, S.ntK, E.Y[0],
                                                        E.Y[1], E.KX[0], E.KX[1], E.YA, E.KXA,
                                                        E.YANC, E.q, h->sense, E.Rt, E.Rinv, S.partR);
@@ -1116,7 +1179,7 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs,
         launch_spmv<T>(S.gT, st, S.taskT, S.nzT, S.ntT, S.wbegT, S.permT, h->trp, h->tci, E.tval, h->dev_err, m, e2);
     }
     b_launch_check<T>(bh, st, cudaGraphConditionalHandle{}, 0, 0);
-    h->launches += 9 + 3 + 4;
+    h->launches += 11 + 3 + 4;
     LP_CUDA_TRY(cudaGetLastError());
     auto t_setup = std::chrono::steady_clock::now();
     const int slots = o->check_every + (o->adaptive_step ? 4 : 0);
@@ -1130,7 +1193,7 @@ lp_status batch_solve_t(BatchHandle* bh, const lp_opts* o, lp_result* rs,
     if (derr) return LP_DEVICE_TIMEOUT;
     long long bodies = 0;
     for (const Ctrl& c : hc) bodies = std::max(bodies, c.bodies);
-    h->launches += bodies * (long long)(slots * 4 + 9);
+    h->launches += bodies * (long long)(slots * 4 + 11);
     // solutions, unscaled, stacked; then into each caller's buffers
     double* xo = nullptr;
     LP_TRY(dev_alloc_n(h, &xo, (size_t)(n + m)));

@@ -157,6 +157,9 @@ struct SplitRows {
     int* cnt = nullptr;              // [n] tickets taken in the current launch (0 between launches)
     void* slots = nullptr;           // [npieces] piece sums (the launch's T)
     int n = 0;                       // split rows
+    // Compacted task lists (batched solves): list w is perm[wbeg[w], wend[w])
+    // instead of perm[wbeg[w], wbeg[w + 1]).  nullptr: the full lists.
+    const int32_t* wend = nullptr;
 };
 
 // State and scaled data of one precision T (double or float).

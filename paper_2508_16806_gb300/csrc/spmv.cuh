@@ -760,7 +760,7 @@ k_spmv_ws(const int32_t* __restrict__ task_row, const int64_t* __restrict__ task
     __syncthreads();
     typename Epi::Acc acc;
     const int gw = blockIdx.x * kWsPairs + pair;
-    const int pbeg = wbeg[gw], pend = wbeg[gw + 1];
+    const int pbeg = wbeg[gw], pend = sp.wend ? sp.wend[gw] : wbeg[gw + 1];
     if (producer) {
         // ---------------------------------------------------------- producer
         const uint64_t pol = evict_first_policy();
