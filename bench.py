@@ -34,7 +34,7 @@ CACHE = os.environ.get("PDHG_BENCH_CACHE", "/tmp/pdhg_bench_cache")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # step kernels from one ncu capture of the current kernel source (absent when
 # the kernel changed after the capture).  Summary: profiles/spmv_powerlaw_1Mx2M_fp32.md
-NCU_TRAFFIC = {"spmv_K_dual": 198_720_768, "spmv_KT_primal": 230_188_032}
+NCU_TRAFFIC = {"spmv_K_dual": 198_677_504, "spmv_KT_primal": 230_124_032}
 
 # kernel classes of lp_profile_step: a PDHG attempt is the K-side SpMV with the
 # dual step and the Algorithm 5 decision, then the K^T-side SpMV with the fused
